@@ -1,0 +1,13 @@
+"""CPU FP64 oracle for LU_PRRP: test infrastructure only.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU legs (``cpu_baseline`` and
+``--impl reference``) may import this package. The product package
+``paper_1208_2451_gb300`` never imports it and shares no code with it.
+"""
+from .algorithm import (LUResult, NonFiniteError, PanelResult, SingularError, SwapLimitError,
+                      eta, householder_qr, lu_prrp, lu_solve, qrcp, refine, strong_rrqr, unpack)
+from . import metrics
+
+__all__ = ["LUResult", "NonFiniteError", "PanelResult", "SingularError", "SwapLimitError", "eta",
+           "householder_qr", "lu_prrp", "lu_solve", "qrcp", "refine", "strong_rrqr", "unpack",
+           "metrics"]
