@@ -123,7 +123,8 @@ def exact_lu_prrp(A_int, b, tau):
     A = [[Fraction(int(x)) for x in row] for row in A_int]
     perm = list(range(n))
     amax = max(abs(x) for row in A for x in row)
-    gmax = amax
+    gmax = amax                 # A and the block Schur complements
+    umax = Fraction(0)
     max_l21 = Fraction(0)
     margins = []
     swaps = 0
@@ -175,8 +176,9 @@ def exact_lu_prrp(A_int, b, tau):
                 A[r][k0 + c] = sum(row[i] * L11[i][c] for i in range(c, w))
         for r in range(k0, k0 + w):
             for c in range(r, n):
-                gmax = max(gmax, abs(A[r][c]))
+                umax = max(umax, abs(A[r][c]))
     return {"LU": A, "perm": perm, "growth": gmax / amax if amax else Fraction(1),
+            "growth_u": umax / amax if amax else Fraction(1),
             "max_L21": max_l21, "swaps": swaps, "margins": margins}
 
 

@@ -70,6 +70,7 @@ def test_exact_brute_force_agreement():
         scale = max(1.0, np.max(np.abs(LUx)))
         np.testing.assert_allclose(r.LU, LUx, atol=1e-11 * scale, rtol=0)
         assert abs(r.growth - float(ex["growth"])) <= 1e-11 * float(ex["growth"])
+        assert abs(r.growth_u - float(ex["growth_u"])) <= 1e-11 * float(ex["growth_u"])
         assert abs(r.max_L21 - float(ex["max_L21"])) <= 1e-12
     assert checked >= 80
     assert with_swaps >= 5, "the tau-swap path must be exercised"
@@ -142,6 +143,7 @@ def test_wilkinson_b1_growth_is_2_pow_n_minus_1(n):
     """GEPP on Wilkinson's matrix grows exactly as 2^(n-1) (Section 2.2)."""
     r = oracle.lu_prrp(pi.wilkinson(n), b=1)
     assert r.growth == 2.0 ** (n - 1)
+    assert r.growth_u == 2.0 ** (n - 1)
 
 
 @pytest.mark.parametrize("n", [3, 10, 30, 50])
@@ -177,6 +179,28 @@ def test_foster_table():
         ui1 = M.norm1(sl.solve_triangular(U, np.eye(g["n"])))
         assert abs(ui1 - row["U_inv_1"]) <= 0.01, (row, ui1)
         assert M.factor_residual(A, r.LU, r.perm) <= 64 * g["n"] * EPS
+
+
+@pytest.mark.slow
+def test_wright_table_growth():
+    """Table 'tab_wright': g_W = 1 for b = 8..128 at n = 2048, h = 0.3 (both the exact
+    exponential and the first-order block the paper displays give it)."""
+    g = json.load(open(os.path.join(GOLDEN, "wright_n2048.json")))
+    for exact in (True, False):
+        A = pi.wright(g["n"], g["h"], exact)
+        for row in g["rows"]:
+            r = oracle.lu_prrp(A, b=row["b"], tau=2.0)
+            assert abs(r.growth - row["gW"]) <= 0.01, (exact, row, r.growth)
+            assert M.factor_residual(A, r.LU, r.perm) <= 64 * g["n"] * EPS
+
+
+@pytest.mark.slow
+def test_random_growth_context():
+    """Section 2.3: g_W of LU_PRRP on randn(4096) with b = 64 is 'about 19' (statistical:
+    one seed, a wide window; the max|U| variant of the definition gives ~55 and fails)."""
+    r = oracle.lu_prrp(pi.randn(4096, 0), b=64, tau=2.0)
+    assert 10.0 <= r.growth <= 40.0, r.growth
+    assert r.growth_u > r.growth
 
 
 def test_upper_bound_table():
