@@ -1,0 +1,218 @@
+/*
+ * prrp.h - C ABI of the GB300 (sm_103a) LU_PRRP library (libprrp.so).
+ *
+ * LU_PRRP is the blocked LU factorization with panel rank revealing pivoting of
+ * Khabou, Demmel, Grigori and Gu (arXiv:1208.2451): every b-column panel is pivoted by a
+ * strong rank revealing QR of its transpose (Section 2.1, Algorithm 1; Appendix A,
+ * Algorithm 2), which bounds each block multiplier |L21| by tau and the growth factor by
+ * (1 + tau b)^(n/b) (Section 2.2).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are ROW-MAJOR doubles: element (i, j) of a matrix with leading dimension ld
+ *    is at p[i * ld + j]; ld >= number of columns.
+ *  - Pointers named d* are device pointers owned by the caller (for example PyTorch
+ *    tensors); pointers named h* are host pointers owned by the caller.  Handles
+ *    (prrp_ctx, prrp_factors, prrp_server) are owned by the library and released with
+ *    their destroy call.
+ *  - "stream" is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *    Work is enqueued in stream order.  Calls that return a device-side outcome
+ *    (prrp_factor, prrp_solve, ...) synchronize the stream before they return.
+ *  - Errors are reported only through return codes; nothing aborts or traps.  A kernel
+ *    that meets an error (zero pivot, non-finite value, a wait that ran out) writes a
+ *    status word and the kernels after it return at once.
+ *  - One prrp_ctx per host thread.  The server object is internally locked.
+ *  - The permutation convention is perm[i] = original row placed at position i, so
+ *    (P A)[i, :] = A[perm[i], :] and P A = L U.
+ */
+#ifndef PRRP_H
+#define PRRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct prrp_ctx prrp_ctx;
+typedef struct prrp_factors prrp_factors;
+
+typedef enum {
+  PRRP_OK = 0,
+  PRRP_ERR_INVALID_ARG = 1,   /* bad size, pointer, leading dimension or option */
+  PRRP_ERR_SINGULAR = 2,      /* zero pivot; stats.info holds its 1-based column */
+  PRRP_ERR_NONFINITE = 3,     /* NaN or Inf in the input matrix */
+  PRRP_ERR_OOM = 4,           /* device or host allocation failed */
+  PRRP_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+  PRRP_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out */
+  PRRP_ERR_SWAP_LIMIT = 7,    /* a panel needed more than opts.max_swaps interchanges */
+  PRRP_ERR_NOT_CONVERGED = 8, /* iterative refinement stopped above its target */
+  PRRP_ERR_BUSY = 9,          /* server: request can never fit the admission budget */
+  PRRP_ERR_UNSUPPORTED = 10   /* size or option outside what this build supports */
+} prrp_status;
+
+typedef enum {
+  PRRP_FP64 = 0,   /* Schur update and TRSM in FP64 (DFMA) */
+  PRRP_TF32 = 1,   /* Schur update on tcgen05 tensor cores in TF32, FP32 accumulation */
+  PRRP_BF16X3 = 2, /* Schur update on tcgen05 as 3-term split BF16, FP32 accumulation */
+  PRRP_FP32 = 3    /* FP32 factor (batched path) */
+} prrp_precision;
+
+typedef struct {
+  int b;                /* panel width, 1 <= b <= 128 (default 64) */
+  double tau;           /* strong RRQR threshold, tau >= 1 (default 2; the paper uses tau > 1) */
+  int prec;             /* prrp_precision of the trailing update (default PRRP_FP64) */
+  int max_swaps;        /* interchanges allowed per panel after QRCP (default 64) */
+  int refine_max_iter;  /* FP64 iterative refinement corrections (default 10) */
+  double refine_target; /* stop refining once eta <= target (default 2^-53) */
+} prrp_opts;
+
+typedef struct {
+  double growth;   /* g_W = max(|A|, every block Schur complement A22 after an update) / max|A|
+                      (Section 2.2: the entries after each block elimination step) */
+  double growth_u; /* max |U| / max |A| (adds the diagonal-block GEPP) */
+  double max_l21;  /* largest |block multiplier| (R11^-1 R12)^T over all panels, <= tau */
+  double amax;     /* max |a_ij| of the input */
+  int swaps;       /* strong RRQR interchanges over all panels */
+  int info;        /* 1-based column of the first zero pivot, 0 if none */
+  int panels;      /* panels factored */
+} prrp_factor_stats;
+
+typedef struct {
+  int iterations;  /* refinement corrections applied */
+  double eta0;     /* normwise backward error (1-norm) of the first solution */
+  double eta;      /* normwise backward error of the returned solution */
+} prrp_solve_info;
+
+/* Fill *opts with the defaults above. */
+void prrp_opts_default(prrp_opts* opts);
+
+/* Human-readable name of a status code (static string). */
+const char* prrp_status_string(prrp_status s);
+
+/* Library version string (static). */
+const char* prrp_version(void);
+
+/* Text of the last CUDA failure seen by ctx (valid until the next call on ctx). */
+const char* prrp_ctx_last_error(const prrp_ctx* ctx);
+
+/* Create a context bound to CUDA device `device`.  It owns device workspace that grows
+ * with the largest problem seen.  Returns INVALID_ARG for a bad device, CUDA otherwise. */
+prrp_status prrp_create(prrp_ctx** ctx, int device);
+prrp_status prrp_destroy(prrp_ctx* ctx);
+
+/*
+ * prrp_factor - LU_PRRP of the n x n row-major matrix dA (Algorithm 1).
+ *
+ * For each panel j (columns k0 .. k0+w-1, w = min(b, n-k0)):
+ *   1. strong RRQR of the transposed panel selects w pivot rows (Algorithm 2: QR with
+ *      column pivoting, then interchanges while some |(R11^-1 R12)_ij| > tau);
+ *   2. L21 = (R11^-1 R12)^T (Algorithm 1, line 4);
+ *   3. the row permutation is applied to all n columns (line 5);
+ *   4. A22 -= L21 A12 (eq. "update", line 7);
+ *   5. GEPP on the w x w diagonal block and U12 = L11^-1 Pi_jj^T A12 (lines 10-11);
+ *   6. the rows below the block receive the final L21 Pi_jj L11, so that on return dA holds
+ *      the ordinary unit-lower L (strictly below the diagonal) and U (on and above it).
+ * n = 0 is a no-op.  dA is overwritten; *F receives a handle holding the permutation and
+ * statistics (and a reference to dA, which must stay alive while F is used).
+ * Errors: INVALID_ARG, NONFINITE (checked before any write to dA), SINGULAR (dA then holds
+ * a partial factorization), SWAP_LIMIT, TIMEOUT, CUDA, OOM, UNSUPPORTED (n > 65536 or
+ * panel larger than the GPU's shared memory, or prec not available).
+ */
+prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts,
+                        void* stream, prrp_factors** F);
+
+/* Copy the permutation (n ints, may be NULL) and statistics (may be NULL) to the host. */
+prrp_status prrp_factors_get(const prrp_factors* F, int* hperm, prrp_factor_stats* stats);
+
+/* Device pointer to the factor's permutation (n ints, library-owned). */
+const int* prrp_factors_perm_device(const prrp_factors* F);
+
+void prrp_factors_destroy(prrp_factors* F);
+
+/*
+ * prrp_solve - X = A^-1 B with the factors of prrp_factor (Section 2.3 solver tests):
+ * Y = P B, forward substitution with the unit-lower L, back substitution with U.
+ * dB (n x nrhs, row-major, ldb) is overwritten by X.  If dA_orig (the unfactored matrix,
+ * n x n, lda of the factorization) is not NULL, FP64 iterative refinement follows
+ * (Section 3.3): r = B - A X in FP64, X += (LU)^-1 P r, until eta <= opts.refine_target,
+ * eta stops halving, or opts.refine_max_iter corrections (opts may be NULL: defaults).
+ * info (may be NULL) receives eta of the first and final solutions (max over columns).
+ */
+prrp_status prrp_solve(prrp_ctx* ctx, const prrp_factors* F, const double* dA_orig, int nrhs,
+                       double* dB, int ldb, const prrp_opts* opts, void* stream,
+                       prrp_solve_info* info);
+
+/*
+ * prrp_gesv_host - end-to-end solve from HOST memory: copies hA (n x n, lda) and hB
+ * (n x nrhs, ldb) to device workspace owned by ctx, factors, solves (refining in FP64
+ * against the copied A when opts->refine_max_iter > 0), and copies X back into hX
+ * (n x nrhs, ldb).  hA and hB are not modified.  Pinned host memory gives the fastest
+ * copies; pageable memory works.
+ */
+prrp_status prrp_gesv_host(prrp_ctx* ctx, int n, const double* hA, int lda, int nrhs,
+                           const double* hB, int ldb, double* hX, const prrp_opts* opts,
+                           void* stream, prrp_factor_stats* stats, prrp_solve_info* info);
+
+/* ---- single steps of Algorithm 1, exposed for verification and measurement ---- */
+
+/*
+ * prrp_panel_select - steps 1-2 above on one m x w panel dP (row-major, ldp >= w),
+ * 1 <= w <= min(m, 128): strong RRQR of dP^T (Algorithm 2).  On return
+ *   hOrder[i] (m ints, host) = panel row placed at position i (positions 0..w-1 are the
+ *             selected rows, in pivot order);
+ *   dL21     ((m - w) x w, row-major, ld w, device) = (R11^-1 R12)^T, row i belonging to
+ *             the panel row at position w + i;
+ *   *hSwaps   = interchanges made after QRCP.
+ * dP is not modified.  SINGULAR if the panel has rank < w, SWAP_LIMIT as above.
+ */
+prrp_status prrp_panel_select(prrp_ctx* ctx, int m, int w, const double* dP, int ldp,
+                              double tau, int max_swaps, int* hOrder, double* dL21,
+                              int* hSwaps, void* stream);
+
+/*
+ * prrp_schur_update - step 4 alone: C -= L * U with C m x n (ldc), L m x k (ldl),
+ * U k x n (ldu), 1 <= k <= 128, all row-major device pointers, computed in `prec`
+ * (PRRP_FP64 uses DFMA; PRRP_TF32 / PRRP_BF16X3 use tcgen05 with FP32 accumulation).
+ */
+prrp_status prrp_schur_update(prrp_ctx* ctx, int m, int n, int k, const double* dL, int ldl,
+                              const double* dU, int ldu, double* dC, int ldc, int prec,
+                              void* stream);
+
+/* Kernel classes for prrp_ctx_kernel_stats. */
+enum {
+  PRRP_KIND_SCAN = 0,     /* input scan and permutation init */
+  PRRP_KIND_PANEL = 1,    /* strong RRQR panel (Algorithm 2) */
+  PRRP_KIND_PERMUTE = 2,  /* row interchanges of the panel (Algorithm 1, line 5) */
+  PRRP_KIND_UPDATE = 3,   /* Schur update A22 -= L21 A12 (line 7) */
+  PRRP_KIND_DIAG = 4,     /* GEPP of the diagonal block (line 10) */
+  PRRP_KIND_U12 = 5,      /* U12 = L11^-1 Pi_jj^T A12 and block-row interchanges (line 11) */
+  PRRP_KIND_LFIX = 6,     /* final multipliers L21 Pi_jj L11 */
+  PRRP_KIND_SOLVE = 7,    /* gather, forward/back substitution, refinement */
+  PRRP_KIND_COUNT = 8
+};
+
+/* Enable (1) or disable (0) per-kernel-class timing: each launch of ctx is bracketed by
+ * CUDA events on its stream and the elapsed times are summed per class after the call's
+ * synchronize.  Launch and algorithmic-flop counters are kept whether or not it is on. */
+prrp_status prrp_ctx_set_timing(prrp_ctx* ctx, int enable);
+
+/* Copy the per-class totals since the last reset (arrays of PRRP_KIND_COUNT; any may be
+ * NULL): milliseconds (only while timing is on), kernel launches, algorithmic flops
+ * (update: 2 (m-w)(n-k0-w) w per panel).  reset != 0 zeroes them afterwards. */
+prrp_status prrp_ctx_kernel_stats(prrp_ctx* ctx, double* ms, long long* launches,
+                                  long long* flops, int reset);
+
+/*
+ * prrp_selftest_wait - check of the failure path of the device-side bounded waits (no
+ * counterpart in the paper): launches a two-CTA cooperative grid in which one CTA waits at
+ * a grid barrier that the other never reaches.  The wait gives up after `spin_limit` polls
+ * (about 100 ns each; 0 = the library default of ~2 s) and the call returns
+ * PRRP_ERR_TIMEOUT with the context still usable.  Any other return is a failure.
+ */
+prrp_status prrp_selftest_wait(prrp_ctx* ctx, unsigned spin_limit, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRRP_H */

@@ -5,9 +5,10 @@ Only tests/, __graft_entry__.smoke() and bench.py's CPU legs (``cpu_baseline`` a
 ``paper_1208_2451_gb300`` never imports it and shares no code with it.
 """
 from .algorithm import (LUResult, NonFiniteError, PanelResult, SingularError, SwapLimitError,
-                      eta, householder_qr, lu_prrp, lu_solve, qrcp, refine, strong_rrqr, unpack)
+                      eta, householder_qr, lu_prrp, lu_solve, qrcp, refine, selection_multipliers, strong_rrqr, unpack)
 from . import metrics
 
 __all__ = ["LUResult", "NonFiniteError", "PanelResult", "SingularError", "SwapLimitError", "eta",
-           "householder_qr", "lu_prrp", "lu_solve", "qrcp", "refine", "strong_rrqr", "unpack",
+           "householder_qr", "lu_prrp", "lu_solve", "qrcp", "refine", "selection_multipliers",
+           "strong_rrqr", "unpack",
            "metrics"]

@@ -316,3 +316,26 @@ def refine(A: np.ndarray, LU: np.ndarray, perm: np.ndarray, bvec: np.ndarray,
             break
         x, hist = x_new, hist + [e]
     return x, hist
+
+
+def selection_multipliers(A: np.ndarray, perm: np.ndarray, b: int) -> list:
+    """For a permutation produced by some LU_PRRP run, recompute in FP64 each panel's block
+    multipliers L21 = A21 A11^-1 (Section 2.1, the product that equals (R11^-1 R12)^T) from
+    the row sets it implies: panel j selects rows perm[k0:k0+w] (their order inside the
+    block is GEPP's business and does not change L21's row set), and its Schur complement
+    is taken with exactly those rows eliminated.  Returns max |L21| per panel, so a
+    different-but-valid pivot sequence can be checked against tau."""
+    A = np.array(A, dtype=np.float64, copy=True)
+    n = A.shape[0]
+    S = A[np.asarray(perm)]              # rows in the given final order
+    out = []
+    for k0 in range(0, n, b):
+        w = min(b, n - k0)
+        if k0 + w >= n:
+            break
+        A11 = S[k0:k0 + w, k0:k0 + w]
+        A21 = S[k0 + w:, k0:k0 + w]
+        L21 = np.linalg.solve(A11.T, A21.T).T
+        out.append(float(np.max(np.abs(L21))))
+        S[k0 + w:, k0 + w:] -= L21 @ S[k0:k0 + w, k0 + w:]
+    return out

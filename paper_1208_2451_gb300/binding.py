@@ -1,0 +1,305 @@
+"""ctypes binding of libprrp.so: the C entry points under the same names, taking torch
+tensors (device memory) or numpy arrays (host memory).  Only argument marshalling happens
+here; every step of the factorization and solve runs in the library's CUDA kernels.
+
+There is no CPU fallback: importing this module raises ImportError when libprrp.so has
+not been built (``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libprrp.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libprrp.so is not built ({_LIB_PATH} missing); run "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = C.CDLL(_LIB_PATH)
+
+STATUS = {0: "PRRP_OK", 1: "PRRP_ERR_INVALID_ARG", 2: "PRRP_ERR_SINGULAR", 3: "PRRP_ERR_NONFINITE",
+          4: "PRRP_ERR_OOM", 5: "PRRP_ERR_CUDA", 6: "PRRP_ERR_TIMEOUT", 7: "PRRP_ERR_SWAP_LIMIT",
+          8: "PRRP_ERR_NOT_CONVERGED", 9: "PRRP_ERR_BUSY", 10: "PRRP_ERR_UNSUPPORTED"}
+PRRP_OK, PRRP_ERR_INVALID_ARG, PRRP_ERR_SINGULAR, PRRP_ERR_NONFINITE = 0, 1, 2, 3
+PRRP_ERR_OOM, PRRP_ERR_CUDA, PRRP_ERR_TIMEOUT, PRRP_ERR_SWAP_LIMIT = 4, 5, 6, 7
+PRRP_ERR_NOT_CONVERGED, PRRP_ERR_BUSY, PRRP_ERR_UNSUPPORTED = 8, 9, 10
+PRRP_FP64, PRRP_TF32, PRRP_BF16X3, PRRP_FP32 = 0, 1, 2, 3
+
+
+class prrp_opts(C.Structure):
+    _fields_ = [("b", C.c_int), ("tau", C.c_double), ("prec", C.c_int), ("max_swaps", C.c_int),
+                ("refine_max_iter", C.c_int), ("refine_target", C.c_double)]
+
+
+class prrp_factor_stats(C.Structure):
+    _fields_ = [("growth", C.c_double), ("growth_u", C.c_double), ("max_l21", C.c_double),
+                ("amax", C.c_double),
+                ("swaps", C.c_int), ("info", C.c_int), ("panels", C.c_int)]
+
+
+class prrp_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("eta0", C.c_double), ("eta", C.c_double)]
+
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_SIGS = {
+    "prrp_opts_default": (None, [C.POINTER(prrp_opts)]),
+    "prrp_status_string": (C.c_char_p, [_I]),
+    "prrp_version": (C.c_char_p, []),
+    "prrp_ctx_last_error": (C.c_char_p, [_P]),
+    "prrp_create": (_I, [C.POINTER(_P), _I]),
+    "prrp_destroy": (_I, [_P]),
+    "prrp_factor": (_I, [_P, _I, _P, _I, C.POINTER(prrp_opts), _P, C.POINTER(_P)]),
+    "prrp_factors_get": (_I, [_P, _P, C.POINTER(prrp_factor_stats)]),
+    "prrp_factors_perm_device": (_P, [_P]),
+    "prrp_factors_destroy": (None, [_P]),
+    "prrp_solve": (_I, [_P, _P, _P, _I, _P, _I, C.POINTER(prrp_opts), _P, C.POINTER(prrp_solve_info)]),
+    "prrp_gesv_host": (_I, [_P, _I, _P, _I, _I, _P, _I, _P, C.POINTER(prrp_opts), _P,
+                            C.POINTER(prrp_factor_stats), C.POINTER(prrp_solve_info)]),
+    "prrp_panel_select": (_I, [_P, _I, _I, _P, _I, _D, _I, _P, _P, C.POINTER(_I), _P]),
+    "prrp_schur_update": (_I, [_P, _I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _P]),
+    "prrp_selftest_wait": (_I, [_P, C.c_uint, _P]),
+    "prrp_ctx_set_timing": (_I, [_P, _I]),
+    "prrp_ctx_kernel_stats": (_I, [_P, _P, _P, _P, _I]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def exported_symbols() -> list[str]:
+    """Names this binding resolves in libprrp.so (all declared in include/prrp.h)."""
+    return sorted(_SIGS)
+
+
+class PrrpError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        self.name = STATUS.get(status, f"status {status}")
+        msg = f"{where}: {self.name}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+def _check(status: int, where: str, ctx=None, allow=()):
+    if status != PRRP_OK and status not in allow:
+        detail = ""
+        if ctx is not None and status == PRRP_ERR_CUDA:
+            detail = (_lib.prrp_ctx_last_error(ctx) or b"").decode()
+        raise PrrpError(status, where, detail)
+    return status
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_matrix(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or t.dim() != 2:
+        raise TypeError(f"{name}: a 2-D float64 CUDA tensor is expected")
+    if t.shape[1] > 1 and t.stride(1) != 1:
+        raise ValueError(f"{name}: rows must be contiguous (row-major)")
+    return max(t.stride(0), t.shape[1], 1)
+
+
+def default_opts(b=64, tau=2.0, prec=PRRP_FP64, max_swaps=64, refine_max_iter=10,
+                 refine_target=2.0 ** -53) -> prrp_opts:
+    o = prrp_opts()
+    _lib.prrp_opts_default(C.byref(o))
+    o.b, o.tau, o.prec, o.max_swaps = int(b), float(tau), int(prec), int(max_swaps)
+    o.refine_max_iter, o.refine_target = int(refine_max_iter), float(refine_target)
+    return o
+
+
+def prrp_version() -> str:
+    return _lib.prrp_version().decode()
+
+
+def prrp_status_string(status: int) -> str:
+    return _lib.prrp_status_string(int(status)).decode()
+
+
+class Context:
+    """Owns a prrp_ctx* bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        h = C.c_void_p()
+        _check(_lib.prrp_create(C.byref(h), int(device)), "prrp_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.prrp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Factors:
+    """Owns a prrp_factors* (the permutation and statistics of one factorization; L\\U stay
+    in the caller's tensor)."""
+
+    def __init__(self, handle, n, A):
+        self.handle = handle
+        self.n = n
+        self.A = A          # keeps the factored tensor alive
+
+    def perm(self) -> np.ndarray:
+        p = np.empty(self.n, dtype=np.int32)
+        _check(_lib.prrp_factors_get(self.handle, p.ctypes.data_as(C.c_void_p), None),
+               "prrp_factors_get")
+        return p
+
+    def stats(self) -> dict:
+        s = prrp_factor_stats()
+        _check(_lib.prrp_factors_get(self.handle, None, C.byref(s)), "prrp_factors_get")
+        return {"growth": s.growth, "growth_u": s.growth_u, "max_l21": s.max_l21, "amax": s.amax,
+                "swaps": s.swaps,
+                "info": s.info, "panels": s.panels}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.prrp_factors_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prrp_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def prrp_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def prrp_factor(ctx: Context, A, b=64, tau=2.0, prec=PRRP_FP64, max_swaps=64, stream=None,
+                allow=()) -> Factors:
+    """LU_PRRP of the square float64 CUDA tensor A in place (row-major L\\U on return)."""
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("square matrix expected")
+    lda = _dev_matrix(A, "A") if n else 1
+    o = default_opts(b, tau, prec, max_swaps)
+    h = C.c_void_p()
+    st = _lib.prrp_factor(ctx.handle, n, C.c_void_p(A.data_ptr() if n else 0), lda, C.byref(o),
+                          _stream_ptr(stream), C.byref(h))
+    F = Factors(h, n, A) if h.value else None
+    if st != PRRP_OK and st not in allow:
+        if F is not None:
+            F.close()
+        _check(st, "prrp_factor", ctx.handle)
+    if F is not None:
+        F.status = st
+    return F
+
+
+def prrp_solve(ctx: Context, F: Factors, B, A_orig=None, refine_max_iter=10,
+               refine_target=2.0 ** -53, stream=None) -> dict:
+    """Overwrite the float64 CUDA tensor B (n x nrhs) with A^-1 B; refine in FP64 against
+    A_orig when given."""
+    ldb = _dev_matrix(B, "B")
+    o = default_opts(refine_max_iter=refine_max_iter, refine_target=refine_target)
+    info = prrp_solve_info()
+    a0 = C.c_void_p(A_orig.data_ptr()) if A_orig is not None else None
+    st = _lib.prrp_solve(ctx.handle, F.handle, a0, B.shape[1], C.c_void_p(B.data_ptr()), ldb,
+                         C.byref(o), _stream_ptr(stream), C.byref(info))
+    _check(st, "prrp_solve", ctx.handle, allow=(PRRP_ERR_NOT_CONVERGED,))
+    return {"iterations": info.iterations, "eta0": info.eta0, "eta": info.eta,
+            "converged": st == PRRP_OK}
+
+
+def prrp_gesv_host(ctx: Context, A: np.ndarray, B: np.ndarray, b=64, tau=2.0, prec=PRRP_FP64,
+                   max_swaps=64, refine_max_iter=0, refine_target=2.0 ** -53, stream=None,
+                   X: np.ndarray | None = None):
+    """Solve A X = B from host arrays (copies in and out inside the call)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    n, nrhs = A.shape[0], B.shape[1]
+    if X is None:
+        X = np.empty((n, nrhs))
+    o = default_opts(b, tau, prec, max_swaps, refine_max_iter, refine_target)
+    stats, info = prrp_factor_stats(), prrp_solve_info()
+    st = _lib.prrp_gesv_host(ctx.handle, n, A.ctypes.data_as(C.c_void_p), n, nrhs,
+                             B.ctypes.data_as(C.c_void_p), nrhs, X.ctypes.data_as(C.c_void_p),
+                             C.byref(o), _stream_ptr(stream), C.byref(stats), C.byref(info))
+    _check(st, "prrp_gesv_host", ctx.handle, allow=(PRRP_ERR_NOT_CONVERGED,))
+    return X, {"growth": stats.growth, "swaps": stats.swaps, "max_l21": stats.max_l21}, \
+        {"iterations": info.iterations, "eta0": info.eta0, "eta": info.eta}
+
+
+def prrp_panel_select(ctx: Context, P, tau=2.0, max_swaps=64, stream=None):
+    """Strong RRQR selection on the m x w float64 CUDA tensor P: returns (order, L21, swaps)
+    with order[i] the panel row at position i and L21 an (m - w) x w CUDA tensor."""
+    import torch
+    m, w = P.shape
+    ldp = _dev_matrix(P, "P")
+    L21 = torch.empty((max(m - w, 0), w), dtype=torch.float64, device=P.device)
+    order = np.empty(m, dtype=np.int32)
+    sw = C.c_int(0)
+    st = _lib.prrp_panel_select(ctx.handle, m, w, C.c_void_p(P.data_ptr()), ldp, float(tau),
+                                int(max_swaps), order.ctypes.data_as(C.c_void_p),
+                                C.c_void_p(L21.data_ptr() if L21.numel() else 0), C.byref(sw),
+                                _stream_ptr(stream))
+    _check(st, "prrp_panel_select", ctx.handle)
+    return order, L21, sw.value
+
+
+def prrp_schur_update(ctx: Context, L, U, Cm, prec=PRRP_FP64, stream=None) -> None:
+    """Cm -= L @ U on float64 CUDA tensors (k = L.shape[1] <= 128)."""
+    m, k = L.shape
+    n = U.shape[1]
+    st = _lib.prrp_schur_update(ctx.handle, m, n, k, C.c_void_p(L.data_ptr()), _dev_matrix(L, "L"),
+                                C.c_void_p(U.data_ptr()), _dev_matrix(U, "U"),
+                                C.c_void_p(Cm.data_ptr()), _dev_matrix(Cm, "C"), int(prec),
+                                _stream_ptr(stream))
+    _check(st, "prrp_schur_update", ctx.handle)
+
+
+def prrp_selftest_wait(ctx: Context, spin_limit: int = 20000, stream=None) -> int:
+    """Run the bounded-wait self-test; returns the status (PRRP_ERR_TIMEOUT expected)."""
+    return _lib.prrp_selftest_wait(ctx.handle, int(spin_limit), _stream_ptr(stream))
+
+
+KINDS = ["scan", "panel", "permute", "update", "diag", "u12", "lfix", "solve"]
+
+
+def prrp_ctx_set_timing(ctx: Context, enable: bool = True) -> None:
+    _check(_lib.prrp_ctx_set_timing(ctx.handle, int(bool(enable))), "prrp_ctx_set_timing")
+
+
+def prrp_ctx_kernel_stats(ctx: Context, reset: bool = False) -> dict:
+    """Per kernel class: {"ms", "launches", "flops"} since the last reset."""
+    ms = (C.c_double * len(KINDS))()
+    ln = (C.c_longlong * len(KINDS))()
+    fl = (C.c_longlong * len(KINDS))()
+    _check(_lib.prrp_ctx_kernel_stats(ctx.handle, ms, ln, fl, int(bool(reset))),
+           "prrp_ctx_kernel_stats")
+    return {k: {"ms": ms[i], "launches": ln[i], "flops": fl[i]} for i, k in enumerate(KINDS)}

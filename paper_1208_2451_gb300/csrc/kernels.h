@@ -1,0 +1,78 @@
+// Host-side launchers of the LU_PRRP kernels (internal to libprrp.so).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace prrp {
+
+struct PanelParams {
+  const double* P;        // m x w panel, row-major
+  long long ldp;
+  int m, w;
+  double tau;
+  int max_swaps;
+  int col_offset;         // global column of the panel's first column (for info)
+  double* L21;            // (m - w) x w output, row-major
+  int ldl;
+  int* order;             // m ints (final position -> panel row) or nullptr
+  int* pairs;             // (dst, src) row moves, 2 ints each, or nullptr
+  DevState* st;
+  double* xval;           // exchange records: [2][G]
+  int2* xkey;             // [2][G]
+  double* xvec;           // [2][G][kMaxW]
+  int rows_per_cta;
+};
+
+int panel_width_class(int w);
+size_t panel_smem_for(int w, int rows_per_cta);
+cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t stream);
+
+// max |a_ij| and non-finite detection over an n x n row-major matrix.
+cudaError_t launch_scan(const double* A, long long lda, int n, DevState* st, cudaStream_t s);
+
+// Row moves for rows k0.. of A (all n columns) and perm: A[k0+dst] = A_old[k0+src].
+cudaError_t launch_permute(double* A, long long lda, int n, int k0, const int* pairs,
+                           int max_pairs, int* perm, DevState* st, cudaStream_t s);
+
+// C -= L * U in FP64 (DFMA), C m x n, L m x k, U k x n, k <= kMaxW; tracks max |C| into
+// st->gmax_bits when track != 0.
+cudaError_t launch_gemm_fp64(int m, int n, int k, const double* L, long long ldl,
+                             const double* U, long long ldu, double* C, long long ldc,
+                             DevState* st, int track, int num_sms, cudaStream_t s);
+
+// GEPP on the w x w diagonal block at A[k0][k0]; in-block pivots to ipiv, perm updated,
+// max |U11| tracked.
+cudaError_t launch_diag_gepp(double* A, long long lda, int k0, int w, int* ipiv, int* perm,
+                             DevState* st, cudaStream_t s);
+
+// Block rows k0..k0+w-1: apply ipiv to columns [0, k0) and [k0+w, n); U12 = L11^-1 A12.
+cudaError_t launch_u12(double* A, long long lda, int n, int k0, int w, const int* ipiv,
+                       DevState* st, cudaStream_t s);
+
+// Rows k0+w..n-1: A[r][k0:k0+w] = (L21buf[r] with columns interchanged by ipiv) * L11.
+cudaError_t launch_lfix(double* A, long long lda, int n, int k0, int w, const double* L21,
+                        int ldl21, const int* ipiv, DevState* st, cudaStream_t s);
+
+cudaError_t launch_iota(int* p, int n, cudaStream_t s);
+cudaError_t launch_wait_selftest(DevState* st, cudaStream_t s);
+
+// Solve kernels (solve.cu).
+cudaError_t launch_norm1(const double* A, long long lda, int n, double* out, cudaStream_t s);
+cudaError_t launch_gather_rows(const double* B, long long ldb, const int* perm, int n, int nrhs,
+                               double* Y, cudaStream_t s);
+cudaError_t launch_trsv_lower_unit(const double* LU, long long lda, int n, double* Y, int nrhs,
+                                   cudaStream_t s);
+cudaError_t launch_trsv_upper(const double* LU, long long lda, int n, double* Y, int nrhs,
+                              cudaStream_t s);
+cudaError_t launch_residual(const double* A, long long lda, int n, const double* X, long long ldx,
+                            int nrhs, const double* B, long long ldb, double* R, double* norms,
+                            cudaStream_t s);
+cudaError_t launch_axpy_rows(double* X, long long ldx, const double* D, double alpha, int n,
+                             int nrhs, cudaStream_t s);
+cudaError_t launch_copy_rows(const double* src, long long lds, double* dst, long long ldd, int n,
+                             int ncols, cudaStream_t s);
+
+}  // namespace prrp

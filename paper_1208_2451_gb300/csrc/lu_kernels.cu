@@ -1,0 +1,449 @@
+// LU_PRRP kernels after the panel (Algorithm 1, lines 5-11), plain FP64.
+//
+//  scan       max |a_ij| of the input (denominator of g_W, Section 2.2) and NaN/Inf check.
+//  permute    Pi_j^T applied to whole rows (line 5): the (destination, source) row moves of
+//             the panel are staged through shared memory one column slice per CTA, so all
+//             reads of a slice finish before its writes and no grid-wide sync is needed.
+//  gemm_fp64  A22 -= L21 A12 (eq. "update", line 7) on the FP64 FMA pipe; tracks max |A22|
+//             for the growth factor.
+//  diag_gepp  GEPP on the w x w diagonal block (line 10), one CTA.
+//  u12        block-row interchanges of GEPP across all other columns and
+//             U12 = L11^-1 Pi_jj^T A12 (line 11).
+//  lfix       the rows below the block get their final multipliers L21 Pi_jj L11, so the
+//             stored factors are the ordinary P A = L U.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace prrp {
+
+// ---------------------------------------------------------------- scan
+__global__ void __launch_bounds__(256) scan_kernel(const double* __restrict__ A, long long lda,
+                                                   int n, DevState* st) {
+  double mx = 0.0;
+  unsigned bad = 0;
+  for (long long row = blockIdx.x; row < n; row += gridDim.x) {
+    const double* a = A + row * lda;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const double v = a[c];
+      bad |= !isfinite(v);
+      mx = fmax(mx, fabs(v));
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&st->amax_bits, mx);
+    atomic_max_nonneg(&st->gmax_bits, mx);
+    if (bad) {
+      st->nonfinite = 1;
+      set_error(st, PRRP_ERR_NONFINITE);
+    }
+  }
+}
+
+cudaError_t launch_scan(const double* A, long long lda, int n, DevState* st, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = std::min(n, 152 * 8);
+  scan_kernel<<<grid, 256, 0, s>>>(A, lda, n, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- helpers
+__global__ void iota_kernel(int* p, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
+}
+
+cudaError_t launch_iota(int* p, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  iota_kernel<<<std::min((n + 255) / 256, 1024), 256, 0, s>>>(p, n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- permute
+constexpr int kPermCols = 32;
+
+__global__ void __launch_bounds__(256) permute_kernel(double* __restrict__ A, long long lda,
+                                                      int n, int k0, const int* __restrict__ pairs,
+                                                      int max_pairs, int* __restrict__ perm,
+                                                      DevState* st) {
+  if (dev_status(st) != 0) return;
+  extern __shared__ double buf[];                 // max_pairs x kPermCols
+  const int np = min((int)st->npairs, max_pairs);
+  if (np == 0) return;
+  const int c0 = blockIdx.x * kPermCols;
+  const int cw = min(kPermCols, n - c0);
+  for (int e = threadIdx.x; e < np * cw; e += blockDim.x) {
+    const int q = e / cw, c = e - q * cw;
+    buf[q * kPermCols + c] = A[(long long)(k0 + pairs[2 * q + 1]) * lda + c0 + c];
+  }
+  int* pbuf = reinterpret_cast<int*>(buf + (size_t)max_pairs * kPermCols);
+  if (blockIdx.x == 0)
+    for (int q = threadIdx.x; q < np; q += blockDim.x) pbuf[q] = perm[k0 + pairs[2 * q + 1]];
+  __syncthreads();
+  for (int e = threadIdx.x; e < np * cw; e += blockDim.x) {
+    const int q = e / cw, c = e - q * cw;
+    A[(long long)(k0 + pairs[2 * q]) * lda + c0 + c] = buf[q * kPermCols + c];
+  }
+  if (blockIdx.x == 0)
+    for (int q = threadIdx.x; q < np; q += blockDim.x) perm[k0 + pairs[2 * q]] = pbuf[q];
+}
+
+cudaError_t launch_permute(double* A, long long lda, int n, int k0, const int* pairs,
+                           int max_pairs, int* perm, DevState* st, cudaStream_t s) {
+  const size_t smem = (size_t)max_pairs * kPermCols * sizeof(double) + (size_t)max_pairs * sizeof(int);
+  cudaError_t e = cudaFuncSetAttribute(permute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (n + kPermCols - 1) / kPermCols;
+  permute_kernel<<<grid, 256, smem, s>>>(A, lda, n, k0, pairs, max_pairs, perm, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- FP64 Schur update
+// C -= L U with a BM x BN tile per CTA (persistent, strided tile loop), 256 threads each
+// owning a (BM/16) x (BN/16) register block.  The k dimension (<= 128) is staged through
+// shared memory in chunks of 64; operands are stored k-major so each thread's row and column
+// fragments are contiguous.  The FP64 pipe is the bound: a 128 x 128 x 64 tile is 1M DFMA
+// against 128 KB of operand traffic.
+constexpr int kGemmKC = 64;
+
+template <int BM, int BN>
+__global__ void __launch_bounds__(256, 1) gemm_fp64_kernel(int M, int N, int K,
+                                                           const double* __restrict__ L, long long ldl,
+                                                           const double* __restrict__ U, long long ldu,
+                                                           double* __restrict__ C, long long ldc,
+                                                           DevState* st, int track) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  constexpr int BMP = BM + 2;                      // padded k-major strides
+  constexpr int BNP = BN + 2;
+  extern __shared__ double sm[];
+  double* As = sm;                                 // [kGemmKC][BMP]
+  double* Bs = sm + kGemmKC * BMP;                 // [kGemmKC][BNP]
+  if (dev_status(st) != 0) return;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int tiles_n = (N + BN - 1) / BN;
+  const int tiles = ((M + BM - 1) / BM) * tiles_n;
+  double cmax = 0.0;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int bm = (tile / tiles_n) * BM, bn = (tile % tiles_n) * BN;
+    // warm L2 with this tile's C rows while the operands are staged
+    for (int r = tid; r < BM; r += 256)
+      if (bm + r < M)
+        for (int c = 0; c < BN && bn + c < N; c += 16)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (long long)(bm + r) * ldc + bn + c));
+    double acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < K; k0 += kGemmKC) {
+      const int kc = min(kGemmKC, K - k0);
+      __syncthreads();
+      for (int e = tid; e < BM * kGemmKC; e += 256) {
+        const int r = e / kGemmKC, k = e - r * kGemmKC;
+        double v = 0.0;
+        if (bm + r < M && k < kc) v = L[(long long)(bm + r) * ldl + k0 + k];
+        As[k * BMP + r] = v;
+      }
+      for (int e = tid; e < kGemmKC * BN; e += 256) {
+        const int k = e / BN, c = e - k * BN;
+        double v = 0.0;
+        if (bn + c < N && k < kc) v = U[(long long)(k0 + k) * ldu + bn + c];
+        Bs[k * BNP + c] = v;
+      }
+      __syncthreads();
+#pragma unroll 2
+      for (int k = 0; k < kc; ++k) {
+        double a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = As[k * BMP + ty * TM + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = Bs[k * BNP + tx * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int r = bm + ty * TM + i;
+      if (r >= M) continue;
+      double* crow = C + (long long)r * ldc + bn + tx * TN;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        if (bn + tx * TN + j < N) {
+          const double v = crow[j] - acc[i][j];
+          crow[j] = v;
+          cmax = fmax(cmax, fabs(v));
+        }
+      }
+    }
+  }
+  if (track) {
+    for (int off = 16; off > 0; off >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
+    if ((tid & 31) == 0) atomic_max_nonneg(&st->gmax_bits, cmax);
+  }
+}
+
+template <int BM, int BN>
+static cudaError_t launch_gemm_tile(int m, int n, int k, const double* L, long long ldl,
+                                    const double* U, long long ldu, double* C, long long ldc,
+                                    DevState* st, int track, int grid, cudaStream_t s) {
+  const size_t smem = (size_t)kGemmKC * ((BM + 2) + (BN + 2)) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(gemm_fp64_kernel<BM, BN>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  gemm_fp64_kernel<BM, BN><<<grid, 256, smem, s>>>(m, n, k, L, ldl, U, ldu, C, ldc, st, track);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_fp64(int m, int n, int k, const double* L, long long ldl,
+                             const double* U, long long ldu, double* C, long long ldc,
+                             DevState* st, int track, int num_sms, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+  // pick the tile whose wave count wastes least: cost ~ ceil(tiles / sms) * tile area
+  const long long t128 = (long long)((m + 127) / 128) * ((n + 127) / 128);
+  const long long t64 = (long long)((m + 63) / 64) * ((n + 63) / 64);
+  const long long waves128 = (t128 + num_sms - 1) / num_sms;
+  const long long waves64 = (t64 + 2 * num_sms - 1) / (2 * num_sms);   // two 64x64 CTAs per SM
+  if (waves128 * 4 <= waves64 * 1 + 1 && t128 >= num_sms / 2)
+    return launch_gemm_tile<128, 128>(m, n, k, L, ldl, U, ldu, C, ldc, st, track,
+                                      (int)std::min<long long>(t128, num_sms), s);
+  return launch_gemm_tile<64, 64>(m, n, k, L, ldl, U, ldu, C, ldc, st, track,
+                                  (int)std::min<long long>(t64, 2LL * num_sms), s);
+}
+
+// ---------------------------------------------------------------- diagonal GEPP
+__global__ void __launch_bounds__(256) diag_gepp_kernel(double* __restrict__ A, long long lda,
+                                                        int k0, int w, int* __restrict__ ipiv,
+                                                        int* __restrict__ perm, DevState* st) {
+  if (dev_status(st) != 0) return;
+  extern __shared__ double D[];                    // w x (w + 1)
+  const int WP = w + 1;
+  __shared__ int s_p;
+  __shared__ double s_v;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < w * w; e += blockDim.x) {
+    const int i = e / w, j = e - i * w;
+    D[i * WP + j] = A[(long long)(k0 + i) * lda + k0 + j];
+  }
+  __syncthreads();
+  for (int t = 0; t < w; ++t) {
+    if (warp == 0) {
+      double bv = -1.0;
+      int bi = 0x7fffffff;
+      for (int i = t + lane; i < w; i += 32) {
+        const double v = fabs(D[i * WP + t]);
+        if (v > bv) { bv = v; bi = i; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) { s_p = bi; s_v = bv; }
+    }
+    __syncthreads();
+    if (!(s_v > 0.0)) {
+      if (tid == 0) set_error(st, PRRP_ERR_SINGULAR, k0 + t + 1);
+      return;
+    }
+    const int p = s_p;
+    if (tid == 0) ipiv[t] = p;
+    if (p != t)
+      for (int j = tid; j < w; j += blockDim.x) {
+        const double x = D[t * WP + j];
+        D[t * WP + j] = D[p * WP + j];
+        D[p * WP + j] = x;
+      }
+    __syncthreads();
+    const double piv = D[t * WP + t];
+    for (int i = t + 1 + tid; i < w; i += blockDim.x) D[i * WP + t] /= piv;
+    __syncthreads();
+    const int rem = w - t - 1;
+    for (int e = tid; e < rem * rem; e += blockDim.x) {
+      const int i = t + 1 + e / rem, j = t + 1 + e % rem;
+      D[i * WP + j] = fma(-D[i * WP + t], D[t * WP + j], D[i * WP + j]);
+    }
+    __syncthreads();
+  }
+  double umax = 0.0;
+  for (int e = tid; e < w * w; e += blockDim.x) {
+    const int i = e / w, j = e - i * w;
+    const double v = D[i * WP + j];
+    A[(long long)(k0 + i) * lda + k0 + j] = v;
+    if (j >= i) umax = fmax(umax, fabs(v));
+  }
+  for (int off = 16; off > 0; off >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, off));
+  if (lane == 0) atomic_max_nonneg(&st->umax_bits, umax);
+  if (tid == 0)
+    for (int t = 0; t < w; ++t) {
+      const int p = ipiv[t];
+      if (p != t) {
+        const int x = perm[k0 + t];
+        perm[k0 + t] = perm[k0 + p];
+        perm[k0 + p] = x;
+      }
+    }
+}
+
+cudaError_t launch_diag_gepp(double* A, long long lda, int k0, int w, int* ipiv, int* perm,
+                             DevState* st, cudaStream_t s) {
+  const size_t smem = (size_t)w * (w + 1) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(diag_gepp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  diag_gepp_kernel<<<1, 256, smem, s>>>(A, lda, k0, w, ipiv, perm, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- U12 and block-row swaps
+constexpr int kU12Cols = 32;
+
+__global__ void __launch_bounds__(kU12Cols) u12_kernel(double* __restrict__ A, long long lda, int n,
+                                                       int k0, int w, const int* __restrict__ ipiv,
+                                                       int left_slices, DevState* st) {
+  if (dev_status(st) != 0) return;
+  extern __shared__ double sh[];
+  double* Ls = sh;                                  // w x w (L11, unit lower)
+  double* X = sh + w * w;                           // w x kU12Cols
+  __shared__ int piv[kMaxW];
+  const int tid = threadIdx.x;
+  const bool right = blockIdx.x >= left_slices;
+  const int c0 = right ? k0 + w + (blockIdx.x - left_slices) * kU12Cols : blockIdx.x * kU12Cols;
+  const int cend = right ? n : k0;
+  const int cw = min(kU12Cols, cend - c0);
+  for (int t = tid; t < w; t += blockDim.x) piv[t] = ipiv[t];
+  if (right)
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int i = e / w, j = e - i * w;
+      Ls[e] = (j < i) ? A[(long long)(k0 + i) * lda + k0 + j] : 0.0;
+    }
+  for (int i = 0; i < w; ++i)
+    if (tid < cw) X[i * kU12Cols + tid] = A[(long long)(k0 + i) * lda + c0 + tid];
+  __syncthreads();
+  if (tid < cw) {
+    double* x = X + tid;
+    for (int t = 0; t < w; ++t) {
+      const int p = piv[t];
+      if (p != t) {
+        const double v = x[t * kU12Cols];
+        x[t * kU12Cols] = x[p * kU12Cols];
+        x[p * kU12Cols] = v;
+      }
+    }
+    if (right)
+      for (int k = 0; k < w; ++k) {
+        const double xk = x[k * kU12Cols];
+        for (int i = k + 1; i < w; ++i) x[i * kU12Cols] = fma(-Ls[i * w + k], xk, x[i * kU12Cols]);
+      }
+  }
+  __syncthreads();
+  double umax = 0.0;
+  for (int i = 0; i < w; ++i)
+    if (tid < cw) {
+      const double v = X[i * kU12Cols + tid];
+      A[(long long)(k0 + i) * lda + c0 + tid] = v;
+      umax = fmax(umax, fabs(v));
+    }
+  if (right) {
+    for (int off = 16; off > 0; off >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, off));
+    if (tid == 0) atomic_max_nonneg(&st->umax_bits, umax);
+  }
+}
+
+cudaError_t launch_u12(double* A, long long lda, int n, int k0, int w, const int* ipiv,
+                       DevState* st, cudaStream_t s) {
+  const int left = (k0 + kU12Cols - 1) / kU12Cols;
+  const int right = (n - k0 - w + kU12Cols - 1) / kU12Cols;
+  if (left + right == 0) return cudaSuccess;
+  const size_t smem = (size_t)(w * w + w * kU12Cols) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(u12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  u12_kernel<<<left + right, kU12Cols, smem, s>>>(A, lda, n, k0, w, ipiv, left, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- final L below the block
+constexpr int kLfixRows = 32;
+
+__global__ void __launch_bounds__(kLfixRows) lfix_kernel(double* __restrict__ A, long long lda, int n,
+                                                         int k0, int w, const double* __restrict__ L21,
+                                                         int ldl21, const int* __restrict__ ipiv,
+                                                         DevState* st) {
+  if (dev_status(st) != 0) return;
+  extern __shared__ double sh[];
+  double* Ls = sh;                       // w x w unit lower L11
+  double* X = sh + w * w;                // kLfixRows x (w + 1)
+  __shared__ int piv[kMaxW];
+  const int WP = w + 1;
+  const int tid = threadIdx.x;
+  const int rbase = blockIdx.x * kLfixRows;
+  const int rows = min(kLfixRows, n - k0 - w - rbase);
+  for (int t = tid; t < w; t += blockDim.x) piv[t] = ipiv[t];
+  for (int e = tid; e < w * w; e += blockDim.x) {
+    const int i = e / w, j = e - i * w;
+    Ls[e] = (j < i) ? A[(long long)(k0 + i) * lda + k0 + j] : (i == j ? 1.0 : 0.0);
+  }
+  for (int e = tid; e < rows * w; e += blockDim.x) {
+    const int r = e / w, j = e - r * w;
+    X[r * WP + j] = L21[(long long)(rbase + r) * ldl21 + j];
+  }
+  __syncthreads();
+  if (tid < rows) {
+    double* x = X + tid * WP;
+    for (int t = 0; t < w; ++t) {
+      const int p = piv[t];
+      if (p != t) { const double v = x[t]; x[t] = x[p]; x[p] = v; }
+    }
+    // x <- x * L11, in place from the left column: out_c = x_c + sum_{i > c} x_i L11(i, c)
+    for (int c = 0; c < w; ++c) {
+      double acc = x[c];
+      for (int i = c + 1; i < w; ++i) acc = fma(x[i], Ls[i * w + c], acc);
+      x[c] = acc;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < rows * w; e += blockDim.x) {
+    const int r = e / w, j = e - r * w;
+    A[(long long)(k0 + w + rbase + r) * lda + k0 + j] = X[r * WP + j];
+  }
+}
+
+cudaError_t launch_lfix(double* A, long long lda, int n, int k0, int w, const double* L21,
+                        int ldl21, const int* ipiv, DevState* st, cudaStream_t s) {
+  const int rows = n - k0 - w;
+  if (rows <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(w * w + kLfixRows * (w + 1)) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(lfix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  lfix_kernel<<<(rows + kLfixRows - 1) / kLfixRows, kLfixRows, smem, s>>>(A, lda, n, k0, w, L21,
+                                                                          ldl21, ipiv, st);
+  return cudaGetLastError();
+}
+
+}  // namespace prrp
+
+namespace prrp {
+
+// Self-test of the bounded wait: CTA 0 waits at a grid barrier that CTA 1 never reaches,
+// so the wait must run out after st->spin_limit polls and record PRRP_ERR_TIMEOUT.
+__global__ void wait_selftest_kernel(DevState* st) {
+  if (blockIdx.x == 1) return;            // never arrives
+  grid_barrier(st, gridDim.x, 99);
+}
+
+cudaError_t launch_wait_selftest(DevState* st, cudaStream_t s) {
+  void* args[] = {&st};
+  return cudaLaunchCooperativeKernel((const void*)wait_selftest_kernel, dim3(2), dim3(32), args, 0, s);
+}
+
+}  // namespace prrp

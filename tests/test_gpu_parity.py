@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA LU_PRRP path (through the C ABI) against the CPU oracle.
+
+Bar (the benchmark spec's tolerances):
+* pivots: the permutation is identical whenever the oracle's smallest decision margin
+  (QRCP top-two gap, swap-test distance to tau, swap-choice gap, GEPP gap) exceeds 1e-8;
+  otherwise the GPU's own pivots must be a valid LU_PRRP selection, checked in FP64 on the
+  oracle side (every panel's block multipliers |L21| <= tau);
+* backward error of the GPU factors ||PA - LU||_F / ||A||_F <= 64 n 2^-53;
+* factors element by element: both sides run the same operations in different summation
+  orders, so each entry differs by rounding propagated through the elimination.  Bounded
+  by 64 n eps times the largest entry of the factor it belongs to (L or U).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import prrp_inputs as pi
+from oracle import metrics as M
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def prrp():
+    import paper_1208_2451_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(prrp):
+    c = prrp.prrp_create(0)
+    yield c
+    c.close()
+
+
+def gpu_factor(prrp, ctx, A, b, tau=2.0, max_swaps=64):
+    dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    F = prrp.prrp_factor(ctx, dA, b=b, tau=tau, max_swaps=max_swaps)
+    torch.cuda.synchronize()
+    out = dA.cpu().numpy(), F.perm().astype(np.int64), F.stats()
+    F.close()
+    return out
+
+
+def check_parity(prrp, ctx, A, b, tau=2.0, ref=None):
+    n = A.shape[0]
+    ref = ref if ref is not None else oracle.lu_prrp(A, b=b, tau=tau)
+    LU, perm, st = gpu_factor(prrp, ctx, A, b, tau)
+    assert sorted(perm) == list(range(n))
+    res = M.factor_residual(A, LU, perm) if n else 0.0
+    assert res <= 64 * max(n, 1) * EPS, res
+    if ref.min_margin > 1e-8:
+        assert np.array_equal(perm, ref.perm), "pivot sequence differs with untied decisions"
+        Lg, Lo = np.tril(LU, -1), np.tril(ref.LU, -1)
+        Ug, Uo = np.triu(LU), np.triu(ref.LU)
+        tol = 64 * max(n, 1) * EPS
+        assert np.max(np.abs(Lg - Lo), initial=0) <= tol * max(1.0, np.max(np.abs(Lo), initial=0))
+        assert np.max(np.abs(Ug - Uo), initial=0) <= tol * max(1.0, np.max(np.abs(Uo), initial=0))
+        assert st["swaps"] == ref.swaps
+        assert st["growth"] == pytest.approx(ref.growth, rel=1e-9)
+        assert st["growth_u"] == pytest.approx(ref.growth_u, rel=1e-9)
+        assert st["max_l21"] == pytest.approx(ref.max_L21, rel=1e-9, abs=1e-300)
+    else:
+        mx = oracle.selection_multipliers(A, perm, b)
+        assert max(mx, default=0.0) <= tau * (1 + 1e-10), "GPU pivots are not a valid selection"
+    assert st["max_l21"] <= tau * (1 + 1e-12)
+    assert st["growth"] <= M.growth_bound(n, b, tau) if n else True
+    return ref, LU, perm, st
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_small_case_n256_b16(prrp, ctx, seed):
+    """The small configuration: n = 256, b = 16, tau = 2, A iid N(0,1)."""
+    check_parity(prrp, ctx, pi.randn(256, seed), 16)
+
+
+@pytest.mark.parametrize("n,b", [(300, 16), (129, 64), (50, 64), (64, 64), (1, 1), (2, 1), (7, 3),
+                                 (1000, 64), (513, 32), (200, 128), (77, 8), (640, 128), (33, 1)])
+def test_ragged_sizes(prrp, ctx, n, b):
+    check_parity(prrp, ctx, pi.randn(n, 1000 + n), b)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_swap_path(prrp, ctx, seed):
+    """tau close to 1 makes the strong RRQR interchanges fire on random panels."""
+    A = pi.randn(256, 50 + seed)
+    ref, _, _, st = check_parity(prrp, ctx, A, 16, tau=1.05)
+    assert ref.swaps > 0 or ref.min_margin <= 1e-8
+
+
+def test_empty(prrp, ctx):
+    A = torch.empty((0, 0), dtype=torch.float64, device="cuda")
+    F = prrp.prrp_factor(ctx, A, b=16)
+    assert F.stats()["growth"] == 1.0
+
+
+@pytest.mark.parametrize("m,w,tau", [(8192, 64, 2.0), (8192, 64, 1.05), (1000, 16, 1.05),
+                                     (64, 64, 2.0), (65, 64, 2.0), (3000, 128, 2.0), (17, 5, 1.01)])
+def test_panel_select(prrp, ctx, m, w, tau):
+    """Rows a1-a3: strong RRQR of one tall panel, element by element against Algorithm 2."""
+    P = pi.randn(w, 7 + m, m=m)
+    ref = oracle.strong_rrqr(P.T, tau=tau, max_swaps=64)
+    order, L21, swaps = prrp.prrp_panel_select(ctx, torch.from_numpy(P).cuda(), tau=tau)
+    margins = ref.qrcp_margins + ref.test_margins + ref.choice_margins
+    if min(margins, default=np.inf) > 1e-8:
+        assert list(order) == list(ref.order)
+        assert swaps == ref.swaps
+        np.testing.assert_allclose(L21.cpu().numpy(), ref.M.T, atol=1e-10, rtol=1e-9)
+    S = order[:w]
+    Lx = np.linalg.solve(P[S].T, P[order[w:]].T).T if m > w else np.zeros((0, w))
+    np.testing.assert_allclose(L21.cpu().numpy(), Lx, atol=1e-9, rtol=1e-8)
+    assert np.max(np.abs(Lx), initial=0) <= tau * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("m,n,k", [(8128, 8128, 64), (1000, 777, 64), (129, 65, 1), (300, 2000, 128),
+                                   (64, 64, 100), (1, 1, 16), (5000, 31, 16)])
+def test_schur_update(prrp, ctx, m, n, k):
+    """Row a5 alone: C -= L U in FP64 against numpy's matmul."""
+    g = pi.rng(m * 7 + n)
+    L, U, Cm = g.standard_normal((m, k)), g.standard_normal((k, n)), g.standard_normal((m, n))
+    dC = torch.from_numpy(Cm).cuda()
+    prrp.prrp_schur_update(ctx, torch.from_numpy(L).cuda(), torch.from_numpy(U).cuda(), dC)
+    want = Cm - L @ U
+    err = np.max(np.abs(dC.cpu().numpy() - want))
+    assert err <= 4 * k * EPS * np.max(np.abs(L)) * np.max(np.abs(U)) + 4 * EPS * np.max(np.abs(Cm))
+
+
+@pytest.mark.parametrize("b", [16, 64])
+def test_wilkinson_2048(prrp, ctx, b):
+    """GEPP grows as 2^2047 on this matrix; LU_PRRP factors it stably."""
+    A = pi.wilkinson(2048)
+    _, LU, perm, st = check_parity(prrp, ctx, A, b)
+    assert st["growth"] < 10
+
+
+def test_foster_and_wright_2048(prrp, ctx):
+    """Tables tab_foster and tab_wright: g_W = 2.66 and 1 (rows exactly tied: validity path)."""
+    _, _, _, st = check_parity(prrp, ctx, pi.foster(2048), 64)
+    assert abs(st["growth"] - 2.66) <= 0.01
+    _, _, _, st = check_parity(prrp, ctx, pi.wright(2048, 0.3), 64)
+    assert abs(st["growth"] - 1.0) <= 0.01
+
+
+def test_full_size_n8192_b64(prrp, ctx):
+    """The benchmark configuration (n = 8192, b = 64, tau = 2): whole factorization against
+    the oracle, in the same launch configuration bench.py times."""
+    A = pi.randn(8192, 0)
+    ref = oracle.lu_prrp(A, b=64, tau=2.0)
+    check_parity(prrp, ctx, A, 64, ref=ref)
+
+
+def test_solve_and_refine(prrp, ctx):
+    n = 1000
+    A = pi.randn(n, 3)
+    B = pi.rhs(n, 4, 3)
+    dA = torch.from_numpy(A).cuda()
+    F = prrp.prrp_factor(ctx, dA, b=64)
+    dB = torch.from_numpy(B).cuda()
+    info = prrp.prrp_solve(ctx, F, dB, A_orig=torch.from_numpy(A).cuda())
+    X = dB.cpu().numpy()
+    ref = oracle.lu_prrp(A, b=64)
+    Xo = oracle.lu_solve(ref.LU, ref.perm, B)
+    np.testing.assert_allclose(X, Xo, rtol=1e-10, atol=1e-11)
+    assert info["eta"] <= 1e-15
+    for c in range(4):
+        assert M.eta(A, X[:, c], B[:, c]) <= 1e-15
+    # without refinement: plain substitution
+    dB2 = torch.from_numpy(B).cuda()
+    info2 = prrp.prrp_solve(ctx, F, dB2)
+    np.testing.assert_allclose(dB2.cpu().numpy(), Xo, rtol=1e-10, atol=1e-11)
+    assert info2["eta"] == -1.0
+
+
+def test_gesv_host(prrp, ctx):
+    n = 700
+    A = pi.randn(n, 8)
+    B = pi.rhs(n, 2, 8)
+    X, stats, info = prrp.prrp_gesv_host(ctx, A, B, b=64, refine_max_iter=5)
+    np.testing.assert_allclose(X, np.linalg.solve(A, B), rtol=1e-9, atol=1e-10)
+    assert info["eta"] <= 1e-15
+
+
+def test_errors(prrp, ctx):
+    A = pi.randn(64, 1)
+    A[5, 9] = np.nan
+    dA = torch.from_numpy(A).cuda()
+    with pytest.raises(prrp.PrrpError) as e:
+        prrp.prrp_factor(ctx, dA, b=16)
+    assert e.value.name == "PRRP_ERR_NONFINITE"
+    assert np.array_equal(np.isnan(dA.cpu().numpy()), np.isnan(A))
+    assert np.array_equal(dA.cpu().numpy()[~np.isnan(A)], A[~np.isnan(A)]), "input written"
+    S = pi.randn(40, 2)
+    S[:, 8:16] = 0.0
+    F = prrp.prrp_factor(ctx, torch.from_numpy(S).cuda(), b=8, allow=(prrp.binding.PRRP_ERR_SINGULAR,))
+    assert F.status == prrp.binding.PRRP_ERR_SINGULAR and F.stats()["info"] == 9
+    F.close()
+    for kw in ({"b": 0}, {"b": 129}, {"tau": 0.5}, {"max_swaps": -1}):
+        with pytest.raises(prrp.PrrpError) as e:
+            prrp.prrp_factor(ctx, torch.from_numpy(pi.randn(8, 0)).cuda(), **kw)
+        assert e.value.name == "PRRP_ERR_INVALID_ARG"
+    # a case that needs interchanges fails cleanly when none are allowed
+    A = pi.randn(256, 50)
+    need = oracle.lu_prrp(A, b=16, tau=1.05).swaps
+    assert need > 0
+    with pytest.raises(prrp.PrrpError) as e:
+        prrp.prrp_factor(ctx, torch.from_numpy(A).cuda(), b=16, tau=1.05, max_swaps=0)
+    assert e.value.name == "PRRP_ERR_SWAP_LIMIT"
+    # the context stays usable after every error
+    check_parity(prrp, ctx, pi.randn(100, 5), 16)
+
+
+def test_bounded_wait_times_out(prrp, ctx):
+    """A grid barrier that one CTA never reaches gives up and reports PRRP_ERR_TIMEOUT; the
+    context then still factors correctly."""
+    assert prrp.prrp_selftest_wait(ctx, 20000) == prrp.binding.PRRP_ERR_TIMEOUT
+    check_parity(prrp, ctx, pi.randn(128, 9), 16)

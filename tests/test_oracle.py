@@ -297,3 +297,16 @@ def test_max_panels_prefix():
     part = oracle.lu_prrp(A, b=16, max_panels=3)
     assert part.panels == 3
     assert part.panel_transpositions == full.panel_transpositions[:3]
+
+
+def test_selection_multipliers_validator():
+    """The pivot validator used when a decision is a near-tie: on the oracle's own pivots it
+    returns the oracle's block multipliers (<= tau); on a pivot sequence that keeps the
+    natural order of a matrix needing pivoting it reports multipliers far above tau."""
+    A = pi.randn(200, 11)
+    r = oracle.lu_prrp(A, b=16, tau=2.0)
+    mx = oracle.selection_multipliers(A, r.perm, 16)
+    assert max(mx) == pytest.approx(r.max_L21, rel=1e-9)
+    assert max(mx) <= 2.0
+    bad = np.arange(200)
+    assert max(oracle.selection_multipliers(A, bad, 16)) > 2.0
