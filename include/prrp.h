@@ -204,6 +204,36 @@ prrp_status prrp_ctx_kernel_stats(prrp_ctx* ctx, double* ms, long long* launches
                                   long long* flops, int reset);
 
 /*
+ * prrp_panel_select_noalloc - prrp_panel_select for callers that cannot allocate device
+ * memory.  The paper has no counterpart: it is a deployment variant of the same panel
+ * kernel (same grid rule, same arithmetic, same outputs).
+ *
+ * Who needs it: code that runs inside a device-memory arena owned by another allocator,
+ * where a side allocation can fail or fragment the arena; loops whose latency budget
+ * cannot absorb the device synchronization cudaMalloc/cudaFree may imply; and code that
+ * must not create a prrp_ctx (its workspace is allocated).  This call takes no context
+ * and calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Scratch: the kernel's device state word and cross-CTA exchange records live in one
+ * library-wide static device array of 333,056 bytes, which every GPU that loads libprrp.so
+ * holds until the process exits.  The first call on a device (the current device at the
+ * time of the call) looks up that array's device address; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's contents (the
+ * state word is cleared at the start of each call): calls that overlap on the GPU, from
+ * any stream or thread, race and must not be issued.
+ *
+ * Limits: the exchange records hold at most 160 CTAs (the grid is min(#SMs, 160,
+ * ceil(m/32)) CTAs); a panel whose rows then exceed one CTA's shared memory returns
+ * PRRP_ERR_UNSUPPORTED.  Arguments as prrp_panel_select, except dOrder (m ints, DEVICE,
+ * caller-owned) receives the order; hSwaps (host, may be NULL) the interchange count.
+ * The call synchronizes `stream` and returns the kernel's status (SINGULAR, SWAP_LIMIT,
+ * TIMEOUT) or INVALID_ARG / UNSUPPORTED / CUDA.
+ */
+prrp_status prrp_panel_select_noalloc(int m, int w, const double* dP, int ldp, double tau,
+                                      int max_swaps, int* dOrder, double* dL21, int* hSwaps,
+                                      void* stream);
+
+/*
  * prrp_selftest_wait - check of the failure path of the device-side bounded waits (no
  * counterpart in the paper): launches a two-CTA cooperative grid in which one CTA waits at
  * a grid barrier that the other never reaches.  The wait gives up after `spin_limit` polls

@@ -63,6 +63,7 @@ _SIGS = {
     "prrp_panel_select": (_I, [_P, _I, _I, _P, _I, _D, _I, _P, _P, C.POINTER(_I), _P]),
     "prrp_schur_update": (_I, [_P, _I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _P]),
     "prrp_selftest_wait": (_I, [_P, C.c_uint, _P]),
+    "prrp_panel_select_noalloc": (_I, [_I, _I, _P, _I, _D, _I, _P, _P, C.POINTER(_I), _P]),
     "prrp_ctx_set_timing": (_I, [_P, _I]),
     "prrp_ctx_kernel_stats": (_I, [_P, _P, _P, _P, _I]),
 }
@@ -303,3 +304,21 @@ def prrp_ctx_kernel_stats(ctx: Context, reset: bool = False) -> dict:
     _check(_lib.prrp_ctx_kernel_stats(ctx.handle, ms, ln, fl, int(bool(reset))),
            "prrp_ctx_kernel_stats")
     return {k: {"ms": ms[i], "launches": ln[i], "flops": fl[i]} for i, k in enumerate(KINDS)}
+
+
+def prrp_panel_select_noalloc(P, tau=2.0, max_swaps=64, stream=None):
+    """prrp_panel_select without a context or any allocation inside the library (scratch in
+    a static device array).  The outputs are allocated here, by the caller side: returns
+    (order as a device int32 tensor, L21 device tensor, swaps)."""
+    import torch
+    m, w = P.shape
+    ldp = _dev_matrix(P, "P")
+    order = torch.empty(m, dtype=torch.int32, device=P.device)
+    L21 = torch.empty((max(m - w, 0), w), dtype=torch.float64, device=P.device)
+    sw = C.c_int(0)
+    st = _lib.prrp_panel_select_noalloc(m, w, C.c_void_p(P.data_ptr()), ldp, float(tau),
+                                        int(max_swaps), C.c_void_p(order.data_ptr()),
+                                        C.c_void_p(L21.data_ptr() if L21.numel() else 0),
+                                        C.byref(sw), _stream_ptr(stream))
+    _check(st, "prrp_panel_select_noalloc")
+    return order, L21, sw.value

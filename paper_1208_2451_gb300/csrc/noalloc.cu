@@ -1,0 +1,100 @@
+// prrp_panel_select_noalloc: the strong RRQR panel selection (the same kernel as
+// prrp_panel_select) for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs inside a fixed device-memory arena
+// owned by another allocator (a stray allocation there can fail or fragment it), loops
+// with latency budgets that cannot absorb the implicit device synchronization that
+// cudaMalloc and cudaFree may perform, and code that must not create a prrp_ctx (whose
+// workspace is allocated).  This entry point therefore needs no context and allocates
+// nothing: the kernel's scratch (the device state word and the cross-CTA exchange records
+// of the panel tournament) lives in the file-scope array below, which every GPU that loads
+// the library holds until the process exits.
+//
+// Host code must not pass the array's name to a kernel: on the host that name is only a
+// stand-in, not a device address.  The device address is looked up once per device with
+// cudaGetSymbolAddress, with that device current, on the first call made on it.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "prrp.h"
+
+namespace prrp {
+namespace {
+
+constexpr int kStaticMaxCtas = 160;   // panel CTAs the static exchange records can hold
+constexpr size_t kStateBytes = 256;   // DevState, padded
+constexpr size_t kValBytes = 2 * kStaticMaxCtas * sizeof(double);
+constexpr size_t kKeyBytes = 2 * kStaticMaxCtas * sizeof(int2);
+constexpr size_t kVecBytes = 2 * (size_t)kStaticMaxCtas * kMaxW * sizeof(double);
+constexpr size_t kScratchBytes = kStateBytes + kValBytes + kKeyBytes + kVecBytes;   // 333,056 B
+static_assert(sizeof(DevState) <= kStateBytes, "state word does not fit its slot");
+static_assert(kScratchBytes % 256 == 0, "scratch slots keep 256-byte alignment");
+
+static __device__ __align__(256) unsigned char g_panel_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Once per device, with that device current: the device address of the static scratch.
+cudaError_t scratch_address(int dev, unsigned char** out) {
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_panel_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace prrp
+
+using namespace prrp;
+
+extern "C" prrp_status prrp_panel_select_noalloc(int m, int w, const double* dP, int ldp,
+                                                 double tau, int max_swaps, int* dOrder,
+                                                 double* dL21, int* hSwaps, void* stream) {
+  if (w < 1 || w > kMaxW || m < w || ldp < w || !dP || !dOrder || !(tau >= 1.0) || max_swaps < 0)
+    return PRRP_ERR_INVALID_ARG;
+  if (m > w && !dL21) return PRRP_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0, smem = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PRRP_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return PRRP_ERR_CUDA;
+  // Same grid rule as prrp_panel_select, capped by the static exchange records.
+  const int G = std::max(1, std::min(std::min(sms, kStaticMaxCtas), (m + 31) / 32));
+  const int rpc = (m + G - 1) / G;
+  if (panel_smem_for(w, rpc) > (size_t)smem) return PRRP_ERR_UNSUPPORTED;
+  unsigned char* base = nullptr;
+  if (scratch_address(dev, &base) != cudaSuccess) return PRRP_ERR_CUDA;
+  DevState* st = reinterpret_cast<DevState*>(base);
+  // The array keeps the previous call's contents: clear the state word (error status,
+  // barrier arrivals, counters).  The exchange records need no clearing: each is written
+  // before it is read within a call.
+  if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return PRRP_ERR_CUDA;
+  PanelParams p{};
+  p.P = dP; p.ldp = ldp; p.m = m; p.w = w; p.tau = tau; p.max_swaps = max_swaps;
+  p.col_offset = 0; p.L21 = dL21; p.ldl = w; p.order = dOrder; p.pairs = nullptr;
+  p.st = st;
+  p.xval = reinterpret_cast<double*>(base + kStateBytes);
+  p.xkey = reinterpret_cast<int2*>(base + kStateBytes + kValBytes);
+  p.xvec = reinterpret_cast<double*>(base + kStateBytes + kValBytes + kKeyBytes);
+  p.rows_per_cta = rpc;
+  cudaError_t e = launch_panel(p, G, s);
+  if (e == cudaErrorCooperativeLaunchTooLarge) return PRRP_ERR_UNSUPPORTED;
+  if (e != cudaSuccess) return PRRP_ERR_CUDA;
+  DevState h{};
+  if (cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return PRRP_ERR_CUDA;
+  if (hSwaps) *hSwaps = h.panel_swaps;
+  return static_cast<prrp_status>(h.status);
+}
