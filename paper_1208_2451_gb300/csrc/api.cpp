@@ -44,6 +44,8 @@ struct prrp_ctx {
   size_t hA0_cap = 0;
   double* hB = nullptr;
   size_t hB_cap = 0;
+  unsigned char* tcws = nullptr;    // split operands of the tensor-core update
+  size_t tcws_cap = 0;
   std::string last_error;
   // optional per-kernel-class timing with CUDA events on the launching stream
   bool timing = false;
@@ -272,7 +274,7 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   void* ptrs[] = {ctx->st, ctx->xval, ctx->xkey, ctx->xvec, ctx->pairs, ctx->ipiv, ctx->order,
-                  ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB};
+                  ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB, ctx->tcws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -289,7 +291,7 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
   if (n < 0 || lda < std::max(n, 1) || (n > 0 && !dA)) return PRRP_ERR_INVALID_ARG;
   prrp_status ps = check_opts(&o);
   if (ps != PRRP_OK) return ps;
-  if (o.prec != PRRP_FP64) return PRRP_ERR_UNSUPPORTED;
+  if (o.prec == PRRP_FP32) return PRRP_ERR_UNSUPPORTED;
   if (n > 65536) return PRRP_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaSetDevice(ctx->device));
@@ -304,6 +306,9 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
 
   const int b = std::min(o.b, n);
   if ((ps = ensure_panel_ws(ctx, n, b, o.max_swaps)) != PRRP_OK) return fail(ps);
+  if (o.prec != PRRP_FP64 &&
+      (ps = grow(ctx, &ctx->tcws, &ctx->tcws_cap, tc_workspace_bytes(o.prec, n, n, b))) != PRRP_OK)
+    return fail(ps);
   {
     int G, rpc;   // the first panel is the tallest
     if ((ps = panel_grid(ctx, n, b, &G, &rpc)) != PRRP_OK) return fail(ps);
@@ -336,8 +341,12 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
     if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "permute"));
     if (m > w) {
       Timed t(ctx, s, PRRP_KIND_UPDATE, 2LL * (m - w) * (n - k0 - w) * w);
-      e = launch_gemm_fp64(m - w, n - k0 - w, w, ctx->l21, w, Akk + w, lda,
-                           Akk + (long long)w * lda + w, lda, ctx->st, 1, ctx->num_sms, s);
+      if (o.prec == PRRP_FP64)
+        e = launch_gemm_fp64(m - w, n - k0 - w, w, ctx->l21, w, Akk + w, lda,
+                             Akk + (long long)w * lda + w, lda, ctx->st, 1, ctx->num_sms, s);
+      else
+        e = launch_tc_update(o.prec, m - w, n - k0 - w, w, ctx->l21, w, Akk + w, lda,
+                             Akk + (long long)w * lda + w, lda, ctx->st, 1, ctx->tcws, s);
       if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "schur update"));
     }
     {
@@ -556,12 +565,24 @@ prrp_status prrp_schur_update(prrp_ctx* ctx, int m, int n, int k, const double* 
       ldc < std::max(n, 1))
     return PRRP_ERR_INVALID_ARG;
   if (m > 0 && n > 0 && (!dL || !dU || !dC)) return PRRP_ERR_INVALID_ARG;
-  if (prec != PRRP_FP64) return PRRP_ERR_UNSUPPORTED;
+  if (prec != PRRP_FP64 && prec != PRRP_TF32 && prec != PRRP_BF16X3) return PRRP_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaSetDevice(ctx->device));
   CK(cudaMemsetAsync(ctx->st, 0, sizeof(DevState), s));
-  CK(launch_gemm_fp64(m, n, k, dL, ldl, dU, ldu, dC, ldc, ctx->st, 0, ctx->num_sms, s));
-  return PRRP_OK;
+  if (prec == PRRP_FP64) {
+    Timed t(ctx, s, PRRP_KIND_UPDATE, 2LL * m * n * k);
+    CK(launch_gemm_fp64(m, n, k, dL, ldl, dU, ldu, dC, ldc, ctx->st, 0, ctx->num_sms, s));
+  } else {
+    prrp_status ps = grow(ctx, &ctx->tcws, &ctx->tcws_cap, tc_workspace_bytes(prec, m, n, k));
+    if (ps != PRRP_OK) return ps;
+    Timed t(ctx, s, PRRP_KIND_UPDATE, 2LL * m * n * k);
+    CK(launch_tc_update(prec, m, n, k, dL, ldl, dU, ldu, dC, ldc, ctx->st, 0, ctx->tcws, s));
+  }
+  DevState h{};
+  prrp_status ps = read_state(ctx, &h, s);
+  if (ps != PRRP_OK) return ps;
+  collect_timing(ctx);
+  return (prrp_status)h.status;
 }
 
 prrp_status prrp_ctx_set_timing(prrp_ctx* ctx, int enable) {

@@ -43,6 +43,13 @@ cudaError_t launch_gemm_fp64(int m, int n, int k, const double* L, long long ldl
                              const double* U, long long ldu, double* C, long long ldc,
                              DevState* st, int track, int num_sms, cudaStream_t s);
 
+// Same update on tcgen05 tensor cores, prec = PRRP_TF32 or PRRP_BF16X3 (FP32 accumulation,
+// FP64 C); ws holds the split operands (tc_workspace_bytes).
+size_t tc_workspace_bytes(int prec, int m, int n, int k);
+cudaError_t launch_tc_update(int prec, int m, int n, int k, const double* L, long long ldl,
+                             const double* U, long long ldu, double* C, long long ldc, DevState* st,
+                             int track, void* ws, cudaStream_t s);
+
 // GEPP on the w x w diagonal block at A[k0][k0]; in-block pivots to ipiv, perm updated,
 // max |U11| tracked.
 cudaError_t launch_diag_gepp(double* A, long long lda, int k0, int w, int* ipiv, int* perm,

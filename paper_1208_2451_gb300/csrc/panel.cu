@@ -8,13 +8,16 @@
 // QR with column pivoting, step t:
 //   * every CTA proposes its row of largest remaining squared norm ||B(t:w, q)||^2 (ties to
 //     the smallest position) together with that row's values;
-//   * one grid barrier; every CTA reduces the G proposals identically (a tournament across
-//     CTAs), so all CTAs agree on the winner p and build the same Householder reflector
-//     from its values, H = I - beta v v^T with H x = alpha e_1, alpha = -sign(x_1) ||x||;
+//   * one grid barrier; every warp of every CTA reduces the G proposals identically (a
+//     tournament across CTAs), so all agree on the winner p and build the same Householder
+//     reflector from its values, H = I - beta v v^T with H x = alpha e_1,
+//     alpha = -sign(x_1) ||x||;
 //   * the winner takes position t (the row at position t moves to the winner's position),
-//     R(0:t, t) and R(t, t) = alpha are recorded, and every CTA applies H to its remaining
-//     rows with a team of 4 threads per row (shuffle reductions) and recomputes their
-//     remaining norms from scratch.
+//     R(0:t, t) and R(t, t) = alpha are recorded, and every warp applies H to its remaining
+//     rows with a team of 4 lanes per row (shuffle reductions).  Remaining norms are
+//     downdated, ||B(t+1:w, q)||^2 = ||B(t:w, q)||^2 - B(t, q)^2, and recomputed from the
+//     values whenever they fall below 1e-4 of their last exact value, which keeps their
+//     relative error near 1e-12.
 // Then M = R11^-1 R12 for each remaining row by back substitution.  While the largest
 // |M_ij| exceeds tau (ties to the smallest j, then i), selected slot i and remaining row j
 // are interchanged; instead of a new QR, M is updated by the exact basis-exchange formulas
@@ -62,23 +65,6 @@ __device__ __forceinline__ Cand warp_best(Cand c) {
   return c;
 }
 
-// Block-wide best candidate, returned to every thread.
-__device__ Cand block_best(Cand c, Cand* scratch) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  c = warp_best(c);
-  if (lane == 0) scratch[warp] = c;
-  __syncthreads();
-  if (warp == 0) {
-    Cand d = lane < (int)(blockDim.x >> 5) ? scratch[lane] : Cand{-1.0, 0x7fffffff, 0x7fffffff, -1};
-    d = warp_best(d);
-    if (lane == 0) scratch[32] = d;
-  }
-  __syncthreads();
-  Cand r = scratch[32];
-  __syncthreads();
-  return r;
-}
-
 // Sum over the 4 lanes of a row team.  Every lane receives the same bits: the xor
 // butterfly adds the same pairs in each lane, only commuted.
 __device__ __forceinline__ double team_sum(double s) {
@@ -88,39 +74,44 @@ __device__ __forceinline__ double team_sum(double s) {
   return s;
 }
 
-__device__ __forceinline__ double warp_sum(double s) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  return s;
-}
-
 }  // namespace
 
+// Warp-centric layout: warp k of a CTA owns a fixed slice of the CTA's rows for the whole
+// kernel, and inside a warp 8 teams of 4 lanes work on one row each.  All per-row state
+// (values, remaining squared norm, position) is touched only by its own warp, so a QRCP
+// step needs just two block-wide syncs (gathering the warps' proposals, releasing the
+// warps after the grid barrier); every warp reduces the G proposals of the tournament on
+// its own and keeps its own copy of the winning row.
 template <int W>
 __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int SP = W + 4;   // row stride: 4 mod 16 doubles keeps team accesses conflict-light
-  constexpr int kTeams = kPanelThreads / kTeam;
-  __shared__ Cand s_red[33];
-  __shared__ double s_alpha, s_beta;
+  constexpr int kWarps = kPanelThreads / 32;
+  constexpr int kTeamsPerWarp = 32 / kTeam;
+  __shared__ Cand s_wc[kWarps];
+  __shared__ Cand s_cta;
 
   DevState* st = p.st;
   if (dev_status(st) != 0) return;
 
   const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int tl = tid & (kTeam - 1), team = tid / kTeam;
+  const int tl = lane & (kTeam - 1), tw = lane / kTeam;          // lane in team, team in warp
   const unsigned tmask = 0xfu << (lane & ~3);
   const int w = p.w, m = p.m;
   const int rpc = p.rows_per_cta;
   const int r0 = cta * rpc;
   const int nr = max(0, min(rpc, m - r0));
+  const int rpw = (nr + kWarps - 1) / kWarps;                   // rows per warp
+  const int wr0 = min(nr, warp * rpw), wr1 = min(nr, wr0 + rpw);
 
   double* Ps = reinterpret_cast<double*>(smem_raw);      // rpc x SP panel rows
   double* Rs = Ps + (size_t)rpc * SP;                     // W x W, R11 (row-major)
-  double* vs = Rs + W * W;                                // W: broadcast column / reflector
-  double* nrm = vs + W;                                   // rpc remaining squared norms
-  int* pos = reinterpret_cast<int*>(nrm + rpc);           // rpc current positions
+  double* vsw = Rs + W * W;                               // kWarps x W: each warp's winner row
+  double* nrm = vsw + kWarps * W;                         // rpc remaining squared norms
+  double* nref = nrm + rpc;                               // rpc norms at their last exact value
+  int* pos = reinterpret_cast<int*>(nref + rpc);          // rpc current positions
+  double* vs = vsw + warp * W;
 
   unsigned nbar = 0;
 
@@ -128,99 +119,139 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     const int r = e / w, c = e - r * w;
     Ps[r * SP + c] = p.P[(long long)(r0 + r) * p.ldp + c];
   }
-  for (int r = tid; r < nr; r += blockDim.x) pos[r] = r0 + r;
   __syncthreads();
-  for (int r = team; r < nr; r += kTeams) {
+  for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
     double s = 0.0;
     for (int i = tl; i < w; i += kTeam) { const double x = Ps[r * SP + i]; s = fma(x, x, s); }
     s = team_sum(s);
-    if (tl == 0) nrm[r] = s;
+    if (tl == 0) { nrm[r] = s; nref[r] = s; pos[r] = r0 + r; }
   }
-  __syncthreads();
+  __syncwarp();
+
+  // Gather the warps' proposals, publish this CTA's best with its row values, grid barrier.
+  // Returns false when the barrier gave up (an error is recorded) and the CTA must return.
+  auto publish_and_sync = [&](Cand c, int par, unsigned site) -> bool {
+    c = warp_best(c);
+    if (lane == 0) s_wc[warp] = c;
+    __syncthreads();
+    if (warp == 0) {
+      Cand d = lane < kWarps ? s_wc[lane] : Cand{-1.0, 0x7fffffff, 0x7fffffff, -1};
+      d = warp_best(d);
+      const size_t slot = (size_t)par * G + cta;
+      if (lane == 0) { p.xval[slot] = d.v; p.xkey[slot] = make_int2(d.k1, d.k2); }
+      if (d.aux >= 0)
+        for (int i = lane; i < w; i += 32) p.xvec[slot * kMaxW + i] = Ps[d.aux * SP + i];
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence();
+        atomicAdd(&st->barrier, 1u);
+        const unsigned target = (nbar + 1) * G;
+        const unsigned limit = st->spin_limit ? st->spin_limit : kSpinLimit;
+        unsigned spins = 0;
+        int ok = 1;
+        while (ld_acquire_u32(&st->barrier) < target) {
+          if (dev_status(st) != 0) { ok = 0; break; }
+          if (++spins > limit) {
+            if (atomicCAS(&st->status, 0, PRRP_ERR_TIMEOUT) == 0) st->timeout_site = site;
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+        __threadfence();
+        s_cta.v = ok;
+      }
+    }
+    __syncthreads();
+    ++nbar;
+    return s_cta.v != 0.0;
+  };
+
+  // Every warp: the tournament winner among the G proposals of parity `par`.
+  auto global_best = [&](int par) -> Cand {
+    Cand g{-1.0, 0x7fffffff, 0x7fffffff, -1};
+    for (int q = lane; q < G; q += 32) {
+      const size_t sq = (size_t)par * G + q;
+      const int2 k = __ldcg(&p.xkey[sq]);
+      Cand d{__ldcg(&p.xval[sq]), k.x, k.y, q};
+      if (better(d, g)) g = d;
+    }
+    return warp_best(g);
+  };
 
   // ---------------- QR with column pivoting ----------------
   for (int t = 0; t < w; ++t) {
     const int par = t & 1;
     Cand c{-1.0, 0x7fffffff, 0, -1};
-    for (int r = tid; r < nr; r += blockDim.x) {
+    for (int r = wr0 + lane; r < wr1; r += 32) {
       const int pr = pos[r];
       if (pr >= t) {
         Cand d{nrm[r], pr, 0, r};
         if (better(d, c)) c = d;
       }
     }
-    c = block_best(c, s_red);
-    const size_t slot = (size_t)par * G + cta;
-    if (tid == 0) { p.xval[slot] = c.v; p.xkey[slot] = make_int2(c.k1, c.k2); }
-    if (c.aux >= 0)
-      for (int i = tid; i < w; i += blockDim.x) p.xvec[slot * kMaxW + i] = Ps[c.aux * SP + i];
-    if (!grid_barrier(st, (++nbar) * G, 1)) return;
+    if (!publish_and_sync(c, par, 1)) return;
 
-    Cand g{-1.0, 0x7fffffff, 0, -1};
-    for (int q = tid; q < G; q += blockDim.x) {
-      const size_t sq = (size_t)par * G + q;
-      const int2 k = __ldcg(&p.xkey[sq]);
-      Cand d{__ldcg(&p.xval[sq]), k.x, k.y, q};
-      if (better(d, g)) g = d;
-    }
-    g = block_best(g, s_red);
+    const Cand g = global_best(par);
     if (!(g.v > 0.0)) {           // the largest remaining norm is zero: rank < w
       if (cta == 0 && tid == 0) set_error(st, PRRP_ERR_SINGULAR, p.col_offset + t + 1);
       return;
     }
     const int pw = g.k1;
-    for (int i = tid; i < w; i += blockDim.x)
-      vs[i] = __ldcg(&p.xvec[((size_t)par * G + g.aux) * kMaxW + i]);
-    __syncthreads();
+    for (int i = lane; i < w; i += 32) vs[i] = __ldcg(&p.xvec[((size_t)par * G + g.aux) * kMaxW + i]);
+    __syncwarp();
+    // Reflector H = I - beta v v^T with H x = alpha e_1 for x = B(t:w, p):
+    // ||x|| = sqrt of the winner's remaining squared norm, v = x - alpha e_1,
+    // v^T v = 2 ||x|| (||x|| + |x_t|), so beta = 1 / (||x|| (||x|| + |x_t|)).
+    const double x0 = vs[t];
+    const double normx = sqrt(g.v);
+    const double alpha = (x0 >= 0.0) ? -normx : normx;
+    const double beta = 1.0 / (normx * (normx + fabs(x0)));
     if (warp == 0) {
-      double s = 0.0;
-      for (int i = t + lane; i < w; i += 32) s = fma(vs[i], vs[i], s);
-      s = warp_sum(s);
-      const double x0 = vs[t];
-      const double normx = sqrt(s);
-      const double alpha = (x0 >= 0.0) ? -normx : normx;
-      const double v0 = x0 - alpha;
-      double s2 = 0.0;
-      for (int i = t + 1 + lane; i < w; i += 32) s2 = fma(vs[i], vs[i], s2);
-      s2 = warp_sum(s2);
-      const double vv = fma(v0, v0, s2);
       for (int i = lane; i < t; i += 32) Rs[i * W + t] = vs[i];
-      __syncwarp();
-      if (lane == 0) {
-        Rs[t * W + t] = alpha;
-        s_alpha = alpha;
-        s_beta = (vv == 0.0) ? 0.0 : 2.0 / vv;
-        vs[t] = v0;
-      }
+      if (lane == 0) Rs[t * W + t] = alpha;
     }
-    __syncthreads();
-    const double beta = s_beta;
-    for (int r = team; r < nr; r += kTeams) {
+    __syncwarp();
+    if (lane == 0) vs[t] = x0 - alpha;
+    __syncwarp();
+    for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
       const int pr = pos[r];
       if (pr < t) continue;                           // selected at an earlier step
       if (pr == pw) {                                  // the pivot row: now R(:, t)
         if (tl == 0) pos[r] = t;
         continue;
       }
-      const int npos = (pr == t) ? pw : pr;
-      double s = 0.0;
-      for (int i = t + tl; i < w; i += kTeam) s = fma(vs[i], Ps[r * SP + i], s);
-      s = team_sum(s);
-      const double f = beta * s;
-      double n2 = 0.0;
+      double* x = Ps + r * SP;
+      double sdot = 0.0;
+      for (int i = t + tl; i < w; i += kTeam) sdot = fma(vs[i], x[i], sdot);
+      sdot = team_sum(sdot);
+      const double f = beta * sdot;
+      double xt = 0.0;
       for (int i = t + tl; i < w; i += kTeam) {
-        const double x = fma(-f, vs[i], Ps[r * SP + i]);
-        Ps[r * SP + i] = x;
-        if (i > t) n2 = fma(x, x, n2);
+        const double y = fma(-f, vs[i], x[i]);
+        x[i] = y;
+        if (i == t) xt = y;
       }
-      n2 = team_sum(n2);
-      if (tl == 0) { nrm[r] = n2; pos[r] = npos; }
+      // remaining squared norm for step t+1: downdate, recomputed exactly when it has
+      // fallen below 1e-4 of its last exact value (bounds the cancellation error)
+      xt = __shfl_sync(tmask, xt, lane & ~3);      // x[t] is handled by team lane 0
+      double n2 = fma(-xt, xt, nrm[r]);
+      const double ref = nref[r];
+      if (!(n2 > 1e-4 * ref)) {
+        double e2 = 0.0;
+        for (int i = t + 1 + tl; i < w; i += kTeam) e2 = fma(x[i], x[i], e2);
+        n2 = team_sum(e2);
+        if (tl == 0) nref[r] = n2;
+      }
+      __syncwarp(tmask);
+      if (tl == 0) { nrm[r] = n2; pos[r] = (pr == t) ? pw : pr; }
     }
-    __syncthreads();
+    __syncwarp();
   }
+  __syncthreads();
 
   // ---------------- M = R11^-1 R12 (back substitution) ----------------
-  for (int r = team; r < nr; r += kTeams) {
+  for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
     if (pos[r] < w) continue;
     double* b = Ps + r * SP;
     for (int i = w - 1; i >= 0; --i) {
@@ -232,14 +263,14 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
       for (int k = tl; k < i; k += kTeam) b[k] = fma(-Rs[k * W + i], mi, b[k]);
     }
   }
-  __syncthreads();
+  __syncwarp();
 
   // ---------------- tau-bounded interchanges ----------------
   int swaps = 0;
   for (int it = 0;; ++it) {
     const int par = (w + it) & 1;
     Cand c{-1.0, 0x7fffffff, 0x7fffffff, -1};
-    for (int r = team; r < nr; r += kTeams) {
+    for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
       const int pr = pos[r];
       if (pr < w) continue;
       Cand d{-1.0, pr - w, 0x7fffffff, r};
@@ -247,45 +278,32 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
         const double a = fabs(Ps[r * SP + i]);
         if (a > d.v) { d.v = a; d.k2 = i; }
       }
-      // reduce over the team (same row, so k1 equal): larger |M|, then smaller i
       Cand o = shfl_cand(d, 1, tmask);
       if (better(o, d)) d = o;
       o = shfl_cand(d, 2, tmask);
       if (better(o, d)) d = o;
       if (better(d, c)) c = d;
     }
-    c = block_best(c, s_red);
-    const size_t slot = (size_t)par * G + cta;
-    if (tid == 0) { p.xval[slot] = c.v; p.xkey[slot] = make_int2(c.k1, c.k2); }
-    if (c.aux >= 0)
-      for (int i = tid; i < w; i += blockDim.x) p.xvec[slot * kMaxW + i] = Ps[c.aux * SP + i];
-    if (!grid_barrier(st, (++nbar) * G, 2)) return;
+    if (!publish_and_sync(c, par, 2)) return;
 
-    Cand g{-1.0, 0x7fffffff, 0x7fffffff, -1};
-    for (int q = tid; q < G; q += blockDim.x) {
-      const size_t sq = (size_t)par * G + q;
-      const int2 k = __ldcg(&p.xkey[sq]);
-      Cand d{__ldcg(&p.xval[sq]), k.x, k.y, q};
-      if (better(d, g)) g = d;
-    }
-    g = block_best(g, s_red);
+    const Cand g = global_best(par);
     if (!(g.v > p.tau)) break;                  // also ends when there is no remaining row
     if (swaps >= p.max_swaps) {
       if (cta == 0 && tid == 0) set_error(st, PRRP_ERR_SWAP_LIMIT, p.col_offset + 1);
       return;
     }
     const int js = g.k1, is = g.k2;
-    for (int i = tid; i < w; i += blockDim.x)
-      vs[i] = __ldcg(&p.xvec[((size_t)par * G + g.aux) * kMaxW + i]);
-    __syncthreads();
+    for (int i = lane; i < w; i += 32) vs[i] = __ldcg(&p.xvec[((size_t)par * G + g.aux) * kMaxW + i]);
+    __syncwarp();
     const double mu = vs[is];
-    for (int r = team; r < nr; r += kTeams) {
+    for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
       const int pr = pos[r];
       double* x = Ps + r * SP;
       if (pr == w + js) {                          // enters the selection at slot is
         if (tl == 0) pos[r] = is;
       } else if (pr == is) {                       // leaves the selection to slot js
         for (int k = tl; k < w; k += kTeam) x[k] = (k == is) ? 1.0 / mu : -vs[k] / mu;
+        __syncwarp(tmask);
         if (tl == 0) pos[r] = w + js;
       } else if (pr >= w) {
         const int owner = is & (kTeam - 1);
@@ -296,12 +314,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
       }
     }
     ++swaps;
-    __syncthreads();
+    __syncwarp();
   }
 
   // ---------------- outputs ----------------
   double lmax = 0.0;
-  for (int r = team; r < nr; r += kTeams) {
+  for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
     const int pr = pos[r];
     if (pr < w) continue;
     double* dst = p.L21 + (long long)(pr - w) * p.ldl;
@@ -311,7 +329,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
       lmax = fmax(lmax, fabs(v));
     }
   }
-  for (int r = tid; r < nr; r += blockDim.x) {
+  __syncwarp();
+  for (int r = wr0 + lane; r < wr1; r += 32) {
     const int pr = pos[r];
     if (p.order) p.order[pr] = r0 + r;
     if (p.pairs && pr != r0 + r) {
@@ -331,7 +350,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
 template <int W>
 static size_t panel_smem_bytes(int rpc) {
   return (size_t)rpc * (W + 4) * sizeof(double) + (size_t)W * W * sizeof(double) +
-         (size_t)W * sizeof(double) + (size_t)rpc * (sizeof(double) + sizeof(int)) + 16;
+         (size_t)(kPanelThreads / 32) * W * sizeof(double) +
+         (size_t)rpc * (2 * sizeof(double) + sizeof(int)) + 16;
 }
 
 template <int W>

@@ -69,26 +69,45 @@ __device__ void solve_diag_block(const double* __restrict__ LU, long long lda, d
 }
 
 // One step of blocked substitution.  jb = block just solved (-1: none yet).  CTA b updates
-// row block `blk` = next blocks with the solved unknowns of jb; the CTA of the block that
-// becomes final next also solves its triangle.
+// row block `blk` with the solved unknowns of jb: one warp per row, lanes along k (each
+// row of the 64 x 64 block is two coalesced 256-byte loads), the 64 solved unknowns of
+// each right-hand side staged in shared memory.  The CTA of the block that becomes final
+// next then solves its triangle.
+constexpr int kStageRhs = 32;    // right-hand sides staged per pass
+
 __global__ void __launch_bounds__(kSolveThreads) trsv_step_kernel(const double* __restrict__ LU,
                                                                   long long lda, int n, double* Y,
                                                                   int nrhs, int jb, int lower) {
+  __shared__ double xs[kSB * kStageRhs];
   const int nb = (n + kSB - 1) / kSB;
   int blk, next;
   if (lower) { blk = jb + 1 + blockIdx.x; next = jb + 1; }
   else       { blk = (jb < 0 ? nb : jb) - 1 - blockIdx.x; next = (jb < 0 ? nb : jb) - 1; }
   if (blk < 0 || blk >= nb) return;
   const int r0 = blk * kSB, kb = min(kSB, n - r0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   if (jb >= 0) {
     const int c0 = jb * kSB, kc = min(kSB, n - c0);
-    // Y[r0:r0+kb, :] -= LU[r0:r0+kb, c0:c0+kc] * Y[c0:c0+kc, :]
-    for (int e = threadIdx.x; e < kb * nrhs; e += blockDim.x) {
-      const int i = e / nrhs, c = e - i * nrhs;
-      const double* a = LU + (long long)(r0 + i) * lda + c0;
-      double acc = 0.0;
-      for (int k = 0; k < kc; ++k) acc = fma(a[k], Y[(long long)(c0 + k) * nrhs + c], acc);
-      Y[(long long)(r0 + i) * nrhs + c] -= acc;
+    for (int cb = 0; cb < nrhs; cb += kStageRhs) {
+      const int nc = min(kStageRhs, nrhs - cb);
+      __syncthreads();
+      for (int e = threadIdx.x; e < kc * nc; e += blockDim.x) {
+        const int k = e / nc, c = e - k * nc;
+        xs[k * kStageRhs + c] = Y[(long long)(c0 + k) * nrhs + cb + c];
+      }
+      __syncthreads();
+      // Y[r0:r0+kb, cb:cb+nc] -= LU[r0:r0+kb, c0:c0+kc] * xs
+      for (int i = warp; i < kb; i += nwarps) {
+        const double* a = LU + (long long)(r0 + i) * lda + c0;
+        const double a0 = lane < kc ? a[lane] : 0.0;
+        const double a1 = lane + 32 < kc ? a[lane + 32] : 0.0;
+        for (int c = 0; c < nc; ++c) {
+          double acc = a0 * (lane < kc ? xs[lane * kStageRhs + c] : 0.0);
+          if (lane + 32 < kc) acc = fma(a1, xs[(lane + 32) * kStageRhs + c], acc);
+          for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+          if (lane == 0) Y[(long long)(r0 + i) * nrhs + cb + c] -= acc;
+        }
+      }
     }
     __syncthreads();
   }

@@ -1,0 +1,91 @@
+"""Mixed-precision forms on GB300: the Schur update on tcgen05 tensor cores (TF32, or the
+3-term BF16 split with six products), FP64 pivoting, and FP64 iterative refinement of the
+solve back to FP64-level backward error.
+
+Error bounds for C -= L U computed this way (per entry, S = sum_k |L_ik| |U_kj|):
+* TF32: each operand rounded to 11 significant bits (relative error <= 2^-11), FP32
+  accumulation of K terms: |dC| <= (2^-10 + 2^-22 + K 2^-24) S;
+* 3 x BF16: each operand represented by hi + mid + lo to 2^-24 relative, the three dropped
+  cross products are below 3 * 2^-24, FP32 accumulation of 6K terms:
+  |dC| <= (5 * 2^-24 + 6 K 2^-24) S.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import prrp_inputs as pi
+from oracle import metrics as M
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def prrp():
+    import paper_1208_2451_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(prrp):
+    c = prrp.prrp_create(0)
+    yield c
+    c.close()
+
+
+def _bound(prec, K, S):
+    if prec == 1:    # TF32
+        return (2.0 ** -10 + 2.0 ** -22 + K * 2.0 ** -24) * S
+    return (5 * 2.0 ** -24 + 6 * K * 2.0 ** -24) * S
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (1000, 777, 64), (129, 65, 16), (300, 2000, 128),
+                                   (64, 64, 100), (1, 1, 1), (5000, 31, 16), (8128, 8128, 64)])
+def test_schur_update_tensor_cores(prrp, ctx, prec, m, n, k):
+    """Row a5 in the low-precision forms against the exact FP64 product."""
+    g = pi.rng(m * 13 + n * 7 + k)
+    L, U, Cm = g.standard_normal((m, k)), g.standard_normal((k, n)), g.standard_normal((m, n))
+    dC = torch.from_numpy(Cm).cuda()
+    prrp.prrp_schur_update(ctx, torch.from_numpy(L).cuda(), torch.from_numpy(U).cuda(), dC, prec=prec)
+    got = dC.cpu().numpy()
+    want = Cm - L @ U
+    S = np.abs(L) @ np.abs(U)
+    assert np.all(np.abs(got - want) <= _bound(prec, k, S) + 4 * EPS * np.abs(Cm)), \
+        float(np.max(np.abs(got - want) / S))
+    # the tensor cores really computed something: the error is below the TF32/BF16 input
+    # rounding of a single operand, not just the difference of magnitudes
+    rel = np.max(np.abs(got - want)) / np.max(S)
+    assert rel < (2e-3 if prec == 1 else 1e-5)
+
+
+def _mixed_solve(prrp, ctx, A, B, prec, b):
+    dA = torch.from_numpy(A).cuda()
+    F = prrp.prrp_factor(ctx, dA, b=b, prec=prec)
+    st = F.stats()
+    LU = dA.cpu().numpy()
+    perm = F.perm().astype(np.int64)
+    dB = torch.from_numpy(B).cuda()
+    info = prrp.prrp_solve(ctx, F, dB, A_orig=torch.from_numpy(A).cuda(), refine_max_iter=30)
+    F.close()
+    return LU, perm, st, dB.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("prec,n,b,kappa", [(2, 256, 16, None), (2, 1024, 64, None), (2, 1000, 64, 1e6),
+                                            (1, 1024, 64, 1e2), (1, 700, 32, 1e2)])
+def test_mixed_factor_and_refine(prrp, ctx, prec, n, b, kappa):
+    """FP64 pivots on a low-precision Schur update, then FP64 refinement: eta <= 1e-15."""
+    A = pi.randn(n, 21) if kappa is None else pi.conditioned(n, kappa, 21)
+    B = pi.rhs(n, 4, 21)
+    LU, perm, st, X, info = _mixed_solve(prrp, ctx, A, B, prec, b)
+    assert sorted(perm) == list(range(n))
+    res = M.factor_residual(A, LU, perm)
+    assert res <= (1e-2 if prec == 1 else 1e-5) * max(1.0, st["growth"]), res
+    # the pivots are a valid LU_PRRP selection of the exact matrix up to the update's error
+    mx = oracle.selection_multipliers(A, perm, b)
+    assert max(mx) <= 2.0 * (1 + (0.5 if prec == 1 else 1e-3)), max(mx)
+    assert info["eta"] <= 1e-15, info
+    for c in range(B.shape[1]):
+        assert M.eta(A, X[:, c], B[:, c]) <= 1e-15
