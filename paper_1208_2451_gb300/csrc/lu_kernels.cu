@@ -220,6 +220,10 @@ cudaError_t launch_gemm_fp64(int m, int n, int k, const double* L, long long ldl
 }
 
 // ---------------------------------------------------------------- diagonal GEPP
+// One CTA; thread (i, q) = (tid / 4, tid % 4) owns row i's columns j = q mod 4.  Per step:
+// the pivot search compares |a| by IEEE bit pattern (integer pipe), the pivot row is
+// swapped by its owners, and one fused pass forms l_i = a_it / a_tt (one reciprocal per
+// step) and a_ij -= l_i a_tj.  w <= 64 rows per pass of 64 row-teams; larger w loops.
 __global__ void __launch_bounds__(256) diag_gepp_kernel(double* __restrict__ A, long long lda,
                                                         int k0, int w, int* __restrict__ ipiv,
                                                         int* __restrict__ perm, DevState* st) {
@@ -227,35 +231,44 @@ __global__ void __launch_bounds__(256) diag_gepp_kernel(double* __restrict__ A, 
   extern __shared__ double D[];                    // w x (w + 1)
   const int WP = w + 1;
   __shared__ int s_p;
-  __shared__ double s_v;
+  __shared__ unsigned long long s_wv[8];
+  __shared__ int s_wi[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int q = tid & 3, ri = tid >> 2;           // column class, row team
   for (int e = tid; e < w * w; e += blockDim.x) {
     const int i = e / w, j = e - i * w;
     D[i * WP + j] = A[(long long)(k0 + i) * lda + k0 + j];
   }
   __syncthreads();
   for (int t = 0; t < w; ++t) {
-    if (warp == 0) {
-      double bv = -1.0;
-      int bi = 0x7fffffff;
-      for (int i = t + lane; i < w; i += 32) {
-        const double v = fabs(D[i * WP + t]);
-        if (v > bv) { bv = v; bi = i; }
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-      }
-      if (lane == 0) { s_p = bi; s_v = bv; }
+    // pivot: first row i >= t of largest |a_it|
+    unsigned long long bv = 0ull;
+    int bi = 0x7fffffff;
+    for (int i = t + tid; i < w; i += blockDim.x) {
+      const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(D[i * WP + t]));
+      if (v > bv || bi == 0x7fffffff) { bv = v; bi = i; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { s_wv[warp] = bv; s_wi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long v = s_wv[0];
+      int i0 = s_wi[0];
+      for (int k = 1; k < 8; ++k)
+        if (s_wv[k] > v || (s_wv[k] == v && s_wi[k] < i0)) { v = s_wv[k]; i0 = s_wi[k]; }
+      s_p = (v == 0ull) ? -1 : i0;
+      ipiv[t] = i0;
     }
     __syncthreads();
-    if (!(s_v > 0.0)) {
+    const int p = s_p;
+    if (p < 0) {
       if (tid == 0) set_error(st, PRRP_ERR_SINGULAR, k0 + t + 1);
       return;
     }
-    const int p = s_p;
-    if (tid == 0) ipiv[t] = p;
     if (p != t)
       for (int j = tid; j < w; j += blockDim.x) {
         const double x = D[t * WP + j];
@@ -263,13 +276,13 @@ __global__ void __launch_bounds__(256) diag_gepp_kernel(double* __restrict__ A, 
         D[p * WP + j] = x;
       }
     __syncthreads();
-    const double piv = D[t * WP + t];
-    for (int i = t + 1 + tid; i < w; i += blockDim.x) D[i * WP + t] /= piv;
-    __syncthreads();
-    const int rem = w - t - 1;
-    for (int e = tid; e < rem * rem; e += blockDim.x) {
-      const int i = t + 1 + e / rem, j = t + 1 + e % rem;
-      D[i * WP + j] = fma(-D[i * WP + t], D[t * WP + j], D[i * WP + j]);
+    const double rp = 1.0 / D[t * WP + t];
+    const unsigned team_mask = 0xfu << (lane & ~3);
+    for (int i = t + 1 + ri; i < w; i += 64) {        // the 4 lanes of a team share i
+      const double l = D[i * WP + t] * rp;
+      for (int j = t + 1 + q; j < w; j += 4) D[i * WP + j] = fma(-l, D[t * WP + j], D[i * WP + j]);
+      __syncwarp(team_mask);                            // all four have read a_it
+      if (q == 0) D[i * WP + t] = l;
     }
     __syncthreads();
   }
@@ -358,11 +371,109 @@ __global__ void __launch_bounds__(kU12Cols) u12_kernel(double* __restrict__ A, l
   }
 }
 
+// Register-resident U12 for a full-width block (w == W): one thread per column, the
+// column's W values in registers, GEPP's interchanges folded into the loads (each thread
+// reads the block rows in their interchanged order), forward substitution with the unit
+// lower L11 fully unrolled (L11 from shared memory, broadcast).  Left of the block only the
+// interchanges apply.
+template <int W>
+__global__ void __launch_bounds__(32) u12_reg_kernel(double* __restrict__ A, long long lda, int n,
+                                                     int k0, const int* __restrict__ ipiv,
+                                                     int left_slices, DevState* st) {
+  if (dev_status(st) != 0) return;
+  __shared__ double Ls[W * W];
+  __shared__ int src[W];
+  const int tid = threadIdx.x;
+  const bool right = blockIdx.x >= left_slices;
+  const int c = right ? k0 + W + (blockIdx.x - left_slices) * 32 + tid : blockIdx.x * 32 + tid;
+  const int cend = right ? n : k0;
+  if (tid == 0) {                                  // composed row order of the interchanges
+    for (int t = 0; t < W; ++t) src[t] = t;
+    for (int t = 0; t < W; ++t) {
+      const int p = ipiv[t];
+      const int x = src[t]; src[t] = src[p]; src[p] = x;
+    }
+  }
+  if (right)
+    for (int e = tid; e < W * W; e += 32) {
+      const int i = e / W, j = e - i * W;
+      Ls[e] = (j < i) ? A[(long long)(k0 + i) * lda + k0 + j] : 0.0;
+    }
+  __syncthreads();
+  const bool valid = c < cend;
+  double umax = 0.0;
+  if (valid) {
+    double x[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) x[i] = A[(long long)(k0 + src[i]) * lda + c];
+    if (right) {
+#pragma unroll
+      for (int k = 0; k < W; ++k)
+#pragma unroll
+        for (int i = k + 1; i < W; ++i) x[i] = fma(-Ls[i * W + k], x[k], x[i]);
+#pragma unroll
+      for (int i = 0; i < W; ++i) umax = fmax(umax, fabs(x[i]));
+    }
+#pragma unroll
+    for (int i = 0; i < W; ++i) A[(long long)(k0 + i) * lda + c] = x[i];
+  }
+  if (right) {                                      // every lane takes part in the reduction
+    for (int off = 16; off > 0; off >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, off));
+    if (tid == 0) atomic_max_nonneg(&st->umax_bits, umax);
+  }
+}
+
+// Register-resident final multipliers for w == W: one thread per row below the block,
+// row = (L21 with GEPP's column interchanges) * L11, fully unrolled.
+template <int W>
+__global__ void __launch_bounds__(32) lfix_reg_kernel(double* __restrict__ A, long long lda, int n,
+                                                      int k0, const double* __restrict__ L21, int ldl21,
+                                                      const int* __restrict__ ipiv, DevState* st) {
+  if (dev_status(st) != 0) return;
+  __shared__ double Ls[W * W];
+  __shared__ int src[W];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int t = 0; t < W; ++t) src[t] = t;
+    for (int t = 0; t < W; ++t) {
+      const int p = ipiv[t];
+      const int x = src[t]; src[t] = src[p]; src[p] = x;
+    }
+  }
+  for (int e = tid; e < W * W; e += 32) {
+    const int i = e / W, j = e - i * W;
+    Ls[e] = (j < i) ? A[(long long)(k0 + i) * lda + k0 + j] : 0.0;
+  }
+  __syncthreads();
+  const int r = blockIdx.x * 32 + tid;             // row below the block
+  if (r >= n - k0 - W) return;
+  const double* l = L21 + (long long)r * ldl21;
+  double x[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) x[i] = l[src[i]];
+  double* out = A + (long long)(k0 + W + r) * lda + k0;
+#pragma unroll
+  for (int cc = 0; cc < W; ++cc) {
+    double acc = x[cc];
+#pragma unroll
+    for (int i = cc + 1; i < W; ++i) acc = fma(x[i], Ls[i * W + cc], acc);
+    out[cc] = acc;
+  }
+}
+
 cudaError_t launch_u12(double* A, long long lda, int n, int k0, int w, const int* ipiv,
                        DevState* st, cudaStream_t s) {
   const int left = (k0 + kU12Cols - 1) / kU12Cols;
   const int right = (n - k0 - w + kU12Cols - 1) / kU12Cols;
   if (left + right == 0) return cudaSuccess;
+  if (w == 64) {
+    u12_reg_kernel<64><<<left + right, 32, 0, s>>>(A, lda, n, k0, ipiv, left, st);
+    return cudaGetLastError();
+  }
+  if (w == 16) {
+    u12_reg_kernel<16><<<left + right, 32, 0, s>>>(A, lda, n, k0, ipiv, left, st);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)(w * w + w * kU12Cols) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(u12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -421,6 +532,14 @@ cudaError_t launch_lfix(double* A, long long lda, int n, int k0, int w, const do
                         int ldl21, const int* ipiv, DevState* st, cudaStream_t s) {
   const int rows = n - k0 - w;
   if (rows <= 0) return cudaSuccess;
+  if (w == 64) {
+    lfix_reg_kernel<64><<<(rows + 31) / 32, 32, 0, s>>>(A, lda, n, k0, L21, ldl21, ipiv, st);
+    return cudaGetLastError();
+  }
+  if (w == 16) {
+    lfix_reg_kernel<16><<<(rows + 31) / 32, 32, 0, s>>>(A, lda, n, k0, L21, ldl21, ipiv, st);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)(w * w + kLfixRows * (w + 1)) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(lfix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);

@@ -34,12 +34,22 @@ namespace prrp {
 
 namespace {
 
+// A proposal in an argmax.  The value is a non-negative double (a squared norm or |M_ij|)
+// kept as its IEEE bit pattern: for x, y >= 0, x < y exactly when bits(x) < bits(y), so
+// the reduction trees compare on the integer pipe instead of the (1/64-rate) FP64 pipe.
 struct Cand {
-  double v;   // key to maximize (-1 = no candidate)
-  int k1;     // first tie-break, ascending (position, or remaining slot j)
-  int k2;     // second tie-break, ascending (selected slot i)
-  int aux;    // payload: local row index, or proposing CTA
+  unsigned long long v;   // bits of the value to maximize (0 with k1 = INT_MAX: none)
+  int k1;                 // first tie-break, ascending (position, or remaining slot j)
+  int k2;                 // second tie-break, ascending (selected slot i)
+  int aux;                // payload: local row index, or proposing CTA
 };
+
+__device__ __forceinline__ unsigned long long vbits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x));
+}
+__device__ __forceinline__ double vval(unsigned long long b) {
+  return __longlong_as_double(static_cast<long long>(b));
+}
 
 __device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
   if (a.v != b.v) return a.v > b.v;
@@ -49,7 +59,7 @@ __device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
 
 __device__ __forceinline__ Cand shfl_cand(const Cand& c, int lane_mask, unsigned mask) {
   Cand o;
-  o.v = __shfl_xor_sync(mask, c.v, lane_mask);
+  o.v = __shfl_xor_sync(mask, c.v, lane_mask);   // 64-bit shuffle
   o.k1 = __shfl_xor_sync(mask, c.k1, lane_mask);
   o.k2 = __shfl_xor_sync(mask, c.k2, lane_mask);
   o.aux = __shfl_xor_sync(mask, c.aux, lane_mask);
@@ -89,7 +99,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   constexpr int kWarps = kPanelThreads / 32;
   constexpr int kTeamsPerWarp = 32 / kTeam;
   __shared__ Cand s_wc[kWarps];
-  __shared__ Cand s_cta;
+  __shared__ int s_ok;
 
   DevState* st = p.st;
   if (dev_status(st) != 0) return;
@@ -135,10 +145,10 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     if (lane == 0) s_wc[warp] = c;
     __syncthreads();
     if (warp == 0) {
-      Cand d = lane < kWarps ? s_wc[lane] : Cand{-1.0, 0x7fffffff, 0x7fffffff, -1};
+      Cand d = lane < kWarps ? s_wc[lane] : Cand{0ull, 0x7fffffff, 0x7fffffff, -1};
       d = warp_best(d);
       const size_t slot = (size_t)par * G + cta;
-      if (lane == 0) { p.xval[slot] = d.v; p.xkey[slot] = make_int2(d.k1, d.k2); }
+      if (lane == 0) { p.xval[slot] = vval(d.v); p.xkey[slot] = make_int2(d.k1, d.k2); }
       if (d.aux >= 0)
         for (int i = lane; i < w; i += 32) p.xvec[slot * kMaxW + i] = Ps[d.aux * SP + i];
       __syncwarp();
@@ -159,21 +169,21 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
           __nanosleep(32);
         }
         __threadfence();
-        s_cta.v = ok;
+        s_ok = ok;
       }
     }
     __syncthreads();
     ++nbar;
-    return s_cta.v != 0.0;
+    return s_ok != 0;
   };
 
   // Every warp: the tournament winner among the G proposals of parity `par`.
   auto global_best = [&](int par) -> Cand {
-    Cand g{-1.0, 0x7fffffff, 0x7fffffff, -1};
+    Cand g{0ull, 0x7fffffff, 0x7fffffff, -1};
     for (int q = lane; q < G; q += 32) {
       const size_t sq = (size_t)par * G + q;
       const int2 k = __ldcg(&p.xkey[sq]);
-      Cand d{__ldcg(&p.xval[sq]), k.x, k.y, q};
+      Cand d{vbits(__ldcg(&p.xval[sq])), k.x, k.y, q};
       if (better(d, g)) g = d;
     }
     return warp_best(g);
@@ -182,18 +192,18 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   // ---------------- QR with column pivoting ----------------
   for (int t = 0; t < w; ++t) {
     const int par = t & 1;
-    Cand c{-1.0, 0x7fffffff, 0, -1};
+    Cand c{0ull, 0x7fffffff, 0, -1};
     for (int r = wr0 + lane; r < wr1; r += 32) {
       const int pr = pos[r];
       if (pr >= t) {
-        Cand d{nrm[r], pr, 0, r};
+        Cand d{vbits(fmax(nrm[r], 0.0)), pr, 0, r};
         if (better(d, c)) c = d;
       }
     }
     if (!publish_and_sync(c, par, 1)) return;
 
     const Cand g = global_best(par);
-    if (!(g.v > 0.0)) {           // the largest remaining norm is zero: rank < w
+    if (g.v == 0ull) {            // the largest remaining norm is zero: rank < w
       if (cta == 0 && tid == 0) set_error(st, PRRP_ERR_SINGULAR, p.col_offset + t + 1);
       return;
     }
@@ -204,7 +214,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     // ||x|| = sqrt of the winner's remaining squared norm, v = x - alpha e_1,
     // v^T v = 2 ||x|| (||x|| + |x_t|), so beta = 1 / (||x|| (||x|| + |x_t|)).
     const double x0 = vs[t];
-    const double normx = sqrt(g.v);
+    const double normx = sqrt(vval(g.v));
     const double alpha = (x0 >= 0.0) ? -normx : normx;
     const double beta = 1.0 / (normx * (normx + fabs(x0)));
     if (warp == 0) {
@@ -222,9 +232,14 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
         continue;
       }
       double* x = Ps + r * SP;
-      double sdot = 0.0;
-      for (int i = t + tl; i < w; i += kTeam) sdot = fma(vs[i], x[i], sdot);
-      sdot = team_sum(sdot);
+      double sd0 = 0.0, sd1 = 0.0;      // two chains halve the dependent-FMA latency
+      int i = t + tl;
+      for (; i + kTeam < w; i += 2 * kTeam) {
+        sd0 = fma(vs[i], x[i], sd0);
+        sd1 = fma(vs[i + kTeam], x[i + kTeam], sd1);
+      }
+      if (i < w) sd0 = fma(vs[i], x[i], sd0);
+      const double sdot = team_sum(sd0 + sd1);
       const double f = beta * sdot;
       double xt = 0.0;
       for (int i = t + tl; i < w; i += kTeam) {
@@ -251,32 +266,36 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   __syncthreads();
 
   // ---------------- M = R11^-1 R12 (back substitution) ----------------
+  // the diagonal's reciprocals once per CTA (a division is ~8 FP64 instructions)
+  double* rdiag = vsw;                                    // the winner rows are no longer needed
+  for (int i = tid; i < w; i += blockDim.x) rdiag[i] = 1.0 / Rs[i * W + i];
+  __syncthreads();
   for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
     if (pos[r] < w) continue;
     double* b = Ps + r * SP;
     for (int i = w - 1; i >= 0; --i) {
       const int owner = i & (kTeam - 1);
       double mi = 0.0;
-      if (tl == owner) mi = b[i] / Rs[i * W + i];
+      if (tl == owner) mi = b[i] * rdiag[i];
       mi = __shfl_sync(tmask, mi, (lane & ~3) | owner);
       if (tl == owner) b[i] = mi;
       for (int k = tl; k < i; k += kTeam) b[k] = fma(-Rs[k * W + i], mi, b[k]);
     }
   }
-  __syncwarp();
+  __syncthreads();              // rdiag shares memory with the warps' winner rows
 
   // ---------------- tau-bounded interchanges ----------------
   int swaps = 0;
   for (int it = 0;; ++it) {
     const int par = (w + it) & 1;
-    Cand c{-1.0, 0x7fffffff, 0x7fffffff, -1};
+    Cand c{0ull, 0x7fffffff, 0x7fffffff, -1};
     for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
       const int pr = pos[r];
       if (pr < w) continue;
-      Cand d{-1.0, pr - w, 0x7fffffff, r};
+      Cand d{0ull, pr - w, 0x7fffffff, r};
       for (int i = tl; i < w; i += kTeam) {
-        const double a = fabs(Ps[r * SP + i]);
-        if (a > d.v) { d.v = a; d.k2 = i; }
+        const unsigned long long a = vbits(fabs(Ps[r * SP + i]));
+        if (a > d.v || d.k2 == 0x7fffffff) { d.v = a; d.k2 = i; }
       }
       Cand o = shfl_cand(d, 1, tmask);
       if (better(o, d)) d = o;
@@ -287,7 +306,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     if (!publish_and_sync(c, par, 2)) return;
 
     const Cand g = global_best(par);
-    if (!(g.v > p.tau)) break;                  // also ends when there is no remaining row
+    if (g.aux < 0 || !(vval(g.v) > p.tau)) break;   // also ends when there is no remaining row
     if (swaps >= p.max_swaps) {
       if (cta == 0 && tid == 0) set_error(st, PRRP_ERR_SWAP_LIMIT, p.col_offset + 1);
       return;
