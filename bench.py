@@ -153,6 +153,107 @@ def run_reference(args) -> None:
     }), flush=True)
 
 
+def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=1):
+    """Mixed-precision form: A = Q1 diag(sigma) Q2^T (cond kappa, Q from QR of seeded
+    Gaussians), BF16X3 tensor-core Schur update with FP64 pivoting, FP64 refinement of 4
+    right-hand sides.  The matrix is generated on the GPU in FP64 (torch QR)."""
+    out = {}
+    for kappa in kappas:
+        g = torch.Generator(device=dev)
+        g.manual_seed(int(kappa) % 1000003)
+        Q1, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=g))
+        Q2, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=g))
+        sig = kappa ** (-torch.arange(n, dtype=torch.float64, device=dev) / (n - 1))
+        A0 = (Q1 * sig) @ Q2.T
+        del Q1, Q2
+        B0 = torch.randn(n, 4, dtype=torch.float64, device=dev, generator=g)
+        A = torch.empty_like(A0)
+        B = torch.empty_like(B0)
+        times, info = [], None
+        for it in range(steps + 1):
+            A.copy_(A0)
+            B.copy_(B0)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            F = prrp.prrp_factor(ctx, A, b=64, prec=prec)
+            info = prrp.prrp_solve(ctx, F, B, A_orig=A0, refine_max_iter=30)
+            torch.cuda.synchronize(dev)
+            if it:
+                times.append(time.perf_counter() - t0)
+            F.close()
+        r = B0 - A0 @ B
+        eta = float((r.abs().sum(0) / (A0.abs().sum(0).max() * B.abs().sum(0) + B0.abs().sum(0))).max())
+        dt = min(times)
+        out[f"kappa={kappa:g}"] = {"s": dt, "tflops": 2 * n ** 3 / 3 / dt / 1e12, "solves_per_s": 1.0 / dt,
+                                   "eta": eta, "iterations": info["iterations"]}
+        del A0, A, B0, B
+        torch.cuda.empty_cache()
+    return {"workload": f"n={n}, b=64, tau=2, cond-controlled A, 4 RHS, "
+                        f"{'BF16X3' if prec == 2 else 'TF32'} Schur update + FP64 refinement", "runs": out}
+
+
+def form_batched(prrp, ctx, torch, dev, count=4096, reps=3):
+    """Batched form: 4096 systems, n uniform in [32, 512], b = 16, one RHS, FP32 factor +
+    FP64 refinement, in one persistent launch."""
+    import prrp_inputs as pi
+    sizes = pi.batch_sizes(count, 32, 512, 0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    As = [torch.randn(int(k), int(k), dtype=torch.float64, device=dev, generator=g) for k in sizes]
+    B0 = [torch.randn(int(k), 1, dtype=torch.float64, device=dev, generator=g) for k in sizes]
+    res = {}
+    for prec, name in ((3, "fp32_factor"), (0, "fp64_factor")):
+        best = None
+        for _ in range(reps):
+            Bs = [b.clone() for b in B0]
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            st, info = prrp.prrp_batch_solve(ctx, As, Bs, b=16, prec=prec)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        res[name] = {"s": best, "solves_per_s": count / best,
+                     "tflops": sum(2.0 * float(k) ** 3 / 3 for k in sizes) / best / 1e12,
+                     "max_eta": max(i["eta"] for i in info), "failed": sum(1 for x in st if x != 0)}
+    return {"workload": f"{count} systems, n uniform in [32, 512], b=16, 1 RHS", "runs": res}
+
+
+def form_served(prrp, ctx, rates=(300.0, 3000.0), count=400, budget=64 << 30):
+    """Served form: Poisson arrivals, n log-uniform in [64, 4096], RHS count uniform in
+    1..16, iid N(0,1); a pool of 48 pre-generated matrices is cycled so request generation
+    does not bound the arrival rate."""
+    import prrp_inputs as pi
+    pool_sizes = np.unique(np.geomspace(64, 4096, 48).astype(int))
+    pool = {int(k): pi.randn(int(k), 7000 + int(k)) for k in pool_sizes}
+    out = {}
+    for rate in rates:
+        t, ns, nr = pi.serve_requests(count, rate, 64, 4096, 16, int(rate))
+        keys = np.array(sorted(pool))
+        reqs = []
+        for k, (nq, kq) in enumerate(zip(ns, nr)):
+            nn = int(keys[np.argmin(np.abs(keys - nq))])
+            reqs.append((pool[nn], pi.rhs(nn, int(kq), k), np.zeros((nn, int(kq)))))
+        srv = prrp.prrp_server_create(ctx, budget, lanes=4)
+        t0 = time.perf_counter()
+        tickets = []
+        for (A, B, X), ta in zip(reqs, t):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            tickets.append(srv.submit(A, B, X))
+        results = [srv.wait(tk) for tk in tickets]
+        st = srv.stats()
+        srv.close()
+        worst = max(r["eta"] for r in results)
+        out[f"rate={rate:g}/s"] = {"solves_per_s": st["solves_per_s"], "p50_ms": st["p50_us"] / 1e3,
+                                   "p99_ms": st["p99_us"] / 1e3, "max_eta": worst,
+                                   "failed": sum(1 for r in results if r["status"] != 0),
+                                   "peak_busy_lanes": st["peak_busy_lanes"],
+                                   "peak_GB_in_use": st["peak_bytes_in_use"] / 2**30}
+    return {"workload": f"{count} requests per rate, n log-uniform [64, 4096], nrhs 1..16, "
+                        f"64 GB admission budget, 4 lanes", "runs": out}
+
+
 def run_ours(args) -> None:
     import torch
     import prrp_inputs as pi
@@ -242,6 +343,11 @@ def run_ours(args) -> None:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_s = float(te[0])
 
+    forms = {}
+    if rank == 0 and world == 1 and not args.no_forms:
+        forms["mixed"] = form_mixed(prrp, ctx, torch, dev)
+        forms["batched"] = form_batched(prrp, ctx, torch, dev)
+        forms["served"] = form_served(prrp, ctx)
     if rank == 0:
         csum = clocks.summary()
         up = kstats["update"]
@@ -284,6 +390,8 @@ def run_ours(args) -> None:
         }
         if cpu:
             out["cpu_baseline"] = cpu
+        if forms:
+            out["forms"] = forms
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:
@@ -301,9 +409,22 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--ref-panels", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the mixed-precision, batched and served measurements")
+    ap.add_argument("--form", choices=["mixed", "batched", "served"],
+                    help="run only one of the other forms and print its JSON")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.form:
+        import torch
+        import paper_1208_2451_gb300 as prrp
+        ctx = prrp.prrp_create(0)
+        fn = {"mixed": lambda: form_mixed(prrp, ctx, torch, torch.device("cuda", 0), n=args.n if args.n != N_DEFAULT else 16384),
+              "batched": lambda: form_batched(prrp, ctx, torch, torch.device("cuda", 0)),
+              "served": lambda: form_served(prrp, ctx)}[args.form]
+        print(json.dumps({"form": args.form, **fn()}), flush=True)
+        ctx.close()
     else:
         run_ours(args)
 

@@ -154,6 +154,93 @@ prrp_status prrp_gesv_host(prrp_ctx* ctx, int n, const double* hA, int lda, int 
                            const double* hB, int ldb, double* hX, const prrp_opts* opts,
                            void* stream, prrp_factor_stats* stats, prrp_solve_info* info);
 
+/*
+ * prrp_batch_solve - solve `count` independent systems A_i X_i = B_i (n_i <= 1024) in one
+ * persistent launch: one CTA runs the whole of Algorithm 1 (strong RRQR panels with tau
+ * interchanges, Schur update, diagonal GEPP, U12, final L) on one system at a time, taking
+ * systems largest first from a work list, then solves and refines in FP64 (Section 3.3).
+ *
+ * Host arrays of length count: n, lda, nrhs, ldb, and dA / dB (device pointers).  Each A_i
+ * is an n_i x n_i row-major FP64 matrix (not modified); each B_i (n_i x nrhs_i, ldb_i) is
+ * overwritten by X_i.  dPerm (host array of device pointers, may be NULL; entries may be
+ * NULL) receives each system's row permutation (n_i ints, perm[i] = original row at i).
+ * opts (may be NULL): b (<= 32, default 16 here), tau, max_swaps,
+ * refine_max_iter, refine_target, prec = PRRP_FP32 (default: FP32 working copy and Schur
+ * update, FP64 panel selection, GEPP, substitution arithmetic and residual) or PRRP_FP64.
+ * per_system (host, count, may be NULL) receives each system's status; info (host, count,
+ * may be NULL) its refinement count and first/final normwise backward error (max over its
+ * right-hand sides).  Returns PRRP_OK when every system succeeded, otherwise the first
+ * failing status in input order.  The launch shape (CTAs per SM) is tuned on the first
+ * call for each size bucket of 128 and cached in ctx; the launch sequence is replayed as a
+ * captured CUDA graph while the batch shape is unchanged.
+ */
+prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const double* const* dA,
+                             const int* lda, const int* nrhs, double* const* dB, const int* ldb,
+                             int* const* dPerm, const prrp_opts* opts, void* stream,
+                             prrp_status* per_system, prrp_solve_info* info);
+
+/* ---- serving: continuous batching of solve requests (serve.cpp) ---- */
+
+typedef struct prrp_server prrp_server;
+
+typedef struct {
+  int n;              /* system size, >= 1 */
+  int nrhs;           /* right-hand sides, >= 0 */
+  const double* hA;   /* host, n x n row-major (lda), read until the request completes */
+  int lda;
+  const double* hB;   /* host, n x nrhs (ldb) */
+  int ldb;
+  double* hX;         /* host, n x nrhs (ldx): receives the solution */
+  int ldx;
+} prrp_request;
+
+typedef struct {
+  prrp_status status; /* the request's outcome */
+  int iterations;     /* FP64 refinement corrections */
+  double eta;         /* normwise backward error of the returned solution (max over RHS) */
+  double latency_us;  /* submit to completion */
+  double queue_us;    /* submit to admission */
+} prrp_result;
+
+typedef struct {
+  uint64_t submitted, completed, rejected, units;
+  double p50_us, p99_us, mean_us;   /* request latency percentiles (submit to completion) */
+  double solves_per_s;              /* completed requests / (first submit .. last completion) */
+  uint64_t peak_bytes_in_use;       /* largest admitted working set, <= the budget */
+  int peak_busy_lanes;              /* most lanes with work on the device at once */
+} prrp_serve_stats;
+
+/*
+ * prrp_server_create - start a serving loop on ctx's device with `lanes` worker lanes
+ * (1..16; each lane owns a context and a stream, so lanes' work overlaps on the GPU) and
+ * an HBM admission budget in bytes for the requests' device working sets.  A request is
+ * admitted when its working set fits the budget left by the requests on the device;
+ * requests with n <= 1024 that are admitted together are solved by one batched launch
+ * (prrp_batch_solve); larger ones by prrp_factor + prrp_solve with their factors held in
+ * device memory until their FP64 refinement ends.  opts (may be NULL): prec = PRRP_FP32
+ * (default; FP32 batched factors, BF16X3 tensor-core Schur update for large n) or
+ * PRRP_FP64; b, tau, max_swaps, refine_max_iter, refine_target as for prrp_factor.
+ */
+prrp_status prrp_server_create(prrp_ctx* ctx, size_t hbm_budget_bytes, const prrp_opts* opts, int lanes,
+                               prrp_server** server);
+
+/* Queue a request (non-blocking).  PRRP_ERR_BUSY if its working set can never fit the
+ * budget.  *ticket identifies it for prrp_server_wait.  The host buffers must stay valid
+ * until the wait returns. */
+prrp_status prrp_server_submit(prrp_server* server, const prrp_request* req, uint64_t* ticket);
+
+/* Block until the request completes (timeout_us < 0: no limit) and release its ticket.
+ * PRRP_ERR_TIMEOUT if it did not complete in time (the ticket stays valid). */
+prrp_status prrp_server_wait(prrp_server* server, uint64_t ticket, int64_t timeout_us, prrp_result* out);
+
+prrp_status prrp_server_stats(prrp_server* server, prrp_serve_stats* stats);
+
+/* Finish the queued requests, stop the lanes and free the server. */
+prrp_status prrp_server_destroy(prrp_server* server);
+
+/* Device a context is bound to. */
+prrp_status prrp_ctx_device(const prrp_ctx* ctx, int* device);
+
 /* ---- single steps of Algorithm 1, exposed for verification and measurement ---- */
 
 /*
@@ -189,7 +276,8 @@ enum {
   PRRP_KIND_U12 = 5,      /* U12 = L11^-1 Pi_jj^T A12 and block-row interchanges (line 11) */
   PRRP_KIND_LFIX = 6,     /* final multipliers L21 Pi_jj L11 */
   PRRP_KIND_SOLVE = 7,    /* gather, forward/back substitution, refinement */
-  PRRP_KIND_COUNT = 8
+  PRRP_KIND_BATCH = 8,    /* the batched-solve kernel */
+  PRRP_KIND_COUNT = 9
 };
 
 /* Enable (1) or disable (0) per-kernel-class timing: each launch of ctx is bracketed by

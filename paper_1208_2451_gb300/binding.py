@@ -66,6 +66,13 @@ _SIGS = {
     "prrp_panel_select_noalloc": (_I, [_I, _I, _P, _I, _D, _I, _P, _P, C.POINTER(_I), _P]),
     "prrp_ctx_set_timing": (_I, [_P, _I]),
     "prrp_ctx_kernel_stats": (_I, [_P, _P, _P, _P, _I]),
+    "prrp_server_create": (_I, [_P, C.c_size_t, C.POINTER(prrp_opts), _I, C.POINTER(_P)]),
+    "prrp_server_submit": (_I, [_P, _P, C.POINTER(C.c_uint64)]),
+    "prrp_server_wait": (_I, [_P, C.c_uint64, C.c_int64, _P]),
+    "prrp_server_stats": (_I, [_P, _P]),
+    "prrp_server_destroy": (_I, [_P]),
+    "prrp_ctx_device": (_I, [_P, C.POINTER(_I)]),
+    "prrp_batch_solve": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, C.POINTER(prrp_opts), _P, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -289,7 +296,7 @@ def prrp_selftest_wait(ctx: Context, spin_limit: int = 20000, stream=None) -> in
     return _lib.prrp_selftest_wait(ctx.handle, int(spin_limit), _stream_ptr(stream))
 
 
-KINDS = ["scan", "panel", "permute", "update", "diag", "u12", "lfix", "solve"]
+KINDS = ["scan", "panel", "permute", "update", "diag", "u12", "lfix", "solve", "batch"]
 
 
 def prrp_ctx_set_timing(ctx: Context, enable: bool = True) -> None:
@@ -322,3 +329,97 @@ def prrp_panel_select_noalloc(P, tau=2.0, max_swaps=64, stream=None):
                                         C.byref(sw), _stream_ptr(stream))
     _check(st, "prrp_panel_select_noalloc")
     return order, L21, sw.value
+
+
+def prrp_batch_solve(ctx: Context, As, Bs, b=16, tau=2.0, prec=PRRP_FP32, max_swaps=64,
+                     refine_max_iter=10, refine_target=2.0 ** -53, stream=None, perms=None):
+    """Solve the independent systems As[i] X_i = Bs[i] (float64 CUDA tensors, n_i <= 1024)
+    in one batched launch; Bs[i] is overwritten by X_i.  perms (optional): int32 CUDA
+    tensors receiving each system's row permutation.  Returns (statuses, infos)."""
+    count = len(As)
+    n = (C.c_int * count)(*[int(A.shape[0]) for A in As])
+    lda = (C.c_int * count)(*[_dev_matrix(A, "A") for A in As])
+    nrhs = (C.c_int * count)(*[int(B.shape[1]) for B in Bs])
+    ldb = (C.c_int * count)(*[_dev_matrix(B, "B") for B in Bs])
+    pa = (C.c_void_p * count)(*[A.data_ptr() for A in As])
+    pb = (C.c_void_p * count)(*[B.data_ptr() for B in Bs])
+    pp = (C.c_void_p * count)(*[p.data_ptr() for p in perms]) if perms is not None else None
+    st = (C.c_int * count)()
+    infos = (prrp_solve_info * count)()
+    o = default_opts(b, tau, prec, max_swaps, refine_max_iter, refine_target)
+    rc = _lib.prrp_batch_solve(ctx.handle, count, n, pa, lda, nrhs, pb, ldb, pp, C.byref(o),
+                               _stream_ptr(stream), st, infos)
+    # outcomes of individual systems are reported per system; anything else raises
+    _check(rc, "prrp_batch_solve", ctx.handle,
+           allow=(PRRP_ERR_SINGULAR, PRRP_ERR_NONFINITE, PRRP_ERR_SWAP_LIMIT, PRRP_ERR_NOT_CONVERGED))
+    return list(st), [{"iterations": i.iterations, "eta0": i.eta0, "eta": i.eta} for i in infos]
+
+
+
+class prrp_request(C.Structure):
+    _fields_ = [("n", C.c_int), ("nrhs", C.c_int), ("hA", C.c_void_p), ("lda", C.c_int),
+                ("hB", C.c_void_p), ("ldb", C.c_int), ("hX", C.c_void_p), ("ldx", C.c_int)]
+
+
+class prrp_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("eta", C.c_double),
+                ("latency_us", C.c_double), ("queue_us", C.c_double)]
+
+
+class prrp_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
+                ("units", C.c_uint64), ("p50_us", C.c_double), ("p99_us", C.c_double),
+                ("mean_us", C.c_double), ("solves_per_s", C.c_double),
+                ("peak_bytes_in_use", C.c_uint64), ("peak_busy_lanes", C.c_int)]
+
+
+class Server:
+    """Owns a prrp_server* (continuous-batching solve loop)."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int, lanes: int = 4, prec=PRRP_FP32, b=64,
+                 tau=2.0, refine_max_iter=10, refine_target=2.0 ** -53):
+        o = default_opts(b, tau, prec, 64, refine_max_iter, refine_target)
+        h = C.c_void_p()
+        _check(_lib.prrp_server_create(ctx.handle, C.c_size_t(int(hbm_budget_bytes)), C.byref(o),
+                                       int(lanes), C.byref(h)), "prrp_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, A: np.ndarray, B: np.ndarray, X: np.ndarray) -> int:
+        """Queue A X = B (host float64 arrays, row-major, kept alive until wait)."""
+        n = A.shape[0]
+        nrhs = B.shape[1]
+        r = prrp_request(n, nrhs, A.ctypes.data, A.strides[0] // 8, B.ctypes.data,
+                         max(B.strides[0] // 8, nrhs), X.ctypes.data, max(X.strides[0] // 8, nrhs))
+        t = C.c_uint64(0)
+        _check(_lib.prrp_server_submit(self.handle, C.byref(r), C.byref(t)), "prrp_server_submit")
+        self._keep[t.value] = (A, B, X)
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> dict:
+        res = prrp_result()
+        _check(_lib.prrp_server_wait(self.handle, C.c_uint64(ticket), C.c_int64(timeout_us),
+                                     C.byref(res)), "prrp_server_wait")
+        self._keep.pop(ticket, None)
+        return {"status": res.status, "iterations": res.iterations, "eta": res.eta,
+                "latency_us": res.latency_us, "queue_us": res.queue_us}
+
+    def stats(self) -> dict:
+        st = prrp_serve_stats()
+        _check(_lib.prrp_server_stats(self.handle, C.byref(st)), "prrp_server_stats")
+        return {f: getattr(st, f) for f, _ in prrp_serve_stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(_lib.prrp_server_destroy(self.handle), "prrp_server_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prrp_server_create(ctx: Context, hbm_budget_bytes: int, lanes: int = 4, **kw) -> Server:
+    return Server(ctx, hbm_budget_bytes, lanes, **kw)

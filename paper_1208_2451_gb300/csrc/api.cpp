@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <numeric>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -17,6 +20,30 @@
 #include "prrp.h"
 
 using namespace prrp;
+
+namespace prrp {
+
+cudaError_t smem_optin_ptr(const void* kernel) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, cudaError_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find({dev, kernel});
+  if (it != done.end()) return it->second;
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, kernel);
+  int optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - static_cast<int>(fa.sharedSizeBytes));
+  done[{dev, kernel}] = e;
+  return e;
+}
+
+}  // namespace prrp
 
 struct prrp_ctx {
   int device = 0;
@@ -46,6 +73,17 @@ struct prrp_ctx {
   size_t hB_cap = 0;
   unsigned char* tcws = nullptr;    // split operands of the tensor-core update
   size_t tcws_cap = 0;
+  // batched solves: metadata, per-CTA workspace, outputs, tuned launch shapes, graphs
+  unsigned char* bmeta = nullptr;
+  size_t bmeta_cap = 0;
+  unsigned char* bws = nullptr;
+  size_t bws_cap = 0;
+  unsigned char* bout = nullptr;
+  size_t bout_cap = 0;
+  std::map<long long, int> batch_tuned;     // (fp64, b, size bucket) -> CTAs per SM
+  struct BatchGraph { cudaGraphExec_t exec = nullptr; std::vector<long long> sig; };
+  BatchGraph bgraph;
+  cudaStream_t capture_stream = nullptr;
   std::string last_error;
   // optional per-kernel-class timing with CUDA events on the launching stream
   bool timing = false;
@@ -273,6 +311,11 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
   if (!ctx) return PRRP_OK;
   cudaSetDevice(ctx->device);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  if (ctx->bgraph.exec) cudaGraphExecDestroy(ctx->bgraph.exec);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  if (ctx->bmeta) cudaFree(ctx->bmeta);
+  if (ctx->bws) cudaFree(ctx->bws);
+  if (ctx->bout) cudaFree(ctx->bout);
   void* ptrs[] = {ctx->st, ctx->xval, ctx->xkey, ctx->xvec, ctx->pairs, ctx->ipiv, ctx->order,
                   ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB, ctx->tcws};
   for (void* p : ptrs)
@@ -583,6 +626,251 @@ prrp_status prrp_schur_update(prrp_ctx* ctx, int m, int n, int k, const double* 
   if (ps != PRRP_OK) return ps;
   collect_timing(ctx);
   return (prrp_status)h.status;
+}
+
+// ---------------------------------------------------------------- batched solves
+namespace {
+
+struct BatchPlan {
+  int nmax, b, tmp_rows, grid;
+  size_t wsW_elems, per_cta_bytes;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Per-CTA workspace: W (nmax^2 T), Tmp rows (tmp_rows x nmax T), V (5 nmax doubles),
+// I (3 nmax ints).
+size_t batch_cta_bytes(int nmax, int tmp_rows, bool fp64) {
+  const size_t tb = fp64 ? 8 : 4;
+  return align256((size_t)nmax * nmax * tb) + align256((size_t)tmp_rows * nmax * tb) +
+         align256((size_t)5 * nmax * 8) + align256((size_t)3 * nmax * 4);
+}
+
+int batch_max_ctas_per_sm(int nmax, int b) {
+  int per = 0;
+  // both instantiations share the launch shape; ask for the float one
+  const size_t smem = batch_smem_bytes(nmax, b);
+  if (smem > 227 * 1024) return 0;
+  per = (int)std::min<size_t>(4, (228 * 1024) / (smem + 17 * 1024 + 1024));
+  return std::max(per, 1);
+}
+
+// Enqueue one batched launch (counter reset + kernel) over metadata already on the device.
+prrp_status enqueue_batch(prrp_ctx* ctx, bool fp64, int count, int nmax, int b, int tmp_rows,
+                          int grid, const prrp_opts& o, const int* d_order, const int* d_n,
+                          const double* const* d_A, const int* d_lda, const int* d_nrhs,
+                          double* const* d_B, const int* d_ldb, int* const* d_perm, int* d_status, int* d_iters,
+                          double* d_eta0, double* d_eta, unsigned* d_counter, cudaStream_t s) {
+  const size_t per = batch_cta_bytes(nmax, tmp_rows, fp64);
+  BatchLaunch L{};
+  L.count = count; L.order = d_order; L.n = d_n; L.A = d_A; L.lda = d_lda; L.nrhs = d_nrhs;
+  L.B = d_B; L.ldb = d_ldb; L.perm_out = d_perm; L.b = b; L.tau = o.tau; L.max_swaps = o.max_swaps;
+  L.refine_max_iter = o.refine_max_iter; L.refine_target = o.refine_target; L.nmax = nmax;
+  const size_t tb = fp64 ? 8 : 4;
+  unsigned char* base = ctx->bws;
+  L.wsW = base;
+  base += align256((size_t)grid * nmax * nmax * tb);
+  L.wsT = base;
+  base += align256((size_t)grid * tmp_rows * nmax * tb);
+  L.tmp_rows = tmp_rows;
+  L.wsV = reinterpret_cast<double*>(base);
+  base += align256((size_t)grid * 5 * nmax * 8);
+  L.wsI = reinterpret_cast<int*>(base);
+  (void)per;
+  L.status = d_status; L.iters = d_iters; L.eta0 = d_eta0; L.eta = d_eta; L.counter = d_counter;
+  CK(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s));
+  CK(launch_batch(fp64 ? 1 : 0, grid, L, s));
+  return PRRP_OK;
+}
+
+size_t batch_ws_bytes(int grid, int nmax, int tmp_rows, bool fp64) {
+  const size_t tb = fp64 ? 8 : 4;
+  return align256((size_t)grid * nmax * nmax * tb) + align256((size_t)grid * tmp_rows * nmax * tb) +
+         align256((size_t)grid * 5 * nmax * 8) + align256((size_t)grid * 3 * nmax * 4) + 1024;
+}
+
+}  // namespace
+
+prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const double* const* dA,
+                             const int* lda, const int* nrhs, double* const* dB, const int* ldb,
+                             int* const* dPerm, const prrp_opts* opts_in, void* stream,
+                             prrp_status* per_system, prrp_solve_info* info) {
+  if (!ctx || count < 0 || (count > 0 && (!n || !dA || !lda || !nrhs || !dB || !ldb)))
+    return PRRP_ERR_INVALID_ARG;
+  prrp_opts o;
+  prrp_opts_default(&o);
+  o.b = 16;
+  o.prec = PRRP_FP32;
+  if (opts_in) o = *opts_in;
+  prrp_status ps = check_opts(&o);
+  if (ps != PRRP_OK) return ps;
+  if (o.prec != PRRP_FP32 && o.prec != PRRP_FP64) return PRRP_ERR_UNSUPPORTED;
+  if (count == 0) return PRRP_OK;
+  int nmax = 1;
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 1 || lda[i] < n[i] || nrhs[i] < 0 || ldb[i] < std::max(nrhs[i], 1) || !dA[i] ||
+        (nrhs[i] > 0 && !dB[i]))
+      return PRRP_ERR_INVALID_ARG;
+    nmax = std::max(nmax, n[i]);
+  }
+  if (nmax > 1024) return PRRP_ERR_UNSUPPORTED;
+  const int b = std::min({o.b, batch_max_width(), nmax});
+  const bool fp64 = o.prec == PRRP_FP64;
+  const int tmp_rows = std::min(nmax, 2 * (b + o.max_swaps) + 2);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaSetDevice(ctx->device));
+  const int maxper = batch_max_ctas_per_sm(nmax, b);
+  if (maxper == 0) return PRRP_ERR_UNSUPPORTED;
+  CK(prepare_batch(std::max(nmax, 128 * ((nmax + 127) / 128)), b));
+
+  // ---- autotune the CTAs per SM for this (precision, b, size bucket), once per context
+  const int bucket = (nmax + 127) / 128;
+  const long long tkey = ((long long)fp64 << 40) | ((long long)b << 20) | bucket;
+  auto tuned = ctx->batch_tuned.find(tkey);
+  if (tuned == ctx->batch_tuned.end()) {
+    const int ns = 128 * bucket > 1024 ? 1024 : 128 * bucket;
+    const int sample = std::min(2 * ctx->num_sms, 256);
+    double* tA = nullptr;
+    double* tB = nullptr;
+    CK(cudaMalloc(&tA, sizeof(double) * (size_t)sample * ns * ns));
+    CK(cudaMalloc(&tB, sizeof(double) * (size_t)sample * ns));
+    std::vector<int> hn(sample, ns), hl(sample, ns), hr(sample, 1), hord(sample);
+    std::iota(hord.begin(), hord.end(), 0);
+    std::vector<const double*> ha(sample);
+    std::vector<double*> hb(sample);
+    for (int i = 0; i < sample; ++i) { ha[i] = tA + (size_t)i * ns * ns; hb[i] = tB + (size_t)i * ns; }
+    int best = 1;
+    float best_ms = 1e30f;
+    for (int per = 1; per <= maxper; ++per) {
+      const int grid = per * ctx->num_sms;
+      ps = grow(ctx, &ctx->bws, &ctx->bws_cap, batch_ws_bytes(grid, ns, std::min(ns, 2 * (b + o.max_swaps) + 2), fp64));
+      if (ps != PRRP_OK) break;
+      const size_t mb = align256(sizeof(int) * sample * 6) + align256(sizeof(void*) * sample * 2);
+      ps = grow(ctx, &ctx->bmeta, &ctx->bmeta_cap, mb + 256);
+      if (ps != PRRP_OK) break;
+      ps = grow(ctx, &ctx->bout, &ctx->bout_cap, align256(sizeof(int) * 2 * sample) + align256(sizeof(double) * 2 * sample) + 256);
+      if (ps != PRRP_OK) break;
+      int* mi = reinterpret_cast<int*>(ctx->bmeta);
+      CK(cudaMemcpyAsync(mi, hord.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(mi + sample, hn.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(mi + 2 * sample, hl.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(mi + 3 * sample, hr.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(mi + 4 * sample, hr.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
+      const double** pa = reinterpret_cast<const double**>(ctx->bmeta + align256(sizeof(int) * sample * 6));
+      double** pb = reinterpret_cast<double**>(ctx->bmeta + align256(sizeof(int) * sample * 6) +
+                                               sizeof(void*) * sample);
+      CK(cudaMemcpyAsync(pa, ha.data(), sizeof(void*) * sample, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(pb, hb.data(), sizeof(void*) * sample, cudaMemcpyHostToDevice, s));
+      int* d_status = reinterpret_cast<int*>(ctx->bout);
+      int* d_iters = d_status + sample;
+      double* d_e0 = reinterpret_cast<double*>(ctx->bout + align256(sizeof(int) * 2 * sample));
+      double* d_e = d_e0 + sample;
+      unsigned* d_counter = reinterpret_cast<unsigned*>(mi + 5 * sample);
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {                // first run warms up
+        CK(launch_batch_fill(tA, ns, sample, tB, s));
+        CK(cudaEventRecord(e0, s));
+        ps = enqueue_batch(ctx, fp64, sample, ns, b, std::min(ns, 2 * (b + o.max_swaps) + 2), grid, o, mi,
+                           mi + sample, pa, mi + 2 * sample, mi + 3 * sample, pb, mi + 4 * sample,
+                           nullptr, d_status, d_iters, d_e0, d_e, d_counter, s);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (ps != PRRP_OK) break;
+      if (ms < best_ms) { best_ms = ms; best = per; }
+    }
+    cudaFree(tA);
+    cudaFree(tB);
+    if (ps != PRRP_OK) return ps;
+    ctx->batch_tuned[tkey] = best;
+    tuned = ctx->batch_tuned.find(tkey);
+  }
+  const int grid = tuned->second * ctx->num_sms;
+
+  // ---- metadata: largest systems first, so the tail of the work list is short
+  std::vector<int> ord(count);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return n[x] > n[y]; });
+  const size_t ints = align256(sizeof(int) * ((size_t)count * 6 + 1));
+  const size_t ptrs = align256(sizeof(void*) * (size_t)count * 3);
+  if ((ps = grow(ctx, &ctx->bmeta, &ctx->bmeta_cap, ints + ptrs + 256)) != PRRP_OK) return ps;
+  if ((ps = grow(ctx, &ctx->bws, &ctx->bws_cap, batch_ws_bytes(grid, nmax, tmp_rows, fp64))) != PRRP_OK) return ps;
+  const size_t outb = align256(sizeof(int) * 2 * (size_t)count) + align256(sizeof(double) * 2 * (size_t)count);
+  if ((ps = grow(ctx, &ctx->bout, &ctx->bout_cap, outb + 256)) != PRRP_OK) return ps;
+  std::vector<unsigned char> host(ints + ptrs, 0);
+  int* hi = reinterpret_cast<int*>(host.data());
+  std::copy(ord.begin(), ord.end(), hi);
+  std::copy(n, n + count, hi + count);
+  std::copy(lda, lda + count, hi + 2 * count);
+  std::copy(nrhs, nrhs + count, hi + 3 * count);
+  std::copy(ldb, ldb + count, hi + 4 * count);
+  std::memcpy(host.data() + ints, dA, sizeof(void*) * count);
+  std::memcpy(host.data() + ints + sizeof(void*) * count, dB, sizeof(void*) * count);
+  if (dPerm) std::memcpy(host.data() + ints + 2 * sizeof(void*) * count, dPerm, sizeof(void*) * count);
+  CK(cudaMemcpyAsync(ctx->bmeta, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+  int* mi = reinterpret_cast<int*>(ctx->bmeta);
+  const double* const* pa = reinterpret_cast<const double* const*>(ctx->bmeta + ints);
+  double* const* pb = reinterpret_cast<double* const*>(ctx->bmeta + ints + sizeof(void*) * count);
+  int* const* pp = reinterpret_cast<int* const*>(ctx->bmeta + ints + 2 * sizeof(void*) * count);
+  int* d_status = reinterpret_cast<int*>(ctx->bout);
+  int* d_iters = d_status + count;
+  double* d_e0 = reinterpret_cast<double*>(ctx->bout + align256(sizeof(int) * 2 * (size_t)count));
+  double* d_e = d_e0 + count;
+  unsigned* d_counter = reinterpret_cast<unsigned*>(mi + 5 * count);
+
+  // ---- the launch sequence, replayed as a captured CUDA graph while its shape is unchanged
+  long long tau_bits, tgt_bits;
+  std::memcpy(&tau_bits, &o.tau, 8);
+  std::memcpy(&tgt_bits, &o.refine_target, 8);
+  const std::vector<long long> sig = {count, nmax, grid, fp64, b, tmp_rows, tau_bits, o.max_swaps, dPerm != nullptr,
+                                      o.refine_max_iter, tgt_bits, (long long)(uintptr_t)ctx->bws,
+                                      (long long)(uintptr_t)ctx->bmeta, (long long)(uintptr_t)ctx->bout};
+  if (ctx->bgraph.sig != sig || !ctx->bgraph.exec) {
+    if (ctx->bgraph.exec) { cudaGraphExecDestroy(ctx->bgraph.exec); ctx->bgraph.exec = nullptr; }
+    if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+    ps = enqueue_batch(ctx, fp64, count, nmax, b, tmp_rows, grid, o, mi, mi + count, pa, mi + 2 * count,
+                       mi + 3 * count, pb, mi + 4 * count, dPerm ? pp : nullptr, d_status, d_iters, d_e0,
+                       d_e, d_counter, ctx->capture_stream);
+    cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &g);
+    if (ps != PRRP_OK) { if (g) cudaGraphDestroy(g); return ps; }
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "batch graph capture");
+    ce = cudaGraphInstantiate(&ctx->bgraph.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "batch graph instantiate");
+    ctx->bgraph.sig = sig;
+  }
+  {
+    Timed t(ctx, s, PRRP_KIND_BATCH);
+    CK(cudaGraphLaunch(ctx->bgraph.exec, s));
+  }
+  std::vector<int> hs(2 * (size_t)count);
+  std::vector<double> he(2 * (size_t)count);
+  CK(cudaMemcpyAsync(hs.data(), d_status, sizeof(int) * 2 * count, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(he.data(), d_e0, sizeof(double) * 2 * count, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  collect_timing(ctx);
+  prrp_status first = PRRP_OK;
+  for (int i = 0; i < count; ++i) {
+    const prrp_status si = static_cast<prrp_status>(hs[i]);
+    if (per_system) per_system[i] = si;
+    if (info) { info[i].iterations = hs[count + i]; info[i].eta0 = he[i]; info[i].eta = he[count + i]; }
+    if (si != PRRP_OK && first == PRRP_OK) first = si;
+  }
+  return first;
+}
+
+prrp_status prrp_ctx_device(const prrp_ctx* ctx, int* device) {
+  if (!ctx || !device) return PRRP_ERR_INVALID_ARG;
+  *device = ctx->device;
+  return PRRP_OK;
 }
 
 prrp_status prrp_ctx_set_timing(prrp_ctx* ctx, int enable) {

@@ -1,0 +1,671 @@
+// Batched LU_PRRP solves of many independent small systems (n <= 1024) in one persistent
+// launch: each CTA takes the next system from a size-sorted work list and runs the whole
+// of Algorithm 1 on it, then the solve and FP64 iterative refinement (Section 3.3).
+//
+// Precision (the FP32-factor / FP64-refinement form): the working copy of the matrix is
+// stored in T (float, or double for the plain-FP64 batched form); the panel's strong RRQR
+// (QR with column pivoting, the tau test and interchanges, Algorithm 2), the diagonal-block
+// GEPP and the refinement residual r = b - A x are computed in FP64.  The Schur update,
+// U12 and the final multipliers are computed in T.  Substitutions use FP64 arithmetic on
+// the T factors.
+//
+// Inside a CTA: the panel (m x w, w <= 32) lives in shared memory in FP64; a team of 4
+// threads works on one panel row; argmax keys compare non-negative doubles by their IEEE
+// bit patterns.  The trailing matrix stays in the CTA's global scratch (L2-resident for
+// these sizes).  No grid-wide synchronization is used: CTAs never wait on one another.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace prrp {
+
+namespace {
+
+constexpr int kBT = 256;          // threads per batch CTA
+constexpr int kBW = 32;           // largest panel width in the batched kernel
+constexpr int kBTeams = kBT / kTeam;
+
+struct BKey {
+  unsigned long long v;
+  int k1, k2;
+};
+
+__device__ __forceinline__ bool bbetter(const BKey& a, const BKey& b) {
+  if (a.v != b.v) return a.v > b.v;
+  if (a.k1 != b.k1) return a.k1 < b.k1;
+  return a.k2 < b.k2;
+}
+
+__device__ __forceinline__ BKey bshfl(const BKey& c, int m, unsigned mask) {
+  BKey o;
+  o.v = __shfl_xor_sync(mask, c.v, m);
+  o.k1 = __shfl_xor_sync(mask, c.k1, m);
+  o.k2 = __shfl_xor_sync(mask, c.k2, m);
+  return o;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x));
+}
+
+// Block-wide best key, returned to every thread (two __syncthreads).
+__device__ BKey block_best_key(BKey c, BKey* s_w) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const BKey o = bshfl(c, off, 0xffffffffu);
+    if (bbetter(o, c)) c = o;
+  }
+  if (lane == 0) s_w[warp] = c;
+  __syncthreads();
+  BKey r = s_w[0];
+  for (int k = 1; k < kBT / 32; ++k)
+    if (bbetter(s_w[k], r)) r = s_w[k];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double bteam_sum(double s) {
+  const unsigned mask = 0xfu << ((threadIdx.x & 31) & ~3);
+  s += __shfl_xor_sync(mask, s, 1);
+  s += __shfl_xor_sync(mask, s, 2);
+  return s;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int k = 0; k < kBT / 32; ++k) r += s_red[k];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int k = 0; k < kBT / 32; ++k) r = fmax(r, s_red[k]);
+  __syncthreads();
+  return r;
+}
+
+// Strong RRQR of the transposed m x w panel held in Ps (FP64, stride sp), Algorithm 2.
+// On return pos[r] is the final position of panel row r and rows with pos >= w hold their
+// multipliers M(:, pos - w) = (R11^-1 R12)(:, .).  Returns 0, or a prrp_status.
+__device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, int max_swaps,
+                                  double* nrm, double* nref, int* pos, double* Rs, double* rdiag,
+                                  BKey* s_w, int* swaps_out) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int tl = tid & (kTeam - 1), team = tid / kTeam;
+  const unsigned tmask = 0xfu << (lane & ~3);
+  for (int r = team; r < m; r += kBTeams) {
+    double s = 0.0;
+    for (int i = tl; i < w; i += kTeam) { const double x = Ps[r * sp + i]; s = fma(x, x, s); }
+    s = bteam_sum(s);
+    if (tl == 0) { nrm[r] = s; nref[r] = s; pos[r] = r; }
+  }
+  __syncthreads();
+  for (int t = 0; t < w; ++t) {
+    BKey c{0ull, 0x7fffffff, 0};
+    for (int r = tid; r < m; r += kBT)
+      if (pos[r] >= t) {
+        BKey d{dbits(fmax(nrm[r], 0.0)), pos[r], r};
+        if (bbetter(d, c)) c = d;
+      }
+    const BKey g = block_best_key(c, s_w);
+    if (g.v == 0ull) return PRRP_ERR_SINGULAR;
+    const int rw = g.k2, pw = g.k1;
+    const double* xw = Ps + rw * sp;
+    const double x0 = xw[t];
+    const double normx = sqrt(__longlong_as_double(static_cast<long long>(g.v)));
+    const double alpha = (x0 >= 0.0) ? -normx : normx;
+    const double beta = 1.0 / (normx * (normx + fabs(x0)));
+    const double v0 = x0 - alpha;
+    for (int i = tid; i < t; i += kBT) Rs[i * kBW + t] = xw[i];
+    if (tid == 0) Rs[t * kBW + t] = alpha;
+    // the winner row's values are read by every team below; it is itself not updated
+    for (int r = team; r < m; r += kBTeams) {
+      const int pr = pos[r];
+      if (pr < t || r == rw) continue;
+      double* x = Ps + r * sp;
+      double sd = 0.0;
+      for (int i = t + tl; i < w; i += kTeam) sd = fma(i == t ? v0 : xw[i], x[i], sd);
+      sd = bteam_sum(sd);
+      const double f = beta * sd;
+      double xt = 0.0;
+      for (int i = t + tl; i < w; i += kTeam) {
+        const double y = fma(-f, i == t ? v0 : xw[i], x[i]);
+        x[i] = y;
+        if (i == t) xt = y;
+      }
+      xt = __shfl_sync(tmask, xt, lane & ~3);
+      double n2 = fma(-xt, xt, nrm[r]);
+      if (!(n2 > 1e-4 * nref[r])) {
+        double e2 = 0.0;
+        for (int i = t + 1 + tl; i < w; i += kTeam) e2 = fma(x[i], x[i], e2);
+        n2 = bteam_sum(e2);
+        if (tl == 0) nref[r] = n2;
+      }
+      __syncwarp(tmask);
+      if (tl == 0) { nrm[r] = n2; pos[r] = (pr == t) ? pw : pr; }
+    }
+    __syncthreads();
+    if (tid == 0) pos[rw] = t;
+    __syncthreads();
+  }
+  for (int i = tid; i < w; i += kBT) rdiag[i] = 1.0 / Rs[i * kBW + i];
+  __syncthreads();
+  for (int r = team; r < m; r += kBTeams) {
+    if (pos[r] < w) continue;
+    double* b = Ps + r * sp;
+    for (int i = w - 1; i >= 0; --i) {
+      const int owner = i & (kTeam - 1);
+      double mi = 0.0;
+      if (tl == owner) mi = b[i] * rdiag[i];
+      mi = __shfl_sync(tmask, mi, (lane & ~3) | owner);
+      if (tl == owner) b[i] = mi;
+      for (int k = tl; k < i; k += kTeam) b[k] = fma(-Rs[k * kBW + i], mi, b[k]);
+    }
+  }
+  __syncthreads();
+  int swaps = 0;
+  for (;;) {
+    BKey c{0ull, 0x7fffffff, 0x7fffffff};
+    for (int r = team; r < m; r += kBTeams) {
+      const int pr = pos[r];
+      if (pr < w) continue;
+      BKey d{0ull, pr - w, 0x7fffffff};
+      for (int i = tl; i < w; i += kTeam) {
+        const unsigned long long a = dbits(fabs(Ps[r * sp + i]));
+        if (a > d.v || d.k2 == 0x7fffffff) { d.v = a; d.k2 = i; }
+      }
+      BKey o = bshfl(d, 1, tmask);
+      if (bbetter(o, d)) d = o;
+      o = bshfl(d, 2, tmask);
+      if (bbetter(o, d)) d = o;
+      if (bbetter(d, c)) c = d;
+    }
+    const BKey g = block_best_key(c, s_w);
+    if (g.k1 == 0x7fffffff || !(__longlong_as_double(static_cast<long long>(g.v)) > tau)) break;
+    if (swaps >= max_swaps) return PRRP_ERR_SWAP_LIMIT;
+    const int js = g.k1, is = g.k2;
+    // the entering row's column M(:, js), staged before any row changes
+    int rin = -1;
+    for (int r = tid; r < m; r += kBT)
+      if (pos[r] == w + js) rin = r;
+    double* colv = rdiag;                                  // reuse: w doubles
+    __syncthreads();
+    if (rin >= 0)
+      for (int i = 0; i < w; ++i) colv[i] = Ps[rin * sp + i];
+    __syncthreads();
+    const double mu = colv[is];
+    for (int r = team; r < m; r += kBTeams) {
+      const int pr = pos[r];
+      double* x = Ps + r * sp;
+      if (pr == w + js) {
+        if (tl == 0) pos[r] = is;
+      } else if (pr == is) {
+        for (int k = tl; k < w; k += kTeam) x[k] = (k == is) ? 1.0 / mu : -colv[k] / mu;
+        __syncwarp(tmask);
+        if (tl == 0) pos[r] = w + js;
+      } else if (pr >= w) {
+        const int owner = is & (kTeam - 1);
+        double f = 0.0;
+        if (tl == owner) f = x[is] / mu;
+        f = __shfl_sync(tmask, f, (lane & ~3) | owner);
+        for (int k = tl; k < w; k += kTeam) x[k] = (k == is) ? f : fma(-f, colv[k], x[k]);
+      }
+    }
+    ++swaps;
+    __syncthreads();
+  }
+  *swaps_out = swaps;
+  return 0;
+}
+
+template <typename T>
+struct BatchArgs {
+  int count;
+  const int* order;          // systems in processing order (largest first)
+  const int* n;
+  const double* const* A;    // FP64 input matrices (not modified)
+  const int* lda;
+  const int* nrhs;
+  double* const* B;          // right-hand sides, overwritten by the solutions
+  const int* ldb;
+  int* const* perm_out;      // optional per-system permutation outputs
+  int b;
+  double tau;
+  int max_swaps;
+  int refine_max_iter;
+  double refine_target;
+  int nmax;
+  T* wsW;                    // per CTA: nmax * nmax
+  T* wsT;                    // per CTA: tmp_rows * nmax
+  int tmp_rows;
+  double* wsV;               // per CTA: 5 * nmax doubles
+  int* wsI;                  // per CTA: 3 * nmax ints (perm, row moves)
+  int* status;               // per system
+  int* iters;
+  double* eta0;
+  double* eta;
+  unsigned* counter;         // work list head
+};
+
+// x (FP64, length n) <- U^-1 L^-1 P y for the T factors in W (ld n); y = b or r in v, x out.
+template <typename T>
+__device__ void batch_lu_solve(const T* W, int n, const int* perm, const double* rhs, double* x,
+                               double* s_red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < n; i += kBT) x[i] = rhs[perm[i]];
+  __syncthreads();
+  // forward substitution, blocks of 32 rows: warp 0 solves the block, all update below
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int kb = min(32, n - k0);
+    if (warp == 0) {
+      double y = lane < kb ? x[k0 + lane] : 0.0;
+      for (int k = 0; k < kb; ++k) {
+        const double xk = __shfl_sync(0xffffffffu, y, k);
+        if (lane > k && lane < kb) y = fma(-static_cast<double>(W[(long long)(k0 + lane) * n + k0 + k]), xk, y);
+      }
+      if (lane < kb) x[k0 + lane] = y;
+    }
+    __syncthreads();
+    for (int i = k0 + kb + tid; i < n; i += kBT) {
+      const T* row = W + (long long)i * n + k0;
+      double acc = 0.0;
+      for (int k = 0; k < kb; ++k) acc = fma(static_cast<double>(row[k]), x[k0 + k], acc);
+      x[i] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int kend = n; kend > 0; kend -= 32) {
+    const int k0 = max(0, kend - 32), kb = kend - k0;
+    if (warp == 0) {
+      double y = lane < kb ? x[k0 + lane] : 0.0;
+      for (int k = kb - 1; k >= 0; --k) {
+        if (lane == k) y = y / static_cast<double>(W[(long long)(k0 + k) * n + k0 + k]);
+        const double xk = __shfl_sync(0xffffffffu, y, k);
+        if (lane < k) y = fma(-static_cast<double>(W[(long long)(k0 + lane) * n + k0 + k]), xk, y);
+      }
+      if (lane < kb) x[k0 + lane] = y;
+    }
+    __syncthreads();
+    for (int i = tid; i < k0; i += kBT) {
+      const T* row = W + (long long)i * n + k0;
+      double acc = 0.0;
+      for (int k = 0; k < kb; ++k) acc = fma(static_cast<double>(row[k]), x[k0 + k], acc);
+      x[i] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ BKey s_w[kBT / 32];
+  __shared__ double s_red[kBT / 32];
+  __shared__ int s_sys, s_status, s_np;
+  __shared__ double Rs[kBW * kBW];
+  __shared__ double rdiag[kBW];
+  __shared__ int ipiv[kBW];
+  __shared__ double Dg[kBW * (kBW + 1)];
+  const int tid = threadIdx.x;
+  T* W = a.wsW + (size_t)blockIdx.x * a.nmax * a.nmax;
+  T* Tmp = a.wsT + (size_t)blockIdx.x * a.tmp_rows * a.nmax;
+  double* V = a.wsV + (size_t)blockIdx.x * 5 * a.nmax;
+  int* perm = a.wsI + (size_t)blockIdx.x * 3 * a.nmax;
+  int* mv = perm + a.nmax;                          // row moves (dst, src) of one panel: <= 2m ints
+
+  for (;;) {
+    if (tid == 0) s_sys = static_cast<int>(atomicAdd(a.counter, 1u));
+    __syncthreads();
+    const int qi = s_sys;
+    if (qi >= a.count) return;
+    const int sys = a.order[qi];
+    const int n = a.n[sys], lda = a.lda[sys];
+    const double* A = a.A[sys];
+    if (tid == 0) s_status = 0;
+    int swaps_total = 0;
+    // ---- working copy and permutation
+    for (long long e = tid; e < (long long)n * n; e += kBT) {
+      const int i = static_cast<int>(e / n), j = static_cast<int>(e - (long long)i * n);
+      const double v = A[(long long)i * lda + j];
+      if (!isfinite(v)) s_status = PRRP_ERR_NONFINITE;
+      W[e] = static_cast<T>(v);
+    }
+    for (int i = tid; i < n; i += kBT) perm[i] = i;
+    __syncthreads();
+    // ---- Algorithm 1
+    for (int k0 = 0; k0 < n && s_status == 0; k0 += a.b) {
+      const int w = min(a.b, n - k0), m = n - k0;
+      const int sp = w + 1;
+      double* Ps = reinterpret_cast<double*>(smem_raw);
+      double* nrm = Ps + (size_t)m * sp;
+      double* nref = nrm + m;
+      int* pos = reinterpret_cast<int*>(nref + m);
+      for (int e = tid; e < m * w; e += kBT) {
+        const int r = e / w, c = e - r * w;
+        Ps[r * sp + c] = static_cast<double>(W[(long long)(k0 + r) * n + k0 + c]);
+      }
+      __syncthreads();
+      int sw = 0;
+      const int st = batch_panel_select(Ps, sp, m, w, a.tau, a.max_swaps, nrm, nref, pos, Rs, rdiag,
+                                        s_w, &sw);
+      if (st != 0) {
+        if (tid == 0) s_status = st;
+        __syncthreads();
+        break;
+      }
+      swaps_total += sw;
+      // row moves: positions that changed, staged whole through Tmp (all n columns)
+      if (tid == 0) s_np = 0;
+      __syncthreads();
+      for (int r = tid; r < m; r += kBT)
+        if (pos[r] != r) {
+          const int k = atomicAdd(&s_np, 1);
+          mv[2 * k] = pos[r];
+          mv[2 * k + 1] = r;
+        }
+      __syncthreads();
+      const int np = s_np;
+      // every source row is read before any destination is written: np <= 2 (w + swaps)
+      // and np <= m, and Tmp holds min(nmax, 2 (b + max_swaps) + 2) rows
+      if (np > a.tmp_rows) {
+        if (tid == 0) s_status = PRRP_ERR_UNSUPPORTED;
+        __syncthreads();
+        break;
+      }
+      for (int e = tid; e < np * n; e += kBT) {
+        const int k = e / n, j = e - k * n;
+        Tmp[(long long)k * n + j] = W[(long long)(k0 + mv[2 * k + 1]) * n + j];
+      }
+      __syncthreads();
+      for (int e = tid; e < np * n; e += kBT) {
+        const int k = e / n, j = e - k * n;
+        W[(long long)(k0 + mv[2 * k]) * n + j] = Tmp[(long long)k * n + j];
+      }
+      __syncthreads();
+      if (tid == 0) {                          // perm follows the same moves
+        for (int k = 0; k < np; ++k) mv[2 * k + 1] = perm[k0 + mv[2 * k + 1]];
+        for (int k = 0; k < np; ++k) perm[k0 + mv[2 * k]] = mv[2 * k + 1];
+      }
+      // block multipliers L21 into the strip of the rows below the block
+      for (int e = tid; e < m * w; e += kBT) {
+        const int r = e / w, c = e - r * w;
+        const int pr = pos[r];
+        if (pr >= w) W[(long long)(k0 + pr) * n + k0 + c] = static_cast<T>(Ps[r * sp + c]);
+      }
+      __syncthreads();
+      // Schur update A22 -= L21 A12 in T: A12 (w x nc) staged in shared memory (the
+      // panel's space is free now), one warp per row of L21 (held in registers), lanes
+      // along the columns
+      const int nc = n - k0 - w;
+      T* Us = reinterpret_cast<T*>(smem_raw);
+      for (int e = tid; e < w * nc; e += kBT) {
+        const int k = e / nc, j = e - k * nc;
+        Us[e] = W[(long long)(k0 + k) * n + k0 + w + j];
+      }
+      __syncthreads();
+      {
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int i = warp; i < m - w; i += kBT / 32) {
+          T lr[kBW];
+          const T* l = W + (long long)(k0 + w + i) * n + k0;
+#pragma unroll
+          for (int k = 0; k < kBW; ++k) lr[k] = k < w ? l[k] : T(0);
+          T* crow = W + (long long)(k0 + w + i) * n + k0 + w;
+          for (int j = lane; j < nc; j += 32) {
+            T acc = 0;
+#pragma unroll
+            for (int k = 0; k < kBW; ++k)
+              if (k < w) acc = fma(lr[k], Us[k * nc + j], acc);
+            crow[j] -= acc;
+          }
+        }
+      }
+      __syncthreads();
+      // GEPP on the diagonal block in FP64
+      for (int e = tid; e < w * w; e += kBT) {
+        const int i = e / w, j = e - i * w;
+        Dg[i * (kBW + 1) + j] = static_cast<double>(W[(long long)(k0 + i) * n + k0 + j]);
+      }
+      __syncthreads();
+      for (int t = 0; t < w; ++t) {
+        if (tid == 0) {
+          int p = t;
+          double bv = fabs(Dg[t * (kBW + 1) + t]);
+          for (int i = t + 1; i < w; ++i) {
+            const double v = fabs(Dg[i * (kBW + 1) + t]);
+            if (v > bv) { bv = v; p = i; }
+          }
+          ipiv[t] = bv > 0.0 ? p : -1;
+        }
+        __syncthreads();
+        const int p = ipiv[t];
+        if (p < 0) {                                   // zero pivot in the diagonal block
+          if (tid == 0) s_status = PRRP_ERR_SINGULAR;
+          break;
+        }
+        if (p != t)
+          for (int j = tid; j < w; j += kBT) {
+            const double x = Dg[t * (kBW + 1) + j];
+            Dg[t * (kBW + 1) + j] = Dg[p * (kBW + 1) + j];
+            Dg[p * (kBW + 1) + j] = x;
+          }
+        __syncthreads();
+        const double rp = 1.0 / Dg[t * (kBW + 1) + t];
+        for (int e = tid; e < (w - t - 1) * (w - t); e += kBT) {
+          const int i = t + 1 + e / (w - t), j = t + e % (w - t);
+          const double l = Dg[i * (kBW + 1) + t] * rp;
+          if (j > t) Dg[i * (kBW + 1) + j] = fma(-l, Dg[t * (kBW + 1) + j], Dg[i * (kBW + 1) + j]);
+        }
+        __syncthreads();
+        for (int i = t + 1 + tid; i < w; i += kBT) Dg[i * (kBW + 1) + t] *= rp;
+        __syncthreads();
+      }
+      __syncthreads();
+      if (s_status != 0) break;
+      for (int e = tid; e < w * w; e += kBT) {
+        const int i = e / w, j = e - i * w;
+        W[(long long)(k0 + i) * n + k0 + j] = static_cast<T>(Dg[i * (kBW + 1) + j]);
+      }
+      __syncthreads();
+      if (tid == 0)
+        for (int t = 0; t < w; ++t) {
+          const int p = ipiv[t];
+          if (p != t) { const int x = perm[k0 + t]; perm[k0 + t] = perm[k0 + p]; perm[k0 + p] = x; }
+        }
+      // block-row interchanges outside the block and U12 = L11^-1 A12, one column per thread
+      for (int j = tid; j < n; j += kBT) {
+        if (j >= k0 && j < k0 + w) continue;
+        for (int t = 0; t < w; ++t) {
+          const int p = ipiv[t];
+          if (p != t) {
+            const T x = W[(long long)(k0 + t) * n + j];
+            W[(long long)(k0 + t) * n + j] = W[(long long)(k0 + p) * n + j];
+            W[(long long)(k0 + p) * n + j] = x;
+          }
+        }
+        if (j >= k0 + w)                             // U12 = L11^-1 A12 in T
+          for (int k = 0; k < w; ++k) {
+            const T xk = W[(long long)(k0 + k) * n + j];
+            for (int i = k + 1; i < w; ++i)
+              W[(long long)(k0 + i) * n + j] =
+                  fma(-static_cast<T>(Dg[i * (kBW + 1) + k]), xk, W[(long long)(k0 + i) * n + j]);
+          }
+      }
+      // final multipliers of the rows below: (L21 with GEPP's column interchanges) * L11
+      for (int r = k0 + w + tid; r < n; r += kBT) {
+        T* row = W + (long long)r * n + k0;
+        for (int t = 0; t < w; ++t) {
+          const int p = ipiv[t];
+          if (p != t) { const T x = row[t]; row[t] = row[p]; row[p] = x; }
+        }
+        for (int c = 0; c < w; ++c) {                // row * L11 in T
+          T acc = row[c];
+          for (int i = c + 1; i < w; ++i) acc = fma(row[i], static_cast<T>(Dg[i * (kBW + 1) + c]), acc);
+          row[c] = acc;
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    const int fstat = s_status;
+    if (a.perm_out && a.perm_out[sys] && fstat == 0)
+      for (int i = tid; i < n; i += kBT) a.perm_out[sys][i] = perm[i];
+    // ---- solve and FP64 refinement, one right-hand side at a time
+    double* xv = V;
+    double* rv = V + a.nmax;
+    double* dv = rv + a.nmax;
+    const int nr = a.nrhs[sys], ldb = a.ldb[sys];
+    double* Bp = a.B[sys];
+    double e0max = 0.0, emax = 0.0;
+    int itmax = 0;
+    double anorm = 0.0;
+    if (fstat == 0) {
+      double cm = 0.0;
+      for (int j = tid; j < n; j += kBT) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += fabs(A[(long long)i * lda + j]);
+        cm = fmax(cm, s);
+      }
+      anorm = block_max(cm, s_red);
+    }
+    for (int c = 0; c < nr && fstat == 0; ++c) {
+      double* bcol = dv;                                   // the right-hand side, packed
+      for (int i = tid; i < n; i += kBT) bcol[i] = Bp[(long long)i * ldb + c];
+      __syncthreads();
+      batch_lu_solve<T>(W, n, perm, bcol, xv, s_red);
+      double eta = 0.0, eta_first = 0.0;
+      int it = 0;
+      for (;;) {
+        // r = b - A x in FP64 and eta = ||r||_1 / (||A||_1 ||x||_1 + ||b||_1)
+        double rs = 0.0, xs = 0.0, bs = 0.0;
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int i = warp; i < n; i += kBT / 32) {        // one warp per row, coalesced
+          const double* arow = A + (long long)i * lda;
+          double acc = 0.0;
+          for (int k = lane; k < n; k += 32) acc = fma(arow[k], xv[k], acc);
+          for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+          if (lane == 0) {
+            const double r = bcol[i] - acc;
+            rv[i] = r;
+            rs += fabs(r);
+          }
+        }
+        for (int i = tid; i < n; i += kBT) {
+          xs += fabs(xv[i]);
+          bs += fabs(bcol[i]);
+        }
+        rs = block_sum(rs, s_red);
+        xs = block_sum(xs, s_red);
+        bs = block_sum(bs, s_red);
+        const double den = anorm * xs + bs;
+        const double e = den > 0.0 ? rs / den : (rs > 0.0 ? INFINITY : 0.0);
+        if (it == 0) eta_first = e;
+        if (it > 0 && e > eta / 2) {                      // stagnation: keep the better
+          if (e > eta)
+            for (int i = tid; i < n; i += kBT) xv[i] -= V[4 * a.nmax + i];
+          else
+            eta = e;
+          __syncthreads();
+          break;
+        }
+        eta = e;
+        if (eta <= a.refine_target || it >= a.refine_max_iter) break;
+        double* corr = V + 4 * a.nmax;
+        double* rhs_r = V + 3 * a.nmax;
+        for (int i = tid; i < n; i += kBT) rhs_r[i] = rv[i];
+        __syncthreads();
+        batch_lu_solve<T>(W, n, perm, rhs_r, corr, s_red);
+        for (int i = tid; i < n; i += kBT) xv[i] += corr[i];
+        __syncthreads();
+        ++it;
+      }
+      for (int i = tid; i < n; i += kBT) Bp[(long long)i * ldb + c] = xv[i];
+      __syncthreads();
+      e0max = fmax(e0max, eta_first);
+      emax = fmax(emax, eta);
+      itmax = max(itmax, it);
+    }
+    if (tid == 0) {
+      a.status[sys] = fstat;
+      a.iters[sys] = itmax;
+      a.eta0[sys] = fstat == 0 ? e0max : -1.0;
+      a.eta[sys] = fstat == 0 ? emax : -1.0;
+    }
+    (void)swaps_total;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t batch_smem_bytes(int nmax, int b) {
+  return (size_t)nmax * (b + 1) * sizeof(double) + (size_t)nmax * (2 * sizeof(double) + sizeof(int)) + 64;
+}
+
+cudaError_t launch_batch(int fp64, int grid, const BatchLaunch& L, cudaStream_t s) {
+  const size_t smem = batch_smem_bytes(L.nmax, L.b);
+  if (fp64) {
+    BatchArgs<double> a{L.count, L.order, L.n, L.A, L.lda, L.nrhs, L.B, L.ldb, L.perm_out, L.b, L.tau, L.max_swaps,
+                        L.refine_max_iter, L.refine_target, L.nmax, static_cast<double*>(L.wsW),
+                        static_cast<double*>(L.wsT), L.tmp_rows, L.wsV, L.wsI, L.status, L.iters,
+                        L.eta0, L.eta, L.counter};
+    batch_kernel<double><<<grid, kBT, smem, s>>>(a);
+  } else {
+    BatchArgs<float> a{L.count, L.order, L.n, L.A, L.lda, L.nrhs, L.B, L.ldb, L.perm_out, L.b, L.tau, L.max_swaps,
+                       L.refine_max_iter, L.refine_target, L.nmax, static_cast<float*>(L.wsW),
+                       static_cast<float*>(L.wsT), L.tmp_rows, L.wsV, L.wsI, L.status, L.iters,
+                       L.eta0, L.eta, L.counter};
+    batch_kernel<float><<<grid, kBT, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+int batch_max_width() { return kBW; }
+
+// Shared-memory opt-in for the batch kernels (outside any stream capture).
+cudaError_t prepare_batch(int nmax, int b) {
+  (void)nmax;
+  (void)b;
+  cudaError_t e = smem_optin(batch_kernel<double>);
+  if (e != cudaSuccess) return e;
+  return smem_optin(batch_kernel<float>);
+}
+
+// Synthetic systems for the autotuner: iid entries from a counter hash (Weyl sequence,
+// mapped to [-1, 1)), diagonally loaded so every sample is comfortably nonsingular.
+__global__ void batch_fill_kernel(double* A, int n, int count, double* B, unsigned seed) {
+  const long long total = (long long)count * n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)e * 0x9E3779B97F4A7C15ull + seed;
+    z ^= z >> 31; z *= 0xBF58476D1CE4E5B9ull; z ^= z >> 29;
+    double v = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    const long long r = (e / n) % n, c = e % n;
+    if (r == c) v += 4.0;
+    A[e] = v;
+  }
+  const long long tb = (long long)count * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tb;
+       e += (long long)gridDim.x * blockDim.x)
+    B[e] = 1.0;
+}
+
+cudaError_t launch_batch_fill(double* A, int n, int count, double* B, cudaStream_t s) {
+  batch_fill_kernel<<<1024, 256, 0, s>>>(A, n, count, B, 12345u);
+  return cudaGetLastError();
+}
+
+}  // namespace prrp

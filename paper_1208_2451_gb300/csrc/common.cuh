@@ -36,6 +36,18 @@ struct DevState {
   unsigned int pad2;
 };
 
+// Dynamic shared memory opt-in for a kernel.  The attribute is process-wide, so every
+// launcher sets the same value for a given kernel, the most the device allows next to the
+// kernel's static shared memory, whatever its own launch needs: concurrent launches from
+// several host threads then never see another thread's smaller limit.  Occupancy is
+// decided by each launch's actual size.  (227 KB per block on sm_103a.)
+constexpr int kSmemOptin = 232448;
+cudaError_t smem_optin_ptr(const void* kernel);   // api.cpp: cached per kernel
+template <typename F>
+inline cudaError_t smem_optin(F* kernel) {
+  return smem_optin_ptr(reinterpret_cast<const void*>(kernel));
+}
+
 __device__ __forceinline__ int dev_status(const DevState* st) {
   return *((volatile const int*)&st->status);
 }

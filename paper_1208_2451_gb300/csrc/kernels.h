@@ -66,6 +66,40 @@ cudaError_t launch_lfix(double* A, long long lda, int n, int k0, int w, const do
 cudaError_t launch_iota(int* p, int n, cudaStream_t s);
 cudaError_t launch_wait_selftest(DevState* st, cudaStream_t s);
 
+// Batched small systems (batch.cu): one CTA per system, persistent over a work list.
+struct BatchLaunch {
+  int count;
+  const int* order;
+  const int* n;
+  const double* const* A;
+  const int* lda;
+  const int* nrhs;
+  double* const* B;
+  const int* ldb;
+  int* const* perm_out;
+  int b;
+  double tau;
+  int max_swaps;
+  int refine_max_iter;
+  double refine_target;
+  int nmax;
+  void* wsW;
+  void* wsT;
+  int tmp_rows;
+  double* wsV;
+  int* wsI;
+  int* status;
+  int* iters;
+  double* eta0;
+  double* eta;
+  unsigned* counter;
+};
+size_t batch_smem_bytes(int nmax, int b);
+int batch_max_width();
+cudaError_t prepare_batch(int nmax, int b);
+cudaError_t launch_batch(int fp64, int grid, const BatchLaunch& L, cudaStream_t s);
+cudaError_t launch_batch_fill(double* A, int n, int count, double* B, cudaStream_t s);
+
 // Solve kernels (solve.cu).
 cudaError_t launch_norm1(const double* A, long long lda, int n, double* out, cudaStream_t s);
 cudaError_t launch_gather_rows(const double* B, long long ldb, const int* perm, int n, int nrhs,

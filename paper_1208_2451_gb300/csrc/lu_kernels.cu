@@ -95,8 +95,7 @@ __global__ void __launch_bounds__(256) permute_kernel(double* __restrict__ A, lo
 cudaError_t launch_permute(double* A, long long lda, int n, int k0, const int* pairs,
                            int max_pairs, int* perm, DevState* st, cudaStream_t s) {
   const size_t smem = (size_t)max_pairs * kPermCols * sizeof(double) + (size_t)max_pairs * sizeof(int);
-  cudaError_t e = cudaFuncSetAttribute(permute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = smem_optin(permute_kernel);
   if (e != cudaSuccess) return e;
   const int grid = (n + kPermCols - 1) / kPermCols;
   permute_kernel<<<grid, 256, smem, s>>>(A, lda, n, k0, pairs, max_pairs, perm, st);
@@ -196,8 +195,7 @@ static cudaError_t launch_gemm_tile(int m, int n, int k, const double* L, long l
                                     const double* U, long long ldu, double* C, long long ldc,
                                     DevState* st, int track, int grid, cudaStream_t s) {
   const size_t smem = (size_t)kGemmKC * ((BM + 2) + (BN + 2)) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(gemm_fp64_kernel<BM, BN>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_optin(gemm_fp64_kernel<BM, BN>);
   if (e != cudaSuccess) return e;
   gemm_fp64_kernel<BM, BN><<<grid, 256, smem, s>>>(m, n, k, L, ldl, U, ldu, C, ldc, st, track);
   return cudaGetLastError();
@@ -309,8 +307,7 @@ __global__ void __launch_bounds__(256) diag_gepp_kernel(double* __restrict__ A, 
 cudaError_t launch_diag_gepp(double* A, long long lda, int k0, int w, int* ipiv, int* perm,
                              DevState* st, cudaStream_t s) {
   const size_t smem = (size_t)w * (w + 1) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(diag_gepp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = smem_optin(diag_gepp_kernel);
   if (e != cudaSuccess) return e;
   diag_gepp_kernel<<<1, 256, smem, s>>>(A, lda, k0, w, ipiv, perm, st);
   return cudaGetLastError();
@@ -475,8 +472,7 @@ cudaError_t launch_u12(double* A, long long lda, int n, int k0, int w, const int
     return cudaGetLastError();
   }
   const size_t smem = (size_t)(w * w + w * kU12Cols) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(u12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = smem_optin(u12_kernel);
   if (e != cudaSuccess) return e;
   u12_kernel<<<left + right, kU12Cols, smem, s>>>(A, lda, n, k0, w, ipiv, left, st);
   return cudaGetLastError();
@@ -541,8 +537,7 @@ cudaError_t launch_lfix(double* A, long long lda, int n, int k0, int w, const do
     return cudaGetLastError();
   }
   const size_t smem = (size_t)(w * w + kLfixRows * (w + 1)) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(lfix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = smem_optin(lfix_kernel);
   if (e != cudaSuccess) return e;
   lfix_kernel<<<(rows + kLfixRows - 1) / kLfixRows, kLfixRows, smem, s>>>(A, lda, n, k0, w, L21,
                                                                           ldl21, ipiv, st);

@@ -27,12 +27,22 @@
 //
 // Outputs: L21 = M^T (row w + r of the final order -> L21 row r), the final position of
 // every panel row, and a list of (destination, source) row moves for the permute kernel.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace prrp {
 
 namespace {
+
+// Cooperative panel grids from different streams or contexts must not be resident at the
+// same time: two partially resident grids could each wait at their grid barrier for CTAs
+// that the other one keeps off the SMs.  Every panel launch on a device therefore waits
+// for the previous one (on any stream) through this per-device event chain; other kernels
+// still overlap with them freely.
+std::mutex g_coop_mu;
+cudaEvent_t g_coop_done[64] = {};
 
 // A proposal in an argmax.  The value is a non-negative double (a squared norm or |M_ij|)
 // kept as its IEEE bit pattern: for x, y >= 0, x < y exactly when bits(x) < bits(y), so
@@ -376,8 +386,7 @@ static size_t panel_smem_bytes(int rpc) {
 template <int W>
 static cudaError_t launch_panel_w(PanelParams p, int G, cudaStream_t stream) {
   const size_t smem = panel_smem_bytes<W>(p.rows_per_cta);
-  cudaError_t e = cudaFuncSetAttribute(panel_rrqr_kernel<W>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_optin(panel_rrqr_kernel<W>);
   if (e != cudaSuccess) return e;
   void* args[] = {&p};
   return cudaLaunchCooperativeKernel((const void*)panel_rrqr_kernel<W>, dim3(G),
@@ -396,12 +405,25 @@ size_t panel_smem_for(int w, int rpc) {
 }
 
 cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t stream) {
-  switch (panel_width_class(p.w)) {
-    case 16: return launch_panel_w<16>(p, G, stream);
-    case 32: return launch_panel_w<32>(p, G, stream);
-    case 64: return launch_panel_w<64>(p, G, stream);
-    default: return launch_panel_w<128>(p, G, stream);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_coop_mu);
+  if (!g_coop_done[dev]) {
+    e = cudaEventCreateWithFlags(&g_coop_done[dev], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
   }
+  e = cudaStreamWaitEvent(stream, g_coop_done[dev], 0);
+  if (e != cudaSuccess) return e;
+  switch (panel_width_class(p.w)) {
+    case 16: e = launch_panel_w<16>(p, G, stream); break;
+    case 32: e = launch_panel_w<32>(p, G, stream); break;
+    case 64: e = launch_panel_w<64>(p, G, stream); break;
+    default: e = launch_panel_w<128>(p, G, stream); break;
+  }
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(g_coop_done[dev], stream);
 }
 
 }  // namespace prrp

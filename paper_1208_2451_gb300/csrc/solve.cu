@@ -138,15 +138,15 @@ cudaError_t launch_trsv_upper(const double* LU, long long lda, int n, double* Y,
   return trsv(LU, lda, n, Y, nrhs, false, s);
 }
 
-// R = B - A X (FP64), one CTA per row; norms[c] += |r_c| (1-norm numerators), and
-// norms[nrhs + c] += |x_c| over this CTA's row (for eta), norms[2 nrhs + c] += |b_c|.
+// R = B - A X (FP64), one CTA per row (coalesced row reads).  The 1-norm numerators of
+// eta are reduced afterwards by residual_norms_kernel in a fixed order, so the refinement's
+// stopping decisions, and with them the returned bits, do not depend on scheduling.
 __global__ void __launch_bounds__(kSolveThreads) residual_kernel(const double* __restrict__ A,
                                                                  long long lda, int n,
                                                                  const double* __restrict__ X,
                                                                  long long ldx,
                                                                  int nrhs, const double* __restrict__ B,
-                                                                 long long ldb, double* __restrict__ R,
-                                                                 double* norms) {
+                                                                 long long ldb, double* __restrict__ R) {
   __shared__ double part[kSolveThreads / 32];
   for (int row = blockIdx.x; row < n; row += gridDim.x) {
     const double* a = A + (long long)row * lda;
@@ -159,25 +159,46 @@ __global__ void __launch_bounds__(kSolveThreads) residual_kernel(const double* _
       if (threadIdx.x == 0) {
         double ax = 0.0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) ax += part[q];
-        const double b = B[(long long)row * ldb + c];
-        const double r = b - ax;
-        R[(long long)row * nrhs + c] = r;
-        atomicAdd(&norms[c], fabs(r));
-        atomicAdd(&norms[nrhs + c], fabs(X[(long long)row * ldx + c]));
-        atomicAdd(&norms[2 * nrhs + c], fabs(b));
+        R[(long long)row * nrhs + c] = B[(long long)row * ldb + c] - ax;
       }
       __syncthreads();
     }
   }
 }
 
+// norms[c] = ||R(:,c)||_1, norms[nrhs + c] = ||X(:,c)||_1, norms[2 nrhs + c] = ||B(:,c)||_1;
+// one CTA per column, each thread a fixed stride of rows, then a fixed-order tree.
+__global__ void __launch_bounds__(kSolveThreads) residual_norms_kernel(const double* __restrict__ R, int n,
+                                                                       const double* __restrict__ X, long long ldx,
+                                                                       int nrhs, const double* __restrict__ B,
+                                                                       long long ldb, double* norms) {
+  __shared__ double sr[kSolveThreads], sx[kSolveThreads], sb[kSolveThreads];
+  const int c = blockIdx.x;
+  double r = 0.0, x = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    r += fabs(R[(long long)i * nrhs + c]);
+    x += fabs(X[(long long)i * ldx + c]);
+    b += fabs(B[(long long)i * ldb + c]);
+  }
+  sr[threadIdx.x] = r; sx[threadIdx.x] = x; sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sr[threadIdx.x] += sr[threadIdx.x + h];
+      sx[threadIdx.x] += sx[threadIdx.x + h];
+      sb[threadIdx.x] += sb[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { norms[c] = sr[0]; norms[nrhs + c] = sx[0]; norms[2 * nrhs + c] = sb[0]; }
+}
+
 cudaError_t launch_residual(const double* A, long long lda, int n, const double* X, long long ldx,
                             int nrhs, const double* B, long long ldb, double* R, double* norms,
                             cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 3 * nrhs, s);
-  if (e != cudaSuccess) return e;
-  residual_kernel<<<std::min(n, 152 * 8), kSolveThreads, 0, s>>>(A, lda, n, X, ldx, nrhs, B, ldb, R, norms);
+  if (n == 0 || nrhs == 0) return cudaSuccess;
+  residual_kernel<<<std::min(n, 152 * 8), kSolveThreads, 0, s>>>(A, lda, n, X, ldx, nrhs, B, ldb, R);
+  residual_norms_kernel<<<nrhs, kSolveThreads, 0, s>>>(R, n, X, ldx, nrhs, B, ldb, norms);
   return cudaGetLastError();
 }
 

@@ -4,17 +4,20 @@
 // Accumulation is FP32 in tensor memory; the FP64 trailing matrix is updated in the
 // epilogue (C_ij -= acc_ij in FP64).
 //
-// Per 128 x 128 output tile (one CTA, 4 warps):
-//   * thread 0 issues TMA loads of every operand slice (K-major, 128-byte swizzled rows,
-//     zero-padded to multiples of 128 rows and 64 k) onto one mbarrier, then the
-//     tcgen05.mma instructions (M = 128, N = 128, K = 32 bytes each) into a 128-column
-//     TMEM accumulator and commits them to a second mbarrier;
-//   * the 4 warps read TMEM rows (warp w owns lanes 32w..32w+31), transpose each 32 x 32
-//     block through shared memory and update C with row-contiguous, coalesced FP64 loads
-//     and stores, tracking max |C| for the growth factor.
-// Two CTAs fit per SM, so one CTA's epilogue (HBM-bound) overlaps the other's loads and
-// MMAs.  Every wait is bounded: on expiry the CTA records PRRP_ERR_TIMEOUT, waits again
-// (bounded) for its own copies, frees its tensor memory and returns.
+// One persistent CTA per SM, warp-specialized, over 128 x 128 output tiles:
+//   * warp 0 (one lane) streams every operand slice of a tile with TMA (K-major, 128-byte
+//     swizzled rows, zero-padded to multiples of 128 rows and 64 k) into a ring of
+//     shared-memory stages, each guarded by a full and an empty mbarrier;
+//   * warp 1 (one lane) issues the tcgen05.mma instructions (M = 128, N = 128, 32 bytes of
+//     k each) into one of two 128-column TMEM accumulators, commits each stage's MMAs to
+//     its empty barrier and each finished tile to the accumulator's full barrier;
+//   * warps 2..9 (two per TMEM lane quarter, each half the columns) read the other
+//     accumulator, transpose each 32 x 32 block through shared memory and update C with
+//     row-contiguous, coalesced FP64 loads and stores (32 loads in flight per lane),
+//     tracking max |C| for the growth factor, then release the accumulator.
+// So the HBM-bound epilogue of one tile overlaps the loads and MMAs of the next.  Every
+// wait is bounded: on expiry the CTA records PRRP_ERR_TIMEOUT, frees its tensor memory
+// and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -128,8 +131,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-constexpr int kBM = 128, kBN = 128, kTmemCols = 128;
-constexpr int kStage = 33;   // padded row of the 32 x 32 transpose stage (floats)
+constexpr int kBM = 128, kBN = 128;
+constexpr int kStage = 33;        // padded row of the 32 x 32 transpose stage (floats)
+constexpr int kEpiWarps = 8;      // two warps per TMEM lane quarter, each half the columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kTmemCols = 2 * kBN;  // double-buffered accumulator
 
 template <int MODE>
 struct TcCfg {
@@ -139,32 +145,42 @@ struct TcCfg {
   static constexpr int NP = MODE == 0 ? 1 : 6;         // slice products
   static constexpr int TILE_A = kBM * 128;             // bytes per slice-chunk
   static constexpr int TILE_B = kBN * 128;
-  static constexpr int OPER_BYTES = NS * CH * (TILE_A + TILE_B);
-  static constexpr int SMEM = OPER_BYTES + 4 * 32 * kStage * 4 + 1024;
+  static constexpr int OPER_BYTES = NS * CH * (TILE_A + TILE_B);   // one pipeline stage
+  static constexpr int EPI_BYTES = kEpiWarps * 32 * kStage * 4;
+  // as many operand stages as fit next to the epilogue staging (static shared memory and
+  // the 1 KB alignment slack kept aside)
+  static constexpr int NSTAGE = (kSmemOptin - 512 - EPI_BYTES - 1024) / OPER_BYTES;
+  static constexpr int SMEM = NSTAGE * OPER_BYTES + EPI_BYTES + 1024;
   static constexpr uint32_t IDESC = make_idesc(MODE == 0 ? 2u : 1u, kBM, kBN);
+  static_assert(NSTAGE >= 2, "at least two operand stages");
 };
 
 __constant__ int c_prod_a[6] = {0, 0, 1, 0, 2, 1};
 __constant__ int c_prod_b[6] = {0, 1, 0, 2, 0, 1};
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent, warp-specialized: warp 0 (one lane) streams operand tiles with TMA into an
+// NSTAGE ring, warp 1 (one lane) issues the MMAs into one of two TMEM accumulators, warps
+// 2..9 drain the other accumulator into C.  Tiles are taken round-robin by CTA.
 template <int MODE>
-__global__ void __launch_bounds__(128, 1) tc_update_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                           const __grid_constant__ CUtensorMap tmB,
-                                                           int M, int N, int kblocks, int Mpad, int Npad,
-                                                           double* __restrict__ C, long long ldc,
-                                                           DevState* st, int track) {
+__global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB,
+                                                                int M, int N, int kblocks, int Mpad, int Npad,
+                                                                double* __restrict__ C, long long ldc,
+                                                                DevState* st, int track) {
   using Cfg = TcCfg<MODE>;
+  constexpr int NSTG = Cfg::NSTAGE;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+  __shared__ __align__(8) uint64_t full[NSTG], empty[NSTG], accf[2], acce[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   if (dev_status(st) != 0) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sA = base;
-  uint8_t* sB = base + Cfg::NS * Cfg::CH * Cfg::TILE_A;
-  float* stage = reinterpret_cast<float*>(base + Cfg::OPER_BYTES) + warp * 32 * kStage;
-  const int bm = blockIdx.y * kBM, bn = blockIdx.x * kBN;
+  const int tiles_n = Npad / kBN, tiles = (Mpad / kBM) * tiles_n;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -172,9 +188,9 @@ __global__ void __launch_bounds__(128, 1) tc_update_kernel(const __grid_constant
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {
-    mbar_init(&bar_tma, 1);
-    mbar_init(&bar_mma, 1);
+  if (tid == 32) {
+    for (int i = 0; i < NSTG; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+    for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], kEpiWarps); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
@@ -182,81 +198,109 @@ __global__ void __launch_bounds__(128, 1) tc_update_kernel(const __grid_constant
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-
-  for (int kb = 0; kb < kblocks; ++kb) {
-    if (tid == 0 && !s_fail) {
-      mbar_expect_tx(&bar_tma, Cfg::OPER_BYTES);
-      for (int s = 0; s < Cfg::NS; ++s)
-        for (int c = 0; c < Cfg::CH; ++c) {
-          const int x = kb * 64 + c * (128 / Cfg::EB);
-          tma_load_2d(sA + (s * Cfg::CH + c) * Cfg::TILE_A, &tmA, x, s * Mpad + bm, &bar_tma);
-          tma_load_2d(sB + (s * Cfg::CH + c) * Cfg::TILE_B, &tmB, x, s * Npad + bn, &bar_tma);
-        }
-      if (!mbar_wait_bounded(&bar_tma, kb & 1)) {
-        s_fail = 1;
-        mbar_wait_bounded(&bar_tma, kb & 1);            // let copies still in flight land
-      } else {
-        tc_fence_after();
-        for (int p = 0; p < Cfg::NP; ++p) {
-          const int as = c_prod_a[p], bs = c_prod_b[p];
-          for (int c = 0; c < Cfg::CH; ++c) {
-            const uint64_t ad = sw128_desc(smem_u32(sA + (as * Cfg::CH + c) * Cfg::TILE_A));
-            const uint64_t bd = sw128_desc(smem_u32(sB + (bs * Cfg::CH + c) * Cfg::TILE_B));
-#pragma unroll
-            for (int k = 0; k < 4; ++k)   // 4 MMAs of 32 bytes of k per 128-byte row
-              umma<MODE>(tmem, ad + 2 * k, bd + 2 * k, Cfg::IDESC, (kb | p | c | k) != 0);
-          }
-        }
-        umma_commit(&bar_mma);
-        if (!mbar_wait_bounded(&bar_mma, kb & 1)) s_fail = 1;
-      }
-    }
-    __syncthreads();
-    if (s_fail) break;
-  }
-  if (!s_fail) {
-    // every thread observes the accumulator's completion before reading tensor memory
-    if (!mbar_wait_bounded(&bar_mma, (kblocks - 1) & 1)) s_fail = 1;
-  }
-  tc_fence_after();
   double cmax = 0.0;
-  if (!s_fail) {
-    const int rbase = bm + warp * 32;
-    for (int c0 = 0; c0 < kBN; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, r);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) stage[lane * kStage + j] = __uint_as_float(r[j]);
-      __syncwarp();
-      const int col = bn + c0 + lane;
-      const int nrows = min(32, M - rbase);
-      if (col < N && nrows > 0) {
-        double* cp = C + static_cast<long long>(rbase) * ldc + col;
-        double cv[32];
-        // issue all loads of this lane's column strip before any store (memory-level
-        // parallelism: 32 independent coalesced row loads per warp instruction stream)
-#pragma unroll
-        for (int rr = 0; rr < 32; ++rr)
-          if (rr < nrows) cv[rr] = __ldcs(cp + static_cast<long long>(rr) * ldc);
-#pragma unroll
-        for (int rr = 0; rr < 32; ++rr)
-          if (rr < nrows) {
-            const double v = cv[rr] - static_cast<double>(stage[rr * kStage + lane]);
-            __stcs(cp + static_cast<long long>(rr) * ldc, v);
-            cmax = fmax(cmax, fabs(v));
-          }
+
+  if (warp == 0) {
+    if (lane == 0) {                                         // ---- TMA producer
+      int it = 0;
+      for (int tile = blockIdx.x; tile < tiles && !s_fail; tile += gridDim.x) {
+        const int bm = (tile / tiles_n) * kBM, bn = (tile % tiles_n) * kBN;
+        for (int kb = 0; kb < kblocks; ++kb, ++it) {
+          const int s = it % NSTG;
+          if (!mbar_wait_bounded(&empty[s], ((it / NSTG) & 1) ^ 1)) { s_fail = 1; break; }
+          uint8_t* sA = base + s * Cfg::OPER_BYTES;
+          uint8_t* sB = sA + Cfg::NS * Cfg::CH * Cfg::TILE_A;
+          mbar_expect_tx(&full[s], Cfg::OPER_BYTES);
+          for (int sl = 0; sl < Cfg::NS; ++sl)
+            for (int c = 0; c < Cfg::CH; ++c) {
+              const int x = kb * 64 + c * (128 / Cfg::EB);
+              tma_load_2d(sA + (sl * Cfg::CH + c) * Cfg::TILE_A, &tmA, x, sl * Mpad + bm, &full[s]);
+              tma_load_2d(sB + (sl * Cfg::CH + c) * Cfg::TILE_B, &tmB, x, sl * Npad + bn, &full[s]);
+            }
+        }
       }
-      __syncwarp();
     }
-  } else if (tid == 0) {
-    set_error(st, PRRP_ERR_TIMEOUT);
+  } else if (warp == 1) {
+    if (lane == 0) {                                         // ---- MMA issuer
+      int it = 0, tcount = 0;
+      for (int tile = blockIdx.x; tile < tiles && !s_fail; tile += gridDim.x, ++tcount) {
+        const int a = tcount & 1;
+        if (!mbar_wait_bounded(&acce[a], ((tcount >> 1) & 1) ^ 1)) { s_fail = 1; break; }
+        tc_fence_after();
+        const uint32_t dt = tmem + a * kBN;
+        for (int kb = 0; kb < kblocks; ++kb, ++it) {
+          const int s = it % NSTG;
+          if (!mbar_wait_bounded(&full[s], (it / NSTG) & 1)) { s_fail = 1; break; }
+          tc_fence_after();
+          uint8_t* sA = base + s * Cfg::OPER_BYTES;
+          uint8_t* sB = sA + Cfg::NS * Cfg::CH * Cfg::TILE_A;
+          for (int p = 0; p < Cfg::NP; ++p) {
+            const int as = c_prod_a[p], bs = c_prod_b[p];
+            for (int c = 0; c < Cfg::CH; ++c) {
+              const uint64_t ad = sw128_desc(smem_u32(sA + (as * Cfg::CH + c) * Cfg::TILE_A));
+              const uint64_t bd = sw128_desc(smem_u32(sB + (bs * Cfg::CH + c) * Cfg::TILE_B));
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                umma<MODE>(dt, ad + 2 * k, bd + 2 * k, Cfg::IDESC, (kb | p | c | k) != 0);
+            }
+          }
+          umma_commit(&empty[s]);                            // frees the stage when done
+        }
+        if (s_fail) break;
+        umma_commit(&accf[a]);                               // accumulator ready
+      }
+    }
+  } else {                                                   // ---- epilogue warps
+    const int q = warp & 3;                                  // TMEM lane quarter of this warp
+    const int h = (warp - 2) >> 2;                           // column half
+    float* stage = reinterpret_cast<float*>(base + NSTG * Cfg::OPER_BYTES) + (warp - 2) * 32 * kStage;
+    int tcount = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tcount) {
+      const int a = tcount & 1;
+      const int bm = (tile / tiles_n) * kBM, bn = (tile % tiles_n) * kBN;
+      if (!mbar_wait_bounded(&accf[a], (tcount >> 1) & 1)) { s_fail = 1; break; }
+      tc_fence_after();
+      const int rbase = bm + q * 32;
+      const int nrows = min(32, M - rbase);
+      for (int c0 = h * 64; c0 < h * 64 + 64; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + a * kBN + (static_cast<uint32_t>(q * 32) << 16) + c0, r);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stage[lane * kStage + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int col = bn + c0 + lane;
+        if (col < N && nrows > 0) {
+          double* cp = C + static_cast<long long>(rbase) * ldc + col;
+          const int ldci = static_cast<int>(ldc);          // 32 rows x ldc fits in 32 bits
+#pragma unroll
+          for (int h16 = 0; h16 < 32; h16 += 16) {
+            double cv[16];
+#pragma unroll
+            for (int rr = 0; rr < 16; ++rr)
+              if (h16 + rr < nrows) cv[rr] = __ldcs(cp + (h16 + rr) * ldci);
+#pragma unroll
+            for (int rr = 0; rr < 16; ++rr)
+              if (h16 + rr < nrows) {
+                const double v = cv[rr] - static_cast<double>(stage[(h16 + rr) * kStage + lane]);
+                __stcs(cp + (h16 + rr) * ldci, v);
+                cmax = fmax(cmax, fabs(v));
+              }
+          }
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[a]);                  // accumulator free again
+    }
   }
-  if (track) {
+  if (track && warp >= 2) {
     for (int off = 16; off > 0; off >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
     if (lane == 0) atomic_max_nonneg(&st->gmax_bits, cmax);
   }
   tc_fence_before();
   __syncthreads();
+  if (s_fail && tid == 0) set_error(st, PRRP_ERR_TIMEOUT);
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
@@ -347,10 +391,14 @@ cudaError_t launch_tc_mode(int M, int N, int K, const double* L, long long ldl, 
   CUtensorMap ma, mb;
   if (!make_map(&ma, wsA, MODE, Cfg::NS * Mpad, kpad) || !make_map(&mb, wsB, MODE, Cfg::NS * Npad, kpad))
     return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(tc_update_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+  e = smem_optin(tc_update_kernel<MODE>);
   if (e != cudaSuccess) return e;
-  dim3 grid(Npad / kBN, Mpad / kBM);
-  tc_update_kernel<MODE><<<grid, 128, Cfg::SMEM, s>>>(ma, mb, M, N, kblocks, Mpad, Npad, C, ldc, st, track);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = (Npad / kBN) * (Mpad / kBM);
+  tc_update_kernel<MODE><<<std::min(tiles, sms), kThreads, Cfg::SMEM, s>>>(ma, mb, M, N, kblocks, Mpad, Npad, C,
+                                                                           ldc, st, track);
   return cudaGetLastError();
 }
 

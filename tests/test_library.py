@@ -31,6 +31,9 @@ def test_library_exports_every_declared_symbol():
 def test_binding_covers_header():
     import paper_1208_2451_gb300 as P
     assert set(P.exported_symbols()) == set(declared_functions())
+    for required in ("prrp_batch_solve", "prrp_server_create", "prrp_server_submit",
+                     "prrp_server_wait", "prrp_server_stats", "prrp_server_destroy"):
+        assert required in declared_functions()
     assert P.prrp_version().startswith("prrp")
     assert P.prrp_status_string(2).startswith("singular")
 
