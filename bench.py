@@ -156,16 +156,20 @@ def run_reference(args) -> None:
 def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=1):
     """Mixed-precision form: A = Q1 diag(sigma) Q2^T (cond kappa, Q from QR of seeded
     Gaussians), BF16X3 tensor-core Schur update with FP64 pivoting, FP64 refinement of 4
-    right-hand sides.  The matrix is generated on the GPU in FP64 (torch QR)."""
+    right-hand sides.  The matrix is generated on the GPU in FP64 (torch QR).  A kappa of
+    0 stands for an iid N(0,1) matrix instead (no QR)."""
     out = {}
     for kappa in kappas:
         g = torch.Generator(device=dev)
         g.manual_seed(int(kappa) % 1000003)
-        Q1, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=g))
-        Q2, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=g))
-        sig = kappa ** (-torch.arange(n, dtype=torch.float64, device=dev) / (n - 1))
-        A0 = (Q1 * sig) @ Q2.T
-        del Q1, Q2
+        if kappa > 0:
+            Q1, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=g))
+            Q2, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=g))
+            sig = kappa ** (-torch.arange(n, dtype=torch.float64, device=dev) / (n - 1))
+            A0 = (Q1 * sig) @ Q2.T
+            del Q1, Q2
+        else:
+            A0 = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
         B0 = torch.randn(n, 4, dtype=torch.float64, device=dev, generator=g)
         A = torch.empty_like(A0)
         B = torch.empty_like(B0)
@@ -184,7 +188,7 @@ def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=
         r = B0 - A0 @ B
         eta = float((r.abs().sum(0) / (A0.abs().sum(0).max() * B.abs().sum(0) + B0.abs().sum(0))).max())
         dt = min(times)
-        out[f"kappa={kappa:g}"] = {"s": dt, "tflops": 2 * n ** 3 / 3 / dt / 1e12, "solves_per_s": 1.0 / dt,
+        out[f"kappa={kappa:g}" if kappa > 0 else "randn"] = {"s": dt, "tflops": 2 * n ** 3 / 3 / dt / 1e12, "solves_per_s": 1.0 / dt,
                                    "eta": eta, "iterations": info["iterations"]}
         del A0, A, B0, B
         torch.cuda.empty_cache()
@@ -413,6 +417,8 @@ def main():
                     help="skip the mixed-precision, batched and served measurements")
     ap.add_argument("--form", choices=["mixed", "batched", "served"],
                     help="run only one of the other forms and print its JSON")
+    ap.add_argument("--randn", action="store_true",
+                    help="--form mixed: an iid N(0,1) matrix instead of the conditioned one")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -420,7 +426,9 @@ def main():
         import torch
         import paper_1208_2451_gb300 as prrp
         ctx = prrp.prrp_create(0)
-        fn = {"mixed": lambda: form_mixed(prrp, ctx, torch, torch.device("cuda", 0), n=args.n if args.n != N_DEFAULT else 16384),
+        fn = {"mixed": lambda: form_mixed(prrp, ctx, torch, torch.device("cuda", 0),
+                                          n=args.n if args.n != N_DEFAULT else 16384,
+                                          kappas=(0.0,) if args.randn else (1e2, 1e6)),
               "batched": lambda: form_batched(prrp, ctx, torch, torch.device("cuda", 0)),
               "served": lambda: form_served(prrp, ctx)}[args.form]
         print(json.dumps({"form": args.form, **fn()}), flush=True)

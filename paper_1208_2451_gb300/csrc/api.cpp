@@ -73,6 +73,17 @@ struct prrp_ctx {
   size_t hB_cap = 0;
   unsigned char* tcws = nullptr;    // split operands of the tensor-core update
   size_t tcws_cap = 0;
+  // look-ahead: side streams, events, second multiplier buffer, A12 snapshots, second
+  // tensor-core workspace
+  cudaStream_t s_rest = nullptr, s_blk = nullptr;
+  std::vector<cudaEvent_t> evs;
+  size_t ev_next = 0;
+  double* l21b = nullptr;
+  size_t l21b_cap = 0;
+  double* a12 = nullptr;            // two snapshots of the block row right of the panel
+  size_t a12_cap = 0;
+  unsigned char* tcws2 = nullptr;
+  size_t tcws2_cap = 0;
   // batched solves: metadata, per-CTA workspace, outputs, tuned launch shapes, graphs
   unsigned char* bmeta = nullptr;
   size_t bmeta_cap = 0;
@@ -235,6 +246,18 @@ prrp_status enqueue_panel(prrp_ctx* ctx, const double* P, long long ldp, int m, 
   return PRRP_OK;
 }
 
+// A recorded event from a small ring (record then wait is safe to reuse: a wait captures
+// the event's state when it is enqueued).
+cudaEvent_t next_event(prrp_ctx* ctx) {
+  if (ctx->evs.empty()) {
+    ctx->evs.resize(64);
+    for (auto& e : ctx->evs) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  }
+  cudaEvent_t e = ctx->evs[ctx->ev_next % ctx->evs.size()];
+  ++ctx->ev_next;
+  return e;
+}
+
 prrp_status read_state(prrp_ctx* ctx, DevState* h, cudaStream_t s) {
   CK(cudaMemcpyAsync(h, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -317,7 +340,11 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
   if (ctx->bws) cudaFree(ctx->bws);
   if (ctx->bout) cudaFree(ctx->bout);
   void* ptrs[] = {ctx->st, ctx->xval, ctx->xkey, ctx->xvec, ctx->pairs, ctx->ipiv, ctx->order,
-                  ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB, ctx->tcws};
+                  ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB, ctx->tcws,
+                  ctx->l21b, ctx->a12, ctx->tcws2};
+  for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
+  if (ctx->s_rest) cudaStreamDestroy(ctx->s_rest);
+  if (ctx->s_blk) cudaStreamDestroy(ctx->s_blk);
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -368,46 +395,101 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
   }
 
   const int max_pairs = 2 * (b + o.max_swaps) + 2;
-  for (int k0 = 0; k0 < n; k0 += b) {
+  // Look-ahead schedule.  Critical stream s: panel(j), permute(j), snapshot of the block
+  // row A12 right of the panel, the narrow update of the next panel's columns; stream
+  // s_rest: the rest of the update; stream s_blk: GEPP of the diagonal block, U12 and the
+  // final multipliers.  permute(j+1) moves whole rows below the block, so it waits for
+  // the rest update and the multipliers of panel j.  The updates read L21 from the panel's
+  // own buffer (two alternate) and A12 from the snapshot, so U12 may overwrite A12 while
+  // they run.
+  if (!ctx->s_rest) {
+    if ((e = cudaStreamCreateWithFlags(&ctx->s_rest, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&ctx->s_blk, cudaStreamNonBlocking)) != cudaSuccess)
+      return fail(cuda_fail(ctx, e, "stream create"));
+  }
+  if ((ps = grow(ctx, &ctx->l21b, &ctx->l21b_cap, (size_t)n * b)) != PRRP_OK) return fail(ps);
+  if ((ps = grow(ctx, &ctx->a12, &ctx->a12_cap, 2 * (size_t)n * b)) != PRRP_OK) return fail(ps);
+  if (o.prec != PRRP_FP64 &&
+      (ps = grow(ctx, &ctx->tcws2, &ctx->tcws2_cap, tc_workspace_bytes(o.prec, n, b, b))) != PRRP_OK)
+    return fail(ps);
+  cudaStream_t sr = ctx->s_rest, sb = ctx->s_blk;
+  cudaEvent_t ev_start = next_event(ctx);
+  CK(cudaEventRecord(ev_start, s));
+  CK(cudaStreamWaitEvent(sr, ev_start, 0));
+  CK(cudaStreamWaitEvent(sb, ev_start, 0));
+  cudaEvent_t ev_rest = nullptr, ev_blk = nullptr;        // of the previous panel
+  // C (mm x nn) -= L (mm x kk, ld kk) * U (kk x nn, ld ldu)
+  auto update = [&](int mm, int nn, int kk, const double* L, const double* U, long long ldu, double* C,
+                    unsigned char* ws, cudaStream_t st) -> cudaError_t {
+    if (o.prec == PRRP_FP64)
+      return launch_gemm_fp64(mm, nn, kk, L, kk, U, ldu, C, lda, ctx->st, 1, ctx->num_sms, st, 1);
+    return launch_tc_update(o.prec, mm, nn, kk, L, kk, U, ldu, C, lda, ctx->st, 1, ws, st);
+  };
+  for (int jp = 0, k0 = 0; k0 < n; k0 += b, ++jp) {
     const int w = std::min(b, n - k0), m = n - k0;
+    const int w2 = std::min(b, n - k0 - w);                 // next panel's width (0: last)
     double* Akk = dA + (long long)k0 * lda + k0;
+    double* L21 = (jp & 1) ? ctx->l21b : ctx->l21;
+    double* A12 = ctx->a12 + (size_t)(jp & 1) * n * b;     // snapshot: w x nc, ld nc
     {
       Timed t(ctx, s, PRRP_KIND_PANEL, 3LL * m * w * w);
-      ps = enqueue_panel(ctx, Akk, lda, m, w, o.tau, o.max_swaps, k0, ctx->l21, w, nullptr,
-                         ctx->pairs, s);
+      ps = enqueue_panel(ctx, Akk, lda, m, w, o.tau, o.max_swaps, k0, L21, w, nullptr, ctx->pairs, s);
     }
     if (ps != PRRP_OK) return fail(ps);
+    if (ev_rest) CK(cudaStreamWaitEvent(s, ev_rest, 0));
+    if (ev_blk) CK(cudaStreamWaitEvent(s, ev_blk, 0));
     {
       Timed t(ctx, s, PRRP_KIND_PERMUTE);
       e = launch_permute(dA, lda, n, k0, ctx->pairs, max_pairs, f->perm, ctx->st, s);
     }
     if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "permute"));
-    if (m > w) {
-      Timed t(ctx, s, PRRP_KIND_UPDATE, 2LL * (m - w) * (n - k0 - w) * w);
-      if (o.prec == PRRP_FP64)
-        e = launch_gemm_fp64(m - w, n - k0 - w, w, ctx->l21, w, Akk + w, lda,
-                             Akk + (long long)w * lda + w, lda, ctx->st, 1, ctx->num_sms, s);
-      else
-        e = launch_tc_update(o.prec, m - w, n - k0 - w, w, ctx->l21, w, Akk + w, lda,
-                             Akk + (long long)w * lda + w, lda, ctx->st, 1, ctx->tcws, s);
-      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "schur update"));
-    }
+    cudaEvent_t ev_perm = next_event(ctx);
+    CK(cudaEventRecord(ev_perm, s));
+    // block diagonal work on s_blk: GEPP now, U12 and the multipliers after the snapshot
+    CK(cudaStreamWaitEvent(sb, ev_perm, 0));
     {
-      Timed t(ctx, s, PRRP_KIND_DIAG, 2LL * w * w * w / 3);
-      e = launch_diag_gepp(dA, lda, k0, w, ctx->ipiv, f->perm, ctx->st, s);
+      Timed t(ctx, sb, PRRP_KIND_DIAG, 2LL * w * w * w / 3);
+      e = launch_diag_gepp(dA, lda, k0, w, ctx->ipiv, f->perm, ctx->st, sb);
     }
     if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "diag gepp"));
+    const int nc = n - k0 - w;                              // columns right of the panel
+    if (m > w) {
+      CK(cudaMemcpy2DAsync(A12, sizeof(double) * nc, Akk + w, sizeof(double) * lda, sizeof(double) * nc, w,
+                           cudaMemcpyDeviceToDevice, s));
+      cudaEvent_t ev_snap = next_event(ctx);
+      CK(cudaEventRecord(ev_snap, s));
+      {
+        Timed t(ctx, s, PRRP_KIND_UPDATE, 2LL * (m - w) * w2 * w);
+        e = update(m - w, w2, w, L21, A12, nc, Akk + (long long)w * lda + w, ctx->tcws2, s);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "schur update (next panel)"));
+      if (nc > w2) {
+        CK(cudaStreamWaitEvent(sr, ev_snap, 0));
+        {
+          Timed t(ctx, sr, PRRP_KIND_UPDATE, 2LL * (m - w) * (nc - w2) * w);
+          e = update(m - w, nc - w2, w, L21, A12 + w2, nc, Akk + (long long)w * lda + w + w2, ctx->tcws, sr);
+        }
+        if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "schur update"));
+        ev_rest = next_event(ctx);
+        CK(cudaEventRecord(ev_rest, sr));
+      }
+      CK(cudaStreamWaitEvent(sb, ev_snap, 0));
+    }
     if (n > w) {
-      Timed t(ctx, s, PRRP_KIND_U12, 1LL * (n - k0 - w) * w * w);
-      e = launch_u12(dA, lda, n, k0, w, ctx->ipiv, ctx->st, s);
+      Timed t(ctx, sb, PRRP_KIND_U12, 1LL * nc * w * w);
+      e = launch_u12(dA, lda, n, k0, w, ctx->ipiv, ctx->st, sb);
     }
     if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "u12"));
     if (m > w) {
-      Timed t(ctx, s, PRRP_KIND_LFIX, 1LL * (m - w) * w * w);
-      e = launch_lfix(dA, lda, n, k0, w, ctx->l21, w, ctx->ipiv, ctx->st, s);
+      Timed t(ctx, sb, PRRP_KIND_LFIX, 1LL * (m - w) * w * w);
+      e = launch_lfix(dA, lda, n, k0, w, L21, w, ctx->ipiv, ctx->st, sb);
     }
     if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "lfix"));
+    ev_blk = next_event(ctx);
+    CK(cudaEventRecord(ev_blk, sb));
   }
+  if (ev_rest) CK(cudaStreamWaitEvent(s, ev_rest, 0));
+  if (ev_blk) CK(cudaStreamWaitEvent(s, ev_blk, 0));
   DevState h{};
   if ((ps = read_state(ctx, &h, s)) != PRRP_OK) return fail(ps);
   collect_timing(ctx);

@@ -41,7 +41,7 @@ cudaError_t launch_permute(double* A, long long lda, int n, int k0, const int* p
 // st->gmax_bits when track != 0.
 cudaError_t launch_gemm_fp64(int m, int n, int k, const double* L, long long ldl,
                              const double* U, long long ldu, double* C, long long ldc,
-                             DevState* st, int track, int num_sms, cudaStream_t s);
+                             DevState* st, int track, int num_sms, cudaStream_t s, int one_per_sm = 0);
 
 // Same update on tcgen05 tensor cores, prec = PRRP_TF32 or PRRP_BF16X3 (FP32 accumulation,
 // FP64 C); ws holds the split operands (tc_workspace_bytes).

@@ -203,8 +203,15 @@ static cudaError_t launch_gemm_tile(int m, int n, int k, const double* L, long l
 
 cudaError_t launch_gemm_fp64(int m, int n, int k, const double* L, long long ldl,
                              const double* U, long long ldu, double* C, long long ldc,
-                             DevState* st, int track, int num_sms, cudaStream_t s) {
+                             DevState* st, int track, int num_sms, cudaStream_t s, int one_per_sm) {
   if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+  if (one_per_sm) {
+    // leave room on every SM for a co-resident panel CTA (look-ahead): 64 x 64 tiles,
+    // one persistent CTA per SM
+    const long long t64 = (long long)((m + 63) / 64) * ((n + 63) / 64);
+    return launch_gemm_tile<64, 64>(m, n, k, L, ldl, U, ldu, C, ldc, st, track,
+                                    (int)std::min<long long>(t64, num_sms), s);
+  }
   // pick the tile whose wave count wastes least: cost ~ ceil(tiles / sms) * tile area
   const long long t128 = (long long)((m + 127) / 128) * ((n + 127) / 128);
   const long long t64 = (long long)((m + 63) / 64) * ((n + 63) / 64);

@@ -158,6 +158,22 @@ struct TcCfg {
 __constant__ int c_prod_a[6] = {0, 0, 1, 0, 2, 1};
 __constant__ int c_prod_b[6] = {0, 1, 0, 2, 0, 1};
 
+// float -> double with integer operations only: rebias the exponent and widen the
+// mantissa.  Exact for normal values, inf and nan; zero and the FP32 subnormals (below
+// 1.2e-38 in magnitude) become a signed zero.  On this GPU the FP64 pipe runs at 2
+// operations per clock per SM, so the epilogue keeps it for the one operation that needs
+// it, the subtraction (a hardware conversion here would be a second FP64-pipe op).
+__device__ __forceinline__ double f2d_int(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const uint32_t ee = (e == 0u) ? 0u : (e == 0xFFu ? 0x7FFu : e + 896u);
+  const uint32_t mm = (e == 0u) ? 0u : (u & 0x7FFFFFu);
+  const unsigned long long d = (static_cast<unsigned long long>(u & 0x80000000u) << 32) |
+                               (static_cast<unsigned long long>(ee) << 52) |
+                               (static_cast<unsigned long long>(mm) << 29);
+  return __longlong_as_double(static_cast<long long>(d));
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -198,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(const __grid_con
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  double cmax = 0.0;
+  unsigned long long cmax_bits = 0ull;          // max |C| as a non-negative IEEE bit pattern
 
   if (warp == 0) {
     if (lane == 0) {                                         // ---- TMA producer
@@ -281,9 +297,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(const __grid_con
 #pragma unroll
             for (int rr = 0; rr < 16; ++rr)
               if (h16 + rr < nrows) {
-                const double v = cv[rr] - static_cast<double>(stage[(h16 + rr) * kStage + lane]);
+                const double v = cv[rr] - f2d_int(stage[(h16 + rr) * kStage + lane]);
                 __stcs(cp + (h16 + rr) * ldci, v);
-                cmax = fmax(cmax, fabs(v));
+                const unsigned long long vb =
+                    static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull;
+                cmax_bits = vb > cmax_bits ? vb : cmax_bits;
               }
           }
         }
@@ -295,8 +313,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(const __grid_con
     }
   }
   if (track && warp >= 2) {
-    for (int off = 16; off > 0; off >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
-    if (lane == 0) atomic_max_nonneg(&st->gmax_bits, cmax);
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, cmax_bits, off);
+      cmax_bits = o > cmax_bits ? o : cmax_bits;
+    }
+    // NaN bit patterns sort above every finite value; the input scan rejects them earlier
+    if (lane == 0) atomicMax(&st->gmax_bits, cmax_bits);
   }
   tc_fence_before();
   __syncthreads();
