@@ -196,6 +196,47 @@ def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=
                         f"{'BF16X3' if prec == 2 else 'TF32'} Schur update + FP64 refinement", "runs": out}
 
 
+def form_update(prrp, ctx, torch, dev, n=16384, k=64, reps=5):
+    """The Schur update alone (Algorithm 1, line 7) at the first trailing shape of the
+    factorization: C (m x m, m = n - k, FP64, 2 GB at n = 16384, far above L2) -= L (m x k)
+    U (k x m), in each precision.  Time = the library's CUDA events around the update
+    (operand split + update kernel), best of `reps`.  Roofline: FP64 C is read and written
+    once (16 bytes per entry) for 2k flops, so HBM bounds it at hbm_gbs * 2k / 16 flop/s;
+    the tensor-core bound (measured bf16 peak x the nominal TF32/BF16 ratio, / products)
+    is far above it."""
+    pk = _peaks()
+    hbm, bf16 = pk.get("hbm_gbs", 6800.0), pk.get("bf16_tflops", 1900.0)
+    m = n - k
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    L = torch.randn(m, k, dtype=torch.float64, device=dev, generator=g)
+    U = torch.randn(k, m, dtype=torch.float64, device=dev, generator=g)
+    Cm = torch.randn(m, m, dtype=torch.float64, device=dev, generator=g)
+    prrp.prrp_ctx_set_timing(ctx, True)
+    out = {}
+    for prec, name, tc_peak in ((1, "tf32", bf16 * 1.1 / 2.25), (2, "bf16x3", bf16 / 6), (0, "fp64", None)):
+        best = None
+        for _ in range(reps + 1):
+            prrp.prrp_ctx_kernel_stats(ctx, reset=True)
+            prrp.prrp_schur_update(ctx, L, U, Cm, prec=prec)
+            ms = prrp.prrp_ctx_kernel_stats(ctx, reset=True)["update"]["ms"]
+            best = ms if best is None else min(best, ms)
+        tf = 2.0 * m * m * k / best / 1e9
+        if tc_peak is None:
+            peak, bound, src = fp64_peak_tflops(), "alu", "FP64 FMA pipe at 2070 MHz"
+        else:
+            hb = hbm * 2 * k / 16 / 1000
+            peak, bound = min(hb, tc_peak), ("hbm" if hb < tc_peak else "tensor")
+            src = f"min(HBM {hbm:g} GB/s x {2 * k}/16 flop/B, tensor {tc_peak:.0f} TFLOP/s) of measured"
+        out[name] = {"ms": best, "tflops": tf, "c_GBs": 16.0 * m * m / best / 1e6,
+                     "roofline": {"bound": bound, "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": tf / peak, "peak_source": src}}
+    prrp.prrp_ctx_set_timing(ctx, False)
+    del L, U, Cm
+    torch.cuda.empty_cache()
+    return {"workload": f"Schur update C -= L U, C {m}x{m} FP64, k={k}", "runs": out}
+
+
 def form_batched(prrp, ctx, torch, dev, count=4096, reps=3):
     """Batched form: 4096 systems, n uniform in [32, 512], b = 16, one RHS, FP32 factor +
     FP64 refinement, in one persistent launch."""
@@ -415,7 +456,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the mixed-precision, batched and served measurements")
-    ap.add_argument("--form", choices=["mixed", "batched", "served"],
+    ap.add_argument("--form", choices=["mixed", "batched", "served", "update"],
                     help="run only one of the other forms and print its JSON")
     ap.add_argument("--randn", action="store_true",
                     help="--form mixed: an iid N(0,1) matrix instead of the conditioned one")
@@ -430,7 +471,9 @@ def main():
                                           n=args.n if args.n != N_DEFAULT else 16384,
                                           kappas=(0.0,) if args.randn else (1e2, 1e6)),
               "batched": lambda: form_batched(prrp, ctx, torch, torch.device("cuda", 0)),
-              "served": lambda: form_served(prrp, ctx)}[args.form]
+              "served": lambda: form_served(prrp, ctx),
+              "update": lambda: form_update(prrp, ctx, torch, torch.device("cuda", 0),
+                                            n=args.n if args.n != N_DEFAULT else 16384)}[args.form]
         print(json.dumps({"form": args.form, **fn()}), flush=True)
         ctx.close()
     else:

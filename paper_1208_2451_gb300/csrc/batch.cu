@@ -184,7 +184,7 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
       if (pr < w) continue;
       BKey d{0ull, pr - w, 0x7fffffff};
       for (int i = tl; i < w; i += kTeam) {
-        const unsigned long long a = dbits(fabs(Ps[r * sp + i]));
+        const unsigned long long a = abs_bits(Ps[r * sp + i]);
         if (a > d.v || d.k2 == 0x7fffffff) { d.v = a; d.k2 = i; }
       }
       BKey o = bshfl(d, 1, tmask);
@@ -443,12 +443,12 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
       for (int t = 0; t < w; ++t) {
         if (tid == 0) {
           int p = t;
-          double bv = fabs(Dg[t * (kBW + 1) + t]);
+          unsigned long long bv = abs_bits(Dg[t * (kBW + 1) + t]);
           for (int i = t + 1; i < w; ++i) {
-            const double v = fabs(Dg[i * (kBW + 1) + t]);
+            const unsigned long long v = abs_bits(Dg[i * (kBW + 1) + t]);
             if (v > bv) { bv = v; p = i; }
           }
-          ipiv[t] = bv > 0.0 ? p : -1;
+          ipiv[t] = bv > 0ull ? p : -1;
         }
         __syncthreads();
         const int p = ipiv[t];
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
       double cm = 0.0;
       for (int j = tid; j < n; j += kBT) {
         double s = 0.0;
-        for (int i = 0; i < n; ++i) s += fabs(A[(long long)i * lda + j]);
+        for (int i = 0; i < n; ++i) s += abs_int(A[(long long)i * lda + j]);
         cm = fmax(cm, s);
       }
       anorm = block_max(cm, s_red);
@@ -560,12 +560,12 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
           if (lane == 0) {
             const double r = bcol[i] - acc;
             rv[i] = r;
-            rs += fabs(r);
+            rs += abs_int(r);
           }
         }
         for (int i = tid; i < n; i += kBT) {
-          xs += fabs(xv[i]);
-          bs += fabs(bcol[i]);
+          xs += abs_int(xv[i]);
+          bs += abs_int(bcol[i]);
         }
         rs = block_sum(rs, s_red);
         xs = block_sum(xs, s_red);

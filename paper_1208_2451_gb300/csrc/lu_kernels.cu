@@ -21,23 +21,18 @@ namespace prrp {
 // ---------------------------------------------------------------- scan
 __global__ void __launch_bounds__(256) scan_kernel(const double* __restrict__ A, long long lda,
                                                    int n, DevState* st) {
-  double mx = 0.0;
-  unsigned bad = 0;
+  unsigned long long mx = 0ull;                   // max |a| as an IEEE bit pattern
   for (long long row = blockIdx.x; row < n; row += gridDim.x) {
     const double* a = A + row * lda;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-      const double v = a[c];
-      bad |= !isfinite(v);
-      mx = fmax(mx, fabs(v));
-    }
+    for (int c = threadIdx.x; c < n; c += blockDim.x) mx = max_bits(mx, abs_bits(a[c]));
   }
-  for (int off = 16; off > 0; off >>= 1) {
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
-  }
+  for (int off = 16; off > 0; off >>= 1) mx = max_bits(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  const bool bad = mx >= kInfBits;                // an inf or nan somewhere (nan sorts above inf)
   if ((threadIdx.x & 31) == 0) {
-    atomic_max_nonneg(&st->amax_bits, mx);
-    atomic_max_nonneg(&st->gmax_bits, mx);
+    if (!bad) {
+      atomicMax(&st->amax_bits, mx);
+      atomicMax(&st->gmax_bits, mx);
+    }
     if (bad) {
       st->nonfinite = 1;
       set_error(st, PRRP_ERR_NONFINITE);
@@ -127,7 +122,7 @@ __global__ void __launch_bounds__(256, 1) gemm_fp64_kernel(int M, int N, int K,
   const int tx = tid & 15, ty = tid >> 4;
   const int tiles_n = (N + BN - 1) / BN;
   const int tiles = ((M + BM - 1) / BM) * tiles_n;
-  double cmax = 0.0;
+  unsigned long long cmax = 0ull;               // max |C| as an IEEE bit pattern
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int bm = (tile / tiles_n) * BM, bn = (tile % tiles_n) * BN;
     // warm L2 with this tile's C rows while the operands are staged
@@ -179,14 +174,14 @@ __global__ void __launch_bounds__(256, 1) gemm_fp64_kernel(int M, int N, int K,
         if (bn + tx * TN + j < N) {
           const double v = crow[j] - acc[i][j];
           crow[j] = v;
-          cmax = fmax(cmax, fabs(v));
+          cmax = max_bits(cmax, abs_bits(v));
         }
       }
     }
   }
   if (track) {
-    for (int off = 16; off > 0; off >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
-    if ((tid & 31) == 0) atomic_max_nonneg(&st->gmax_bits, cmax);
+    for (int off = 16; off > 0; off >>= 1) cmax = max_bits(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
+    if ((tid & 31) == 0) atomicMax(&st->gmax_bits, cmax);
   }
 }
 
@@ -250,7 +245,7 @@ __global__ void __launch_bounds__(256) diag_gepp_kernel(double* __restrict__ A, 
     unsigned long long bv = 0ull;
     int bi = 0x7fffffff;
     for (int i = t + tid; i < w; i += blockDim.x) {
-      const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(D[i * WP + t]));
+      const unsigned long long v = abs_bits(D[i * WP + t]);
       if (v > bv || bi == 0x7fffffff) { bv = v; bi = i; }
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -291,15 +286,15 @@ __global__ void __launch_bounds__(256) diag_gepp_kernel(double* __restrict__ A, 
     }
     __syncthreads();
   }
-  double umax = 0.0;
+  unsigned long long umax = 0ull;
   for (int e = tid; e < w * w; e += blockDim.x) {
     const int i = e / w, j = e - i * w;
     const double v = D[i * WP + j];
     A[(long long)(k0 + i) * lda + k0 + j] = v;
-    if (j >= i) umax = fmax(umax, fabs(v));
+    if (j >= i) umax = max_bits(umax, abs_bits(v));
   }
-  for (int off = 16; off > 0; off >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, off));
-  if (lane == 0) atomic_max_nonneg(&st->umax_bits, umax);
+  for (int off = 16; off > 0; off >>= 1) umax = max_bits(umax, __shfl_xor_sync(0xffffffffu, umax, off));
+  if (lane == 0) atomicMax(&st->umax_bits, umax);
   if (tid == 0)
     for (int t = 0; t < w; ++t) {
       const int p = ipiv[t];
@@ -362,16 +357,16 @@ __global__ void __launch_bounds__(kU12Cols) u12_kernel(double* __restrict__ A, l
       }
   }
   __syncthreads();
-  double umax = 0.0;
+  unsigned long long umax = 0ull;
   for (int i = 0; i < w; ++i)
     if (tid < cw) {
       const double v = X[i * kU12Cols + tid];
       A[(long long)(k0 + i) * lda + c0 + tid] = v;
-      umax = fmax(umax, fabs(v));
+      umax = max_bits(umax, abs_bits(v));
     }
   if (right) {
-    for (int off = 16; off > 0; off >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, off));
-    if (tid == 0) atomic_max_nonneg(&st->umax_bits, umax);
+    for (int off = 16; off > 0; off >>= 1) umax = max_bits(umax, __shfl_xor_sync(0xffffffffu, umax, off));
+    if (tid == 0) atomicMax(&st->umax_bits, umax);
   }
 }
 
@@ -405,7 +400,7 @@ __global__ void __launch_bounds__(32) u12_reg_kernel(double* __restrict__ A, lon
     }
   __syncthreads();
   const bool valid = c < cend;
-  double umax = 0.0;
+  unsigned long long umax = 0ull;
   if (valid) {
     double x[W];
 #pragma unroll
@@ -416,14 +411,14 @@ __global__ void __launch_bounds__(32) u12_reg_kernel(double* __restrict__ A, lon
 #pragma unroll
         for (int i = k + 1; i < W; ++i) x[i] = fma(-Ls[i * W + k], x[k], x[i]);
 #pragma unroll
-      for (int i = 0; i < W; ++i) umax = fmax(umax, fabs(x[i]));
+      for (int i = 0; i < W; ++i) umax = max_bits(umax, abs_bits(x[i]));
     }
 #pragma unroll
     for (int i = 0; i < W; ++i) A[(long long)(k0 + i) * lda + c] = x[i];
   }
   if (right) {                                      // every lane takes part in the reduction
-    for (int off = 16; off > 0; off >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, off));
-    if (tid == 0) atomic_max_nonneg(&st->umax_bits, umax);
+    for (int off = 16; off > 0; off >>= 1) umax = max_bits(umax, __shfl_xor_sync(0xffffffffu, umax, off));
+    if (tid == 0) atomicMax(&st->umax_bits, umax);
   }
 }
 

@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
       if (pr < w) continue;
       Cand d{0ull, pr - w, 0x7fffffff, r};
       for (int i = tl; i < w; i += kTeam) {
-        const unsigned long long a = vbits(fabs(Ps[r * SP + i]));
+        const unsigned long long a = abs_bits(Ps[r * SP + i]);
         if (a > d.v || d.k2 == 0x7fffffff) { d.v = a; d.k2 = i; }
       }
       Cand o = shfl_cand(d, 1, tmask);
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   }
 
   // ---------------- outputs ----------------
-  double lmax = 0.0;
+  unsigned long long lmax = 0ull;
   for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
     const int pr = pos[r];
     if (pr < w) continue;
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     for (int k = tl; k < w; k += kTeam) {
       const double v = Ps[r * SP + k];
       dst[k] = v;
-      lmax = fmax(lmax, fabs(v));
+      lmax = max_bits(lmax, abs_bits(v));
     }
   }
   __syncwarp();
@@ -368,8 +368,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
       p.pairs[2 * idx + 1] = r0 + r;
     }
   }
-  for (int off = 16; off > 0; off >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
-  if (lane == 0) atomic_max_nonneg(&st->l21_bits, lmax);
+  for (int off = 16; off > 0; off >>= 1) lmax = max_bits(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
+  if (lane == 0) atomicMax(&st->l21_bits, lmax);
   if (cta == 0 && tid == 0) {
     st->panel_swaps = swaps;
     st->swaps_total += swaps;

@@ -176,9 +176,9 @@ __global__ void __launch_bounds__(kSolveThreads) residual_norms_kernel(const dou
   const int c = blockIdx.x;
   double r = 0.0, x = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    r += fabs(R[(long long)i * nrhs + c]);
-    x += fabs(X[(long long)i * ldx + c]);
-    b += fabs(B[(long long)i * ldb + c]);
+    r += abs_int(R[(long long)i * nrhs + c]);
+    x += abs_int(X[(long long)i * ldx + c]);
+    b += abs_int(B[(long long)i * ldb + c]);
   }
   sr[threadIdx.x] = r; sx[threadIdx.x] = x; sb[threadIdx.x] = b;
   __syncthreads();
@@ -207,7 +207,7 @@ __global__ void norm1_kernel(const double* __restrict__ A, long long lda, int n,
   double best = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s += fabs(A[(long long)i * lda + j]);
+    for (int i = 0; i < n; ++i) s += abs_int(A[(long long)i * lda + j]);
     best = fmax(best, s);
   }
   for (int off = 16; off > 0; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));

@@ -11,10 +11,12 @@
 //   * warp 1 (one lane) issues the tcgen05.mma instructions (M = 128, N = 128, 32 bytes of
 //     k each) into one of two 128-column TMEM accumulators, commits each stage's MMAs to
 //     its empty barrier and each finished tile to the accumulator's full barrier;
-//   * warps 2..9 (two per TMEM lane quarter, each half the columns) read the other
-//     accumulator, transpose each 32 x 32 block through shared memory and update C with
-//     row-contiguous, coalesced FP64 loads and stores (32 loads in flight per lane),
-//     tracking max |C| for the growth factor, then release the accumulator.
+//   * warps 2..17 (four per TMEM lane quarter, each a 32 x 32 block of the tile) read the
+//     other accumulator, release it, and update C in FP64.  Where C allows (16-byte
+//     aligned, even leading dimension and width) the C boxes move HBM -> shared memory ->
+//     HBM by TMA, loaded a tile ahead and updated in place in shared memory; otherwise each
+//     block is transposed through shared memory and C is loaded and stored from registers
+//     with row-contiguous, coalesced accesses.  Both track max |C| for the growth factor.
 // So the HBM-bound epilogue of one tile overlaps the loads and MMAs of the next.  Every
 // wait is bounded: on expiry the CTA records PRRP_ERR_TIMEOUT, frees its tensor memory
 // and returns.
@@ -133,11 +135,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 constexpr int kBM = 128, kBN = 128;
 constexpr int kStage = 33;        // padded row of the 32 x 32 transpose stage (floats)
-constexpr int kEpiWarps = 8;      // two warps per TMEM lane quarter, each half the columns
+constexpr int kEpiWarps = 16;     // four warps per TMEM lane quarter, each a quarter of the columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kTmemCols = 2 * kBN;  // double-buffered accumulator
+constexpr int kCSlots = 2;          // C boxes per epilogue warp and tile: 32 rows x 16 doubles
+constexpr int kCBox = 32 * 128;     // bytes of one C box (128-byte rows, 128-byte swizzle)
 
-template <int MODE>
+// CT = 1: C moves through shared memory by TMA (needs a 16-byte aligned C, an even leading
+// dimension and an even column count); CT = 0: the epilogue loads and stores C from
+// registers.
+template <int MODE, int CT>
 struct TcCfg {
   static constexpr int EB = MODE == 0 ? 4 : 2;         // operand bytes per element
   static constexpr int CH = MODE == 0 ? 2 : 1;         // 128-byte chunks per 64-wide k block
@@ -146,13 +153,13 @@ struct TcCfg {
   static constexpr int TILE_A = kBM * 128;             // bytes per slice-chunk
   static constexpr int TILE_B = kBN * 128;
   static constexpr int OPER_BYTES = NS * CH * (TILE_A + TILE_B);   // one pipeline stage
-  static constexpr int EPI_BYTES = kEpiWarps * 32 * kStage * 4;
-  // as many operand stages as fit next to the epilogue staging (static shared memory and
+  static constexpr int EPI_BYTES = CT ? kEpiWarps * kCSlots * kCBox : kEpiWarps * 32 * kStage * 4;
+  // as many operand stages as fit next to the epilogue buffers (static shared memory and
   // the 1 KB alignment slack kept aside)
   static constexpr int NSTAGE = (kSmemOptin - 512 - EPI_BYTES - 1024) / OPER_BYTES;
   static constexpr int SMEM = NSTAGE * OPER_BYTES + EPI_BYTES + 1024;
   static constexpr uint32_t IDESC = make_idesc(MODE == 0 ? 2u : 1u, kBM, kBN);
-  static_assert(NSTAGE >= 2, "at least two operand stages");
+  static_assert(NSTAGE >= 1, "operand stages");
 };
 
 __constant__ int c_prod_a[6] = {0, 0, 1, 0, 2, 1};
@@ -174,6 +181,37 @@ __device__ __forceinline__ double f2d_int(float f) {
   return __longlong_as_double(static_cast<long long>(d));
 }
 
+// Ask L2 to fetch the part of one row of C that a warp will update next: the 16-byte
+// aligned interior of [p, p + ncols) (bulk prefetch wants 16-byte aligned address and size;
+// the few bytes outside it are simply not prefetched).  Only addresses inside the row are
+// named, so the hint never reaches past the matrix.
+__device__ __forceinline__ void prefetch_row_l2(const double* p, int ncols) {
+  if (ncols <= 0) return;
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t lo = (a0 + 15) & ~uintptr_t(15);
+  const uintptr_t hi = (a0 + static_cast<uintptr_t>(ncols) * 8u) & ~uintptr_t(15);
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"(static_cast<uint32_t>(hi - lo))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(x), "r"(y), "r"(smem_u32(src))
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// stores issued by this thread: wait until all but the newest N have read shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -181,16 +219,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // Persistent, warp-specialized: warp 0 (one lane) streams operand tiles with TMA into an
 // NSTAGE ring, warp 1 (one lane) issues the MMAs into one of two TMEM accumulators, warps
 // 2..9 drain the other accumulator into C.  Tiles are taken round-robin by CTA.
-template <int MODE>
+template <int MODE, int CT>
 __global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                 const __grid_constant__ CUtensorMap tmB,
+                                                                const __grid_constant__ CUtensorMap tmC,
                                                                 int M, int N, int kblocks, int Mpad, int Npad,
                                                                 double* __restrict__ C, long long ldc,
                                                                 DevState* st, int track) {
-  using Cfg = TcCfg<MODE>;
+  using Cfg = TcCfg<MODE, CT>;
   constexpr int NSTG = Cfg::NSTAGE;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[NSTG], empty[NSTG], accf[2], acce[2];
+  __shared__ __align__(8) uint64_t cbar[CT ? kEpiWarps * kCSlots : 1];
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   if (dev_status(st) != 0) return;
@@ -207,6 +247,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(const __grid_con
   if (tid == 32) {
     for (int i = 0; i < NSTG; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
     for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], kEpiWarps); }
+    if (CT)
+      for (int i = 0; i < kEpiWarps * kCSlots; ++i) mbar_init(&cbar[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
@@ -215,15 +257,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(const __grid_con
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   unsigned long long cmax_bits = 0ull;          // max |C| as a non-negative IEEE bit pattern
+  int p_it = 0;                                 // operand loads issued (producer lane)
 
   if (warp == 0) {
     if (lane == 0) {                                         // ---- TMA producer
-      int it = 0;
       for (int tile = blockIdx.x; tile < tiles && !s_fail; tile += gridDim.x) {
         const int bm = (tile / tiles_n) * kBM, bn = (tile % tiles_n) * kBN;
-        for (int kb = 0; kb < kblocks; ++kb, ++it) {
-          const int s = it % NSTG;
-          if (!mbar_wait_bounded(&empty[s], ((it / NSTG) & 1) ^ 1)) { s_fail = 1; break; }
+        for (int kb = 0; kb < kblocks; ++kb, ++p_it) {
+          const int s = p_it % NSTG;
+          if (!mbar_wait_bounded(&empty[s], ((p_it / NSTG) & 1) ^ 1)) { s_fail = 1; break; }
           uint8_t* sA = base + s * Cfg::OPER_BYTES;
           uint8_t* sB = sA + Cfg::NS * Cfg::CH * Cfg::TILE_A;
           mbar_expect_tx(&full[s], Cfg::OPER_BYTES);
@@ -266,19 +308,104 @@ __global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(const __grid_con
         umma_commit(&accf[a]);                               // accumulator ready
       }
     }
-  } else {                                                   // ---- epilogue warps
+  } else if constexpr (CT) {                                 // ---- epilogue warps, C by TMA
+    // Warp (q, cq) owns rows 32q..32q+31 and columns 32cq..32cq+31 of every tile, as two
+    // 32 x 16 boxes, one shared-memory slot each.  The boxes of the next tile are loaded
+    // while the current tile drains: a slot is refilled as soon as the TMA store of its
+    // previous contents has read it.  Lane i updates row i of a box in place.
+    const int q = warp & 3, cq = (warp - 2) >> 2, ew = warp - 2;
+    uint8_t* ring = base + NSTG * Cfg::OPER_BYTES + ew * kCSlots * kCBox;
+    uint64_t* cb = &cbar[ew * kCSlots];
+    uint32_t phase = 0u, pending = 0u;       // per-slot barrier parity; loads not yet consumed
+    auto box_x = [&](int t, int slot) { return (t % tiles_n) * kBN + cq * 32 + slot * 16; };
+    auto box_y = [&](int t) { return (t / tiles_n) * kBM + q * 32; };
+    auto refill = [&](int t, int slot) {     // lane 0: load box `slot` of tile t if it holds C
+      if (t < tiles && box_y(t) < M && box_x(t, slot) < N) {
+        mbar_expect_tx(&cb[slot], kCBox);
+        tma_load_2d(ring + slot * kCBox, &tmC, box_x(t, slot), box_y(t), &cb[slot]);
+        pending |= 1u << slot;
+      }
+    };
+    if (lane == 0)
+      for (int slot = 0; slot < kCSlots; ++slot) refill(blockIdx.x, slot);
+    int tcount = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tcount) {
+      const int a = tcount & 1;
+      // every lane observes the barrier itself; a timeout in any lane fails the whole warp
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&accf[a], (tcount >> 1) & 1))) { s_fail = 1; break; }
+      tc_fence_after();
+      uint32_t acc[32];
+      tmem_ld32(tmem + a * kBN + (static_cast<uint32_t>(q * 32) << 16) + cq * 32, acc);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[a]);                  // accumulator free again
+      const int y = box_y(tile), next = tile + gridDim.x;
+      bool failed = false;
+#pragma unroll
+      for (int slot = 0; slot < kCSlots; ++slot) {
+        const bool live = y < M && box_x(tile, slot) < N;
+        if (live) {
+          if (!__all_sync(0xffffffffu, mbar_wait_bounded(&cb[slot], (phase >> slot) & 1u))) { failed = true; break; }
+          phase ^= 1u << slot;
+          pending &= ~(1u << slot);
+          uint8_t* row = ring + slot * kCBox + lane * 128;
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            double2* cp = reinterpret_cast<double2*>(row + ((p ^ (lane & 7)) << 4));
+            double2 cv = *cp;
+            cv.x -= f2d_int(__uint_as_float(acc[slot * 16 + 2 * p]));
+            cv.y -= f2d_int(__uint_as_float(acc[slot * 16 + 2 * p + 1]));
+            *cp = cv;
+            cmax_bits = max_bits(cmax_bits, max_bits(abs_bits(cv.x), abs_bits(cv.y)));
+          }
+          fence_proxy_async();                               // generic writes -> TMA store
+          __syncwarp();
+          if (lane == 0) tma_store_2d(&tmC, ring + slot * kCBox, box_x(tile, slot), y);
+        }
+        // the previous slot's store has read its box once at most the newest store is
+        // pending: refill it with the next tile's box
+        if (lane == 0 && slot > 0) {
+          if (live) bulk_wait_read<1>(); else bulk_wait_read<0>();
+          refill(next, slot - 1);
+        }
+        __syncwarp();
+      }
+      if (failed) { s_fail = 1; break; }
+      if (lane == 0) {
+        bulk_wait_read<0>();
+        refill(next, kCSlots - 1);
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      bulk_wait_all();                                       // stores finished
+      for (int slot = 0; slot < kCSlots; ++slot)             // loads in flight after a failure
+        if ((pending >> slot) & 1u) mbar_wait_bounded(&cb[slot], (phase >> slot) & 1u);
+    }
+    __syncwarp();
+  } else {                                                   // ---- epilogue warps, C by registers
     const int q = warp & 3;                                  // TMEM lane quarter of this warp
-    const int h = (warp - 2) >> 2;                           // column half
+    const int cq = (warp - 2) >> 2;                          // column quarter
     float* stage = reinterpret_cast<float*>(base + NSTG * Cfg::OPER_BYTES) + (warp - 2) * 32 * kStage;
+    // each lane owns one row of this warp's 32 x 32 region of a tile: the row of the next
+    // tile is prefetched into L2 while the current one drains
+    auto prefetch_tile = [&](int t) {
+      if (t >= tiles) return;
+      const int r = (t / tiles_n) * kBM + q * 32 + lane, c = (t % tiles_n) * kBN + cq * 32;
+      if (r < M && c < N) prefetch_row_l2(C + static_cast<long long>(r) * ldc + c, min(32, N - c));
+    };
+    prefetch_tile(blockIdx.x);
     int tcount = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tcount) {
       const int a = tcount & 1;
       const int bm = (tile / tiles_n) * kBM, bn = (tile % tiles_n) * kBN;
+      prefetch_tile(tile + gridDim.x);
       if (!mbar_wait_bounded(&accf[a], (tcount >> 1) & 1)) { s_fail = 1; break; }
       tc_fence_after();
       const int rbase = bm + q * 32;
       const int nrows = min(32, M - rbase);
-      for (int c0 = h * 64; c0 < h * 64 + 64; c0 += 32) {
+      {
+        const int c0 = cq * 32;
         uint32_t r[32];
         tmem_ld32(tmem + a * kBN + (static_cast<uint32_t>(q * 32) << 16) + c0, r);
 #pragma unroll
@@ -299,9 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(const __grid_con
               if (h16 + rr < nrows) {
                 const double v = cv[rr] - f2d_int(stage[(h16 + rr) * kStage + lane]);
                 __stcs(cp + (h16 + rr) * ldci, v);
-                const unsigned long long vb =
-                    static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull;
-                cmax_bits = vb > cmax_bits ? vb : cmax_bits;
+                cmax_bits = max_bits(cmax_bits, abs_bits(v));
               }
           }
         }
@@ -314,15 +439,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(const __grid_con
   }
   if (track && warp >= 2) {
     for (int off = 16; off > 0; off >>= 1) {
-      const unsigned long long o = __shfl_xor_sync(0xffffffffu, cmax_bits, off);
-      cmax_bits = o > cmax_bits ? o : cmax_bits;
+      cmax_bits = max_bits(cmax_bits, __shfl_xor_sync(0xffffffffu, cmax_bits, off));
     }
     // NaN bit patterns sort above every finite value; the input scan rejects them earlier
     if (lane == 0) atomicMax(&st->gmax_bits, cmax_bits);
   }
   tc_fence_before();
   __syncthreads();
+  if (warp == 0 && lane == 0 && s_fail) {
+    // operand loads still in flight after a failure: the last load into each stage
+    for (int i = p_it - 1; i >= 0 && i >= p_it - NSTG; --i) mbar_wait_bounded(&full[i % NSTG], (i / NSTG) & 1);
+  }
   if (s_fail && tid == 0) set_error(st, PRRP_ERR_TIMEOUT);
+  __syncwarp();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
@@ -396,11 +525,44 @@ bool make_map(CUtensorMap* m, void* base, int mode, int rows_total, int kpad) {
   return r == CUDA_SUCCESS;
 }
 
+// 2-D map over the FP64 matrix C (M x N, leading dimension ldc), box = 32 rows x 16
+// doubles with 128-byte swizzle; rows and columns past the edge read as zero and are not
+// written back.  Needs a 16-byte aligned C, an even ldc and an even N: the store clips the
+// row at 16-byte granularity, so with an odd N it would also write column N.
+bool make_c_map(CUtensorMap* m, double* C, int M, int N, long long ldc) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(C) & 15u) != 0 || (ldc & 1) != 0 || (N & 1) != 0) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(N), static_cast<cuuint64_t>(M)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldc) * 8};
+  cuuint32_t box[2] = {16, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, C, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int MODE, int CT>
+cudaError_t launch_tc_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mc, int M, int N,
+                             int kblocks, int Mpad, int Npad, double* C, long long ldc, DevState* st, int track,
+                             cudaStream_t s) {
+  using Cfg = TcCfg<MODE, CT>;
+  cudaError_t e = smem_optin(tc_update_kernel<MODE, CT>);
+  if (e != cudaSuccess) return e;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = (Npad / kBN) * (Mpad / kBM);
+  tc_update_kernel<MODE, CT><<<std::min(tiles, sms), kThreads, Cfg::SMEM, s>>>(ma, mb, mc, M, N, kblocks, Mpad,
+                                                                               Npad, C, ldc, st, track);
+  return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t launch_tc_mode(int M, int N, int K, const double* L, long long ldl, const double* U, long long ldu,
                            double* C, long long ldc, DevState* st, int track, void* wsA, void* wsB,
                            cudaStream_t s) {
-  using Cfg = TcCfg<MODE>;
+  using Cfg = TcCfg<MODE, 0>;
   const int kblocks = (K + 63) / 64, kpad = kblocks * 64;
   const int Mpad = (M + kBM - 1) / kBM * kBM, Npad = (N + kBN - 1) / kBN * kBN;
   const long long ta = static_cast<long long>(Mpad) * kpad, tb = static_cast<long long>(Npad) * kpad;
@@ -410,18 +572,12 @@ cudaError_t launch_tc_mode(int M, int N, int K, const double* L, long long ldl, 
       U, ldu, N, K, Npad, kpad, wsB);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  CUtensorMap ma, mb;
+  CUtensorMap ma, mb, mc;
   if (!make_map(&ma, wsA, MODE, Cfg::NS * Mpad, kpad) || !make_map(&mb, wsB, MODE, Cfg::NS * Npad, kpad))
     return cudaErrorInvalidValue;
-  e = smem_optin(tc_update_kernel<MODE>);
-  if (e != cudaSuccess) return e;
-  int sms = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int tiles = (Npad / kBN) * (Mpad / kBM);
-  tc_update_kernel<MODE><<<std::min(tiles, sms), kThreads, Cfg::SMEM, s>>>(ma, mb, M, N, kblocks, Mpad, Npad, C,
-                                                                           ldc, st, track);
-  return cudaGetLastError();
+  if (make_c_map(&mc, C, M, N, ldc))
+    return launch_tc_kernel<MODE, 1>(ma, mb, mc, M, N, kblocks, Mpad, Npad, C, ldc, st, track, s);
+  return launch_tc_kernel<MODE, 0>(ma, mb, ma, M, N, kblocks, Mpad, Npad, C, ldc, st, track, s);
 }
 
 }  // namespace

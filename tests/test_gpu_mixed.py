@@ -61,6 +61,33 @@ def test_schur_update_tensor_cores(prrp, ctx, prec, m, n, k):
     assert rel < (2e-3 if prec == 1 else 1e-5)
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("r0,c0,ld,n", [(3, 2, 1000, 302), (3, 2, 1000, 301), (1, 1, 1000, 302),
+                                        (0, 0, 777, 301), (5, 64, 900, 302), (2, 0, 1000, 302)])
+def test_schur_update_inside_larger_matrix(prrp, ctx, prec, r0, c0, ld, n):
+    """C as a block of a larger row-major matrix: 16-byte aligned blocks with an even
+    leading dimension and column count move through shared memory by TMA, the others
+    through registers; either way only the block changes, including along ragged tile
+    edges."""
+    m, k = 389, 64
+    g = pi.rng(r0 * 31 + c0 * 7 + ld)
+    L, U = g.standard_normal((m, k)), g.standard_normal((k, n))
+    big = g.standard_normal((r0 + m + 7, ld))
+    dbig = torch.from_numpy(big).cuda()
+    prrp.prrp_schur_update(ctx, torch.from_numpy(L).cuda(), torch.from_numpy(U).cuda(),
+                           dbig[r0:r0 + m, c0:c0 + n], prec=prec)
+    got = dbig.cpu().numpy()
+    want = big.copy()
+    want[r0:r0 + m, c0:c0 + n] -= L @ U
+    outside = np.ones(big.shape, dtype=bool)
+    outside[r0:r0 + m, c0:c0 + n] = False
+    assert np.array_equal(got[outside], big[outside])
+    S = np.abs(L) @ np.abs(U)
+    blk = got[r0:r0 + m, c0:c0 + n]
+    assert np.all(np.abs(blk - want[r0:r0 + m, c0:c0 + n]) <= _bound(prec, k, S)
+                  + 4 * EPS * np.abs(big[r0:r0 + m, c0:c0 + n]))
+
+
 def _mixed_solve(prrp, ctx, A, B, prec, b):
     dA = torch.from_numpy(A).cuda()
     F = prrp.prrp_factor(ctx, dA, b=b, prec=prec)
