@@ -84,6 +84,21 @@ struct prrp_ctx {
   size_t a12_cap = 0;
   unsigned char* tcws2 = nullptr;
   size_t tcws2_cap = 0;
+  // substitution: inverted diagonal blocks (FP64 and FP32), FP32 copy of the factors, the
+  // factorization they were made from (generation number), step counters
+  double* dinv64 = nullptr;
+  size_t dinv64_cap = 0;
+  unsigned long long dinv64_gen = 0;
+  float* dinv32 = nullptr;
+  size_t dinv32_cap = 0;
+  float* lu32 = nullptr;
+  size_t lu32_cap = 0;
+  unsigned long long lu32_gen = 0;
+  float* y32 = nullptr;
+  size_t y32_cap = 0;
+  unsigned* tcount = nullptr;
+  size_t tcount_cap = 0;
+  unsigned long long factor_gen = 0;
   // batched solves: metadata, per-CTA workspace, outputs, tuned launch shapes, graphs
   unsigned char* bmeta = nullptr;
   size_t bmeta_cap = 0;
@@ -114,6 +129,7 @@ struct prrp_factors {
   int* perm = nullptr;          // device, owned
   prrp_factor_stats stats{};
   prrp_opts opts{};
+  unsigned long long gen = 0;   // identifies this factorization to the context's solve caches
 };
 
 namespace {
@@ -341,7 +357,8 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
   if (ctx->bout) cudaFree(ctx->bout);
   void* ptrs[] = {ctx->st, ctx->xval, ctx->xkey, ctx->xvec, ctx->pairs, ctx->ipiv, ctx->order,
                   ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB, ctx->tcws,
-                  ctx->l21b, ctx->a12, ctx->tcws2};
+                  ctx->l21b, ctx->a12, ctx->tcws2, ctx->dinv64, ctx->dinv32, ctx->lu32, ctx->y32,
+                  ctx->tcount};
   for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
   if (ctx->s_rest) cudaStreamDestroy(ctx->s_rest);
   if (ctx->s_blk) cudaStreamDestroy(ctx->s_blk);
@@ -368,7 +385,7 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
 
   prrp_factors* f = new (std::nothrow) prrp_factors();
   if (!f) return PRRP_ERR_OOM;
-  f->ctx = ctx; f->n = n; f->dA = dA; f->lda = lda; f->opts = o;
+  f->ctx = ctx; f->n = n; f->dA = dA; f->lda = lda; f->opts = o; f->gen = ++ctx->factor_gen;
   auto fail = [&](prrp_status st) { prrp_factors_destroy(f); return st; };
   cudaError_t e = cudaMalloc(&f->perm, sizeof(int) * std::max(n, 1));
   if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "cudaMalloc perm"));
@@ -534,15 +551,69 @@ void prrp_factors_destroy(prrp_factors* F) {
   delete F;
 }
 
+// Inverted diagonal blocks (and for FP32 the FP32 copy of L\U) of factorization F, made
+// on first use and kept in the context until another factorization is solved.
+static prrp_status prepare_solve(prrp_ctx* ctx, const prrp_factors* F, bool fp32, cudaStream_t s) {
+  const int n = F->n, nb = (n + 63) / 64;
+  prrp_status ps = grow(ctx, &ctx->tcount, &ctx->tcount_cap, (size_t)nb);
+  if (ps != PRRP_OK) return ps;
+  cudaError_t e;
+  if (!fp32) {
+    if (ctx->dinv64_gen == F->gen) return PRRP_OK;
+    if ((ps = grow(ctx, &ctx->dinv64, &ctx->dinv64_cap, (size_t)2 * nb * 4096)) != PRRP_OK) return ps;
+    Timed t(ctx, s, PRRP_KIND_SOLVE, 2LL * nb * 64 * 64 * 64 / 3);
+    if ((e = launch_invert_diag(F->dA, F->lda, n, ctx->dinv64, 0, s)) != cudaSuccess) return cuda_fail(ctx, e, "invert");
+    ctx->dinv64_gen = F->gen;
+    return PRRP_OK;
+  }
+  if (ctx->lu32_gen == F->gen) return PRRP_OK;
+  if ((ps = grow(ctx, &ctx->dinv32, &ctx->dinv32_cap, (size_t)2 * nb * 4096)) != PRRP_OK) return ps;
+  if ((ps = grow(ctx, &ctx->lu32, &ctx->lu32_cap, (size_t)n * n)) != PRRP_OK) return ps;
+  {
+    Timed t(ctx, s, PRRP_KIND_SOLVE, 2LL * nb * 64 * 64 * 64 / 3);
+    if ((e = launch_invert_diag(F->dA, F->lda, n, ctx->dinv32, 1, s)) != cudaSuccess) return cuda_fail(ctx, e, "invert");
+  }
+  {
+    Timed t(ctx, s, PRRP_KIND_SOLVE);
+    if ((e = launch_convert_lu32(F->dA, F->lda, n, ctx->lu32, s)) != cudaSuccess) return cuda_fail(ctx, e, "convert");
+  }
+  ctx->lu32_gen = F->gen;
+  return PRRP_OK;
+}
+
+// Y = U^-1 L^-1 P B in FP64.
 static prrp_status solve_into(prrp_ctx* ctx, const prrp_factors* F, const double* B, long long ldb,
                               int nrhs, double* Y, cudaStream_t s) {
   cudaError_t e;
+  prrp_status ps = prepare_solve(ctx, F, false, s);
+  if (ps != PRRP_OK) return ps;
   const int nb = (F->n + 63) / 64;
   Timed t(ctx, s, PRRP_KIND_SOLVE, 2LL * F->n * F->n * nrhs);
   ctx->kind_launches[PRRP_KIND_SOLVE] += 2LL * nb;   // gather + 2 nb substitution steps
   if ((e = launch_gather_rows(B, ldb, F->perm, F->n, nrhs, Y, s)) != cudaSuccess) return cuda_fail(ctx, e, "gather");
-  if ((e = launch_trsv_lower_unit(F->dA, F->lda, F->n, Y, nrhs, s)) != cudaSuccess) return cuda_fail(ctx, e, "trsv L");
-  if ((e = launch_trsv_upper(F->dA, F->lda, F->n, Y, nrhs, s)) != cudaSuccess) return cuda_fail(ctx, e, "trsv U");
+  if ((e = launch_trsv(F->dA, F->lda, ctx->dinv64, F->n, Y, nrhs, 1, 0, ctx->tcount, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "trsv L");
+  if ((e = launch_trsv(F->dA, F->lda, ctx->dinv64, F->n, Y, nrhs, 0, 0, ctx->tcount, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "trsv U");
+  return PRRP_OK;
+}
+
+// ctx->y32 = U^-1 L^-1 P B in FP32 arithmetic (B rounded to FP32).
+static prrp_status solve_into32(prrp_ctx* ctx, const prrp_factors* F, const double* B, long long ldb, int nrhs,
+                                cudaStream_t s) {
+  cudaError_t e;
+  prrp_status ps = prepare_solve(ctx, F, true, s);
+  if (ps != PRRP_OK) return ps;
+  if ((ps = grow(ctx, &ctx->y32, &ctx->y32_cap, (size_t)F->n * nrhs)) != PRRP_OK) return ps;
+  const int nb = (F->n + 63) / 64;
+  Timed t(ctx, s, PRRP_KIND_SOLVE, 2LL * F->n * F->n * nrhs);
+  ctx->kind_launches[PRRP_KIND_SOLVE] += 2LL * nb;
+  if ((e = launch_gather_rows32(B, ldb, F->perm, F->n, nrhs, ctx->y32, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "gather");
+  if ((e = launch_trsv(ctx->lu32, F->n, ctx->dinv32, F->n, ctx->y32, nrhs, 1, 1, ctx->tcount, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "trsv L");
+  if ((e = launch_trsv(ctx->lu32, F->n, ctx->dinv32, F->n, ctx->y32, nrhs, 0, 1, ctx->tcount, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "trsv U");
   return PRRP_OK;
 }
 
@@ -570,9 +641,17 @@ prrp_status prrp_solve(prrp_ctx* ctx, const prrp_factors* F, const double* dA_or
   double* R = Y + blk;
   double* B0 = R + blk;
   const bool refine = dA_orig != nullptr;
+  // factors from a low-precision Schur update are only about FP32-accurate: with the FP64
+  // residual of the refinement, FP32 substitution converges as fast and costs far less
+  const bool low = refine && F->opts.prec != PRRP_FP64;
   if (refine) CK(launch_copy_rows(dB, ldb, B0, nrhs, n, nrhs, s));
-  if ((ps = solve_into(ctx, F, dB, ldb, nrhs, Y, s)) != PRRP_OK) return ps;
-  {
+  if (low) {
+    if ((ps = solve_into32(ctx, F, dB, ldb, nrhs, s)) != PRRP_OK) return ps;
+    Timed t(ctx, s, PRRP_KIND_SOLVE);
+    CK(cudaMemset2DAsync(dB, sizeof(double) * ldb, 0, sizeof(double) * nrhs, n, s));
+    CK(launch_axpy_rows32(dB, ldb, ctx->y32, 1.0, n, nrhs, s));
+  } else {
+    if ((ps = solve_into(ctx, F, dB, ldb, nrhs, Y, s)) != PRRP_OK) return ps;
     Timed t(ctx, s, PRRP_KIND_SOLVE);
     CK(launch_copy_rows(Y, nrhs, dB, ldb, n, nrhs, s));
   }
@@ -605,13 +684,21 @@ prrp_status prrp_solve(prrp_ctx* ctx, const prrp_factors* F, const double* dA_or
   bool exhausted = false;
   while (eta > o.refine_target) {
     if (it == o.refine_max_iter) { exhausted = true; break; }
-    if ((ps = solve_into(ctx, F, R, nrhs, nrhs, Y, s)) != PRRP_OK) return ps;
-    CK(launch_axpy_rows(dB, ldb, Y, 1.0, n, nrhs, s));
+    if (low) {
+      if ((ps = solve_into32(ctx, F, R, nrhs, nrhs, s)) != PRRP_OK) return ps;
+      CK(launch_axpy_rows32(dB, ldb, ctx->y32, 1.0, n, nrhs, s));
+    } else {
+      if ((ps = solve_into(ctx, F, R, nrhs, nrhs, Y, s)) != PRRP_OK) return ps;
+      CK(launch_axpy_rows(dB, ldb, Y, 1.0, n, nrhs, s));
+    }
     double e2 = 0.0;
     if ((ps = eta_now(&e2)) != PRRP_OK) return ps;
     ++it;
     if (e2 > eta / 2) {              // stagnation: keep the better of the last two
-      if (e2 > eta) CK(launch_axpy_rows(dB, ldb, Y, -1.0, n, nrhs, s));
+      if (e2 > eta) {
+        if (low) CK(launch_axpy_rows32(dB, ldb, ctx->y32, -1.0, n, nrhs, s));
+        else CK(launch_axpy_rows(dB, ldb, Y, -1.0, n, nrhs, s));
+      }
       eta = std::min(eta, e2);
       break;
     }

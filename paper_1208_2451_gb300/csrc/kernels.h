@@ -104,10 +104,18 @@ cudaError_t launch_batch_fill(double* A, int n, int count, double* B, cudaStream
 cudaError_t launch_norm1(const double* A, long long lda, int n, double* out, cudaStream_t s);
 cudaError_t launch_gather_rows(const double* B, long long ldb, const int* perm, int n, int nrhs,
                                double* Y, cudaStream_t s);
-cudaError_t launch_trsv_lower_unit(const double* LU, long long lda, int n, double* Y, int nrhs,
-                                   cudaStream_t s);
-cudaError_t launch_trsv_upper(const double* LU, long long lda, int n, double* Y, int nrhs,
-                              cudaStream_t s);
+// Inverses of the 64 x 64 diagonal blocks of L (unit lower) and U, as T = float (fp32) or
+// double: Dinv[2][nb][64 x 64] row-major, L first.
+cudaError_t launch_invert_diag(const double* LU, long long lda, int n, void* dinv, int fp32, cudaStream_t s);
+// Y <- L^-1 Y (lower) or U^-1 Y with the factors LU (T, leading dimension lda) and their
+// inverted diagonal blocks; Y is n x nrhs row-major (T); counters: nb unsigned scratch.
+cudaError_t launch_trsv(const void* LU, long long lda, const void* dinv, int n, void* Y, int nrhs, int lower,
+                        int fp32, unsigned* counters, cudaStream_t s);
+cudaError_t launch_convert_lu32(const double* LU, long long lda, int n, float* out, cudaStream_t s);
+cudaError_t launch_gather_rows32(const double* B, long long ldb, const int* perm, int n, int nrhs, float* Y,
+                                 cudaStream_t s);
+cudaError_t launch_axpy_rows32(double* X, long long ldx, const float* D, double alpha, int n, int nrhs,
+                               cudaStream_t s);
 cudaError_t launch_residual(const double* A, long long lda, int n, const double* X, long long ldx,
                             int nrhs, const double* B, long long ldb, double* R, double* norms,
                             cudaStream_t s);

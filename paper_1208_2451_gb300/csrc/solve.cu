@@ -1,10 +1,9 @@
 // Triangular solves and FP64 residuals with the in-place L\U of LU_PRRP (the solver tests
 // of Section 2.3; the refinement of Section 3.3).
 //
-// Forward and back substitution are blocked by 64 rows.  Launch j updates every later row
-// block with the 64 unknowns of block j (a GEMV/GEMM strip, HBM-bound on L or U), and the
-// CTA that owns block j+1 then solves its 64 x 64 triangle with one warp per right-hand
-// side (shuffle broadcast of each solved unknown), so the next launch can use it.
+// Forward and back substitution are blocked by 64 rows with inverted diagonal blocks (see
+// the substitution section below).  The refinement residual is always FP64; factors from a
+// low-precision Schur update are applied in FP32 for the correction solves.
 #include <algorithm>
 
 #include "common.cuh"
@@ -14,6 +13,7 @@ namespace prrp {
 
 constexpr int kSB = 64;          // solve block rows
 constexpr int kSolveThreads = 256;
+constexpr int kB1 = kSB + 1;   // padded row of a staged diagonal block
 
 __global__ void gather_rows_kernel(const double* __restrict__ B, long long ldb,
                                    const int* __restrict__ perm, int n, int nrhs,
@@ -35,107 +35,250 @@ cudaError_t launch_gather_rows(const double* B, long long ldb, const int* perm, 
   return cudaGetLastError();
 }
 
-// Solve the kb x kb triangle at rows [r0, r0 + kb) of Y in place, one warp per column.
-// lower: unit lower L; otherwise upper U (divides by the diagonal).
-__device__ void solve_diag_block(const double* __restrict__ LU, long long lda, double* Y,
-                                 int nrhs, int r0, int kb, bool lower) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  for (int c = warp; c < nrhs; c += nwarps) {
-    // lane holds rows r0 + lane and r0 + lane + 32
-    double y0 = lane < kb ? Y[(long long)(r0 + lane) * nrhs + c] : 0.0;
-    double y1 = lane + 32 < kb ? Y[(long long)(r0 + lane + 32) * nrhs + c] : 0.0;
-    if (lower) {
-      for (int k = 0; k < kb; ++k) {
-        const double xk = __shfl_sync(0xffffffffu, k < 32 ? y0 : y1, k & 31);
-        const int i0 = lane, i1 = lane + 32;
-        if (i0 > k && i0 < kb) y0 = fma(-LU[(long long)(r0 + i0) * lda + r0 + k], xk, y0);
-        if (i1 > k && i1 < kb) y1 = fma(-LU[(long long)(r0 + i1) * lda + r0 + k], xk, y1);
-      }
-    } else {
-      for (int k = kb - 1; k >= 0; --k) {
-        const int ko = k & 31;
-        if (k < 32) { if (lane == ko) y0 = y0 / LU[(long long)(r0 + k) * lda + r0 + k]; }
-        else        { if (lane == ko) y1 = y1 / LU[(long long)(r0 + k) * lda + r0 + k]; }
-        const double xk = __shfl_sync(0xffffffffu, k < 32 ? y0 : y1, ko);
-        const int i0 = lane, i1 = lane + 32;
-        if (i0 < k) y0 = fma(-LU[(long long)(r0 + i0) * lda + r0 + k], xk, y0);
-        if (i1 < k) y1 = fma(-LU[(long long)(r0 + i1) * lda + r0 + k], xk, y1);
-      }
+// ---------------------------------------------------------------- blocked substitution
+//
+// Diagonal blocks are inverted once per factorization (invert_diag_kernel), so solving a
+// 64 x 64 triangle is a small GEMV instead of a 64-step dependent chain.  Substitution
+// step j then is one launch: every CTA owns a 16-row chunk of a later row block and
+// subtracts L_ij x_j (forward) or U_ij x_j (backward) from it; the CTA that completes the
+// last chunk of the next block (a counter per block, fenced) applies that block's inverse,
+// making x_{j+1} (x_{j-1}) final for the next launch.  T = double or float.
+
+constexpr int kRC = 16;          // rows per chunk CTA
+constexpr int kXS = 16;          // right-hand sides staged per pass
+constexpr int kXP = kXS + 1;     // padded row of the staged unknowns (conflict-free split-k reads)
+
+// Column t of the inverse of one diagonal block, by substitution against e_t, all columns
+// in lockstep (thread t).  blockIdx.y = 0: unit lower L; 1: upper U.
+template <typename T>
+__global__ void __launch_bounds__(kSB) invert_diag_kernel(const double* __restrict__ LU, long long lda, int n,
+                                                         T* __restrict__ Dinv) {
+  extern __shared__ double dsm[];
+  double* S = dsm;                    // the block, rows padded to kB1
+  double* X = S + kSB * kB1;          // the inverse, column t owned by thread t
+  double* rd = X + kSB * kB1;         // reciprocals of the diagonal
+  const int nb = (n + kSB - 1) / kSB, b = blockIdx.x, upper = blockIdx.y;
+  const int r0 = b * kSB, kb = min(kSB, n - r0), t = threadIdx.x;
+  for (int e = t; e < kSB * kSB; e += kSB) {
+    const int i = e / kSB, k = e - i * kSB;
+    S[i * (kSB + 1) + k] = (i < kb && k < kb) ? LU[(long long)(r0 + i) * lda + r0 + k] : 0.0;
+  }
+  __syncthreads();
+  rd[t] = t < kb ? 1.0 / S[t * kB1 + t] : 0.0;
+  __syncthreads();
+  if (!upper) {
+    for (int i = 0; i < kb; ++i) {
+      double acc = 0.0;
+      for (int k = 0; k < i; ++k) acc = fma(S[i * kB1 + k], X[k * kB1 + t], acc);
+      X[i * kB1 + t] = (i == t) ? 1.0 : (i > t ? -acc : 0.0);
     }
-    if (lane < kb) Y[(long long)(r0 + lane) * nrhs + c] = y0;
-    if (lane + 32 < kb) Y[(long long)(r0 + lane + 32) * nrhs + c] = y1;
+  } else {
+    for (int i = kb - 1; i >= 0; --i) {
+      double acc = 0.0;
+      for (int k = i + 1; k < kb; ++k) acc = fma(S[i * kB1 + k], X[k * kB1 + t], acc);
+      X[i * kB1 + t] = (i == t) ? rd[i] : (i < t ? -acc * rd[i] : 0.0);
+    }
+  }
+  __syncthreads();
+  T* out = Dinv + ((size_t)upper * nb + b) * kSB * kSB;
+  for (int e = t; e < kSB * kSB; e += kSB) {
+    const int i = e / kSB, k = e - i * kSB;
+    out[e] = static_cast<T>((i < kb && k < kb) ? X[i * kB1 + k] : 0.0);
   }
 }
 
-// One step of blocked substitution.  jb = block just solved (-1: none yet).  CTA b updates
-// row block `blk` with the solved unknowns of jb: one warp per row, lanes along k (each
-// row of the 64 x 64 block is two coalesced 256-byte loads), the 64 solved unknowns of
-// each right-hand side staged in shared memory.  The CTA of the block that becomes final
-// next then solves its triangle.
-constexpr int kStageRhs = 32;    // right-hand sides staged per pass
+// Y[rows] -= M[rows, c0:c0+kc] * Xs for `nr` rows of one chunk.  Ms: nr x kSB, Xs: kSB x kXP
+// in shared memory; the outputs (row, column) are split over the CTA with `sk` threads per
+// output summing interleaved k and reducing by shuffles (fixed order: deterministic).
+template <typename T>
+__device__ __forceinline__ void chunk_gemv(const T* Ms, const T* Xs, int nr, int kc, int nc, T* Y, int ldy,
+                                           int row0, int col0, bool subtract) {
+  const int outs = nr * nc;
+  int sk = 1;
+  while (sk < 16 && outs * sk * 2 <= kSolveThreads) sk *= 2;
+  const int kk = threadIdx.x & (sk - 1);
+  for (int o = threadIdx.x / sk; o < ((outs + (kSolveThreads / sk) - 1) / (kSolveThreads / sk)) * (kSolveThreads / sk);
+       o += kSolveThreads / sk) {
+    const bool live = o < outs;
+    const int i = live ? o / nc : 0, c = live ? o - (o / nc) * nc : 0;
+    T acc0 = 0, acc1 = 0;
+    if (live) {
+      int k = kk;
+      for (; k + sk < kc; k += 2 * sk) {
+        acc0 = fma(Ms[i * kSB + k], Xs[k * kXP + c], acc0);
+        acc1 = fma(Ms[i * kSB + k + sk], Xs[(k + sk) * kXP + c], acc1);
+      }
+      if (k < kc) acc0 = fma(Ms[i * kSB + k], Xs[k * kXP + c], acc0);
+    }
+    T acc = acc0 + acc1;
+    for (int off = 1; off < sk; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (live && kk == 0) {
+      T* y = Y + (long long)(row0 + i) * ldy + col0 + c;
+      *y = subtract ? *y - acc : acc;
+    }
+  }
+}
 
-__global__ void __launch_bounds__(kSolveThreads) trsv_step_kernel(const double* __restrict__ LU,
-                                                                  long long lda, int n, double* Y,
-                                                                  int nrhs, int jb, int lower) {
-  __shared__ double xs[kSB * kStageRhs];
-  const int nb = (n + kSB - 1) / kSB;
-  int blk, next;
-  if (lower) { blk = jb + 1 + blockIdx.x; next = jb + 1; }
-  else       { blk = (jb < 0 ? nb : jb) - 1 - blockIdx.x; next = (jb < 0 ? nb : jb) - 1; }
-  if (blk < 0 || blk >= nb) return;
-  const int r0 = blk * kSB, kb = min(kSB, n - r0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  if (jb >= 0) {
-    const int c0 = jb * kSB, kc = min(kSB, n - c0);
-    for (int cb = 0; cb < nrhs; cb += kStageRhs) {
-      const int nc = min(kStageRhs, nrhs - cb);
-      __syncthreads();
-      for (int e = threadIdx.x; e < kc * nc; e += blockDim.x) {
-        const int k = e / nc, c = e - k * nc;
-        xs[k * kStageRhs + c] = Y[(long long)(c0 + k) * nrhs + cb + c];
-      }
-      __syncthreads();
-      // Y[r0:r0+kb, cb:cb+nc] -= LU[r0:r0+kb, c0:c0+kc] * xs
-      for (int i = warp; i < kb; i += nwarps) {
-        const double* a = LU + (long long)(r0 + i) * lda + c0;
-        const double a0 = lane < kc ? a[lane] : 0.0;
-        const double a1 = lane + 32 < kc ? a[lane + 32] : 0.0;
-        for (int c = 0; c < nc; ++c) {
-          double acc = a0 * (lane < kc ? xs[lane * kStageRhs + c] : 0.0);
-          if (lane + 32 < kc) acc = fma(a1, xs[(lane + 32) * kStageRhs + c], acc);
-          for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-          if (lane == 0) Y[(long long)(r0 + i) * nrhs + cb + c] -= acc;
-        }
-      }
+// x_b = Dinv_b y_b for block b (rows r0 .. r0 + kb), all right-hand sides, in place.
+template <typename T>
+__device__ void apply_inverse(const T* __restrict__ D, T* Y, int nrhs, int r0, int kb, T* Ms, T* Xs) {
+  for (int e = threadIdx.x; e < kSB * kSB; e += blockDim.x) Ms[e] = D[e];
+  for (int cb = 0; cb < nrhs; cb += kXS) {
+    const int nc = min(kXS, nrhs - cb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSB * nc; e += blockDim.x) {
+      const int k = e / nc, c = e - k * nc;
+      Xs[k * kXP + c] = k < kb ? __ldcg(&Y[(long long)(r0 + k) * nrhs + cb + c]) : T(0);
     }
     __syncthreads();
+    chunk_gemv(Ms, Xs, kb, kb, nc, Y, nrhs, r0, cb, false);
   }
-  if (blk == next) solve_diag_block(LU, lda, Y, nrhs, r0, kb, lower != 0);
 }
 
-static cudaError_t trsv(const double* LU, long long lda, int n, double* Y, int nrhs, bool lower,
-                        cudaStream_t s) {
-  if (n == 0 || nrhs == 0) return cudaSuccess;
+template <typename T>
+__global__ void __launch_bounds__(kSolveThreads) trsv_first_kernel(const T* __restrict__ Dinv, int n, T* Y,
+                                                                   int nrhs, int lower) {
+  __shared__ T Ms[kSB * kSB];
+  __shared__ T Xs[kSB * kXP];
+  const int nb = (n + kSB - 1) / kSB, b = lower ? 0 : nb - 1;
+  const int r0 = b * kSB, kb = min(kSB, n - r0);
+  apply_inverse(Dinv + ((size_t)(lower ? 0 : 1) * nb + b) * kSB * kSB, Y, nrhs, r0, kb, Ms, Xs);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSolveThreads) trsv_step_kernel(const T* __restrict__ LU, long long lda,
+                                                                  const T* __restrict__ Dinv, int n, T* Y,
+                                                                  int nrhs, int j, int lower,
+                                                                  unsigned* __restrict__ counters) {
+  __shared__ T Ms[kSB * kSB];      // the chunk's rows of L or U, later the next block's inverse
+  __shared__ T Xs[kSB * kXP];
+  __shared__ int s_last;
   const int nb = (n + kSB - 1) / kSB;
-  // first launch: solve the first block only; then nb - 1 update+solve launches, the last
-  // update launch needs no further solve.
-  trsv_step_kernel<<<1, kSolveThreads, 0, s>>>(LU, lda, n, Y, nrhs, -1, lower);
-  for (int j = 0; j < nb - 1; ++j) {
-    const int jb = lower ? j : nb - 1 - j;
-    trsv_step_kernel<<<nb - 1 - j, kSolveThreads, 0, s>>>(LU, lda, n, Y, nrhs, jb, lower);
+  const int per = kSB / kRC;                       // chunks per block
+  const int blk = lower ? j + 1 + (int)blockIdx.x / per : j - 1 - (int)blockIdx.x / per;
+  const int next = lower ? j + 1 : j - 1;
+  const int r0 = blk * kSB + ((int)blockIdx.x % per) * kRC;
+  const int nr = max(0, min(kRC, n - r0));
+  const int c0 = j * kSB, kc = min(kSB, n - c0);
+  for (int e = threadIdx.x; e < kRC * kSB; e += blockDim.x) {
+    const int i = e / kSB, k = e - i * kSB;
+    Ms[e] = (i < nr && k < kc) ? LU[(long long)(r0 + i) * lda + c0 + k] : T(0);
+  }
+  for (int cb = 0; cb < nrhs; cb += kXS) {
+    const int nc = min(kXS, nrhs - cb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSB * nc; e += blockDim.x) {
+      const int k = e / nc, c = e - k * nc;
+      Xs[k * kXP + c] = k < kc ? Y[(long long)(c0 + k) * nrhs + cb + c] : T(0);
+    }
+    __syncthreads();
+    if (nr > 0) chunk_gemv(Ms, Xs, nr, kc, nc, Y, nrhs, r0, cb, true);
+  }
+  if (blk != next) return;
+  // the last chunk of the next block to finish makes its unknowns final
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    // every chunk CTA of the block counts, also those past the matrix edge (no rows)
+    s_last = atomicAdd(&counters[next], 1u) == (unsigned)(per - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nr0 = next * kSB;
+  apply_inverse(Dinv + ((size_t)(lower ? 0 : 1) * nb + next) * kSB * kSB, Y, nrhs, nr0, min(kSB, n - nr0), Ms, Xs);
+}
+
+template <typename T>
+static cudaError_t trsv_t(const T* LU, long long lda, const T* Dinv, int n, T* Y, int nrhs, bool lower,
+                          unsigned* counters, cudaStream_t s) {
+  if (n == 0 || nrhs == 0) return cudaSuccess;
+  const int nb = (n + kSB - 1) / kSB, per = kSB / kRC;
+  cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * nb, s);
+  if (e != cudaSuccess) return e;
+  trsv_first_kernel<T><<<1, kSolveThreads, 0, s>>>(Dinv, n, Y, nrhs, lower);
+  for (int q = 0; q < nb - 1; ++q) {
+    const int j = lower ? q : nb - 1 - q;
+    trsv_step_kernel<T><<<(nb - 1 - q) * per, kSolveThreads, 0, s>>>(LU, lda, Dinv, n, Y, nrhs, j, lower,
+                                                                       counters);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_trsv_lower_unit(const double* LU, long long lda, int n, double* Y, int nrhs,
-                                   cudaStream_t s) {
-  return trsv(LU, lda, n, Y, nrhs, true, s);
+cudaError_t launch_invert_diag(const double* LU, long long lda, int n, void* dinv, int fp32, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const dim3 grid((n + kSB - 1) / kSB, 2);
+  const size_t smem = sizeof(double) * (2 * kSB * kB1 + kSB);
+  cudaError_t e = fp32 ? smem_optin(invert_diag_kernel<float>) : smem_optin(invert_diag_kernel<double>);
+  if (e != cudaSuccess) return e;
+  if (fp32) invert_diag_kernel<float><<<grid, kSB, smem, s>>>(LU, lda, n, static_cast<float*>(dinv));
+  else invert_diag_kernel<double><<<grid, kSB, smem, s>>>(LU, lda, n, static_cast<double*>(dinv));
+  return cudaGetLastError();
 }
 
-cudaError_t launch_trsv_upper(const double* LU, long long lda, int n, double* Y, int nrhs,
-                              cudaStream_t s) {
-  return trsv(LU, lda, n, Y, nrhs, false, s);
+cudaError_t launch_trsv(const void* LU, long long lda, const void* dinv, int n, void* Y, int nrhs, int lower,
+                        int fp32, unsigned* counters, cudaStream_t s) {
+  if (fp32)
+    return trsv_t(static_cast<const float*>(LU), lda, static_cast<const float*>(dinv), n, static_cast<float*>(Y),
+                  nrhs, lower != 0, counters, s);
+  return trsv_t(static_cast<const double*>(LU), lda, static_cast<const double*>(dinv), n, static_cast<double*>(Y),
+                nrhs, lower != 0, counters, s);
+}
+
+// FP32 copy of the factors (for the correction solves of the refinement).
+__global__ void convert_lu32_kernel(const double* __restrict__ LU, long long lda, int n, float* __restrict__ out) {
+  const long long total = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), k = (int)(e - (long long)i * n);
+    out[e] = static_cast<float>(LU[(long long)i * lda + k]);
+  }
+}
+
+cudaError_t launch_convert_lu32(const double* LU, long long lda, int n, float* out, cudaStream_t s) {
+  const long long total = (long long)n * n;
+  if (total == 0) return cudaSuccess;
+  convert_lu32_kernel<<<(int)std::min<long long>((total + 255) / 256, 152 * 16), 256, 0, s>>>(LU, lda, n, out);
+  return cudaGetLastError();
+}
+
+// Y32 = P B rounded to FP32 (the right-hand side of a correction solve).
+__global__ void gather_rows32_kernel(const double* __restrict__ B, long long ldb, const int* __restrict__ perm,
+                                     int n, int nrhs, float* __restrict__ Y) {
+  const long long total = (long long)n * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / nrhs), c = (int)(e - (long long)i * nrhs);
+    Y[e] = static_cast<float>(B[(long long)perm[i] * ldb + c]);
+  }
+}
+
+cudaError_t launch_gather_rows32(const double* B, long long ldb, const int* perm, int n, int nrhs, float* Y,
+                                 cudaStream_t s) {
+  const long long total = (long long)n * nrhs;
+  if (total == 0) return cudaSuccess;
+  gather_rows32_kernel<<<(int)std::min<long long>((total + 255) / 256, 152 * 16), 256, 0, s>>>(B, ldb, perm, n,
+                                                                                               nrhs, Y);
+  return cudaGetLastError();
+}
+
+// X += alpha D for an FP32 correction D.
+__global__ void axpy_rows32_kernel(double* X, long long ldx, const float* D, double alpha, int n, int nrhs) {
+  const long long total = (long long)n * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / nrhs), c = (int)(e - (long long)i * nrhs);
+    X[(long long)i * ldx + c] = fma(alpha, static_cast<double>(D[e]), X[(long long)i * ldx + c]);
+  }
+}
+
+cudaError_t launch_axpy_rows32(double* X, long long ldx, const float* D, double alpha, int n, int nrhs,
+                               cudaStream_t s) {
+  const long long total = (long long)n * nrhs;
+  if (total == 0) return cudaSuccess;
+  axpy_rows32_kernel<<<(int)std::min<long long>((total + 255) / 256, 152 * 16), 256, 0, s>>>(X, ldx, D, alpha, n,
+                                                                                             nrhs);
+  return cudaGetLastError();
 }
 
 // R = B - A X (FP64), one CTA per row (coalesced row reads).  The 1-norm numerators of
