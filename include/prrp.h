@@ -303,7 +303,7 @@ prrp_status prrp_ctx_kernel_stats(prrp_ctx* ctx, double* ms, long long* launches
  * and calls no cudaMalloc, cudaFree or other allocating routine.
  *
  * Scratch: the kernel's device state word and cross-CTA exchange records live in one
- * library-wide static device array of 333,056 bytes, which every GPU that loads libprrp.so
+ * library-wide static device array of 338,176 bytes, which every GPU that loads libprrp.so
  * holds until the process exits.  The first call on a device (the current device at the
  * time of the call) looks up that array's device address; make that first call before any
  * stream capture.  All calls share the array and it keeps the last call's contents (the

@@ -232,7 +232,7 @@ prrp_status ensure_panel_ws(prrp_ctx* ctx, int n, int w, int max_swaps) {
     size_t c1 = 0, c2 = 0, c3 = 0;
     if (ctx->xval) { cudaFree(ctx->xval); cudaFree(ctx->xkey); cudaFree(ctx->xvec); }
     ctx->xval = nullptr; ctx->xkey = nullptr; ctx->xvec = nullptr;
-    if ((s = grow(ctx, &ctx->xval, &c1, 2 * (size_t)G)) != PRRP_OK) return s;
+    if ((s = grow(ctx, &ctx->xval, &c1, 2 * (size_t)G * kXVal)) != PRRP_OK) return s;
     if ((s = grow(ctx, &ctx->xkey, &c2, 2 * (size_t)G)) != PRRP_OK) return s;
     if ((s = grow(ctx, &ctx->xvec, &c3, 2 * (size_t)G * kMaxW)) != PRRP_OK) return s;
     ctx->xcap = G;

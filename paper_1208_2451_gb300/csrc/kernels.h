@@ -8,6 +8,8 @@
 
 namespace prrp {
 
+constexpr int kXVal = 3;   // doubles per panel exchange record: value, reflector alpha, beta
+
 struct PanelParams {
   const double* P;        // m x w panel, row-major
   long long ldp;
@@ -20,7 +22,7 @@ struct PanelParams {
   int* order;             // m ints (final position -> panel row) or nullptr
   int* pairs;             // (dst, src) row moves, 2 ints each, or nullptr
   DevState* st;
-  double* xval;           // exchange records: [2][G]
+  double* xval;           // exchange records: [2][G][kXVal] (value, alpha, beta)
   int2* xkey;             // [2][G]
   double* xvec;           // [2][G][kMaxW]
   int rows_per_cta;

@@ -26,10 +26,10 @@ namespace {
 
 constexpr int kStaticMaxCtas = 160;   // panel CTAs the static exchange records can hold
 constexpr size_t kStateBytes = 256;   // DevState, padded
-constexpr size_t kValBytes = 2 * kStaticMaxCtas * sizeof(double);
+constexpr size_t kValBytes = 2 * kStaticMaxCtas * kXVal * sizeof(double);
 constexpr size_t kKeyBytes = 2 * kStaticMaxCtas * sizeof(int2);
 constexpr size_t kVecBytes = 2 * (size_t)kStaticMaxCtas * kMaxW * sizeof(double);
-constexpr size_t kScratchBytes = kStateBytes + kValBytes + kKeyBytes + kVecBytes;   // 333,056 B
+constexpr size_t kScratchBytes = kStateBytes + kValBytes + kKeyBytes + kVecBytes;   // 338,176 B
 static_assert(sizeof(DevState) <= kStateBytes, "state word does not fit its slot");
 static_assert(kScratchBytes % 256 == 0, "scratch slots keep 256-byte alignment");
 

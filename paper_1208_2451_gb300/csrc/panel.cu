@@ -67,47 +67,59 @@ __device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
   return a.k2 < b.k2;
 }
 
-__device__ __forceinline__ Cand shfl_cand(const Cand& c, int lane_mask, unsigned mask) {
-  Cand o;
-  o.v = __shfl_xor_sync(mask, c.v, lane_mask);   // 64-bit shuffle
-  o.k1 = __shfl_xor_sync(mask, c.k1, lane_mask);
-  o.k2 = __shfl_xor_sync(mask, c.k2, lane_mask);
-  o.aux = __shfl_xor_sync(mask, c.aux, lane_mask);
-  return o;
+// The best candidate of a full warp (largest value, then smallest k1, then smallest k2),
+// returned in every lane: warp-wide max/min reductions on the value's two halves and on
+// the tie-breaks, then the payload from the winning lane.
+__device__ __forceinline__ Cand warp_argmax(const Cand& c) {
+  const unsigned full = 0xffffffffu;
+  const unsigned hi = static_cast<unsigned>(c.v >> 32), lo = static_cast<unsigned>(c.v);
+  const unsigned mhi = __reduce_max_sync(full, hi);
+  const unsigned mlo = __reduce_max_sync(full, hi == mhi ? lo : 0u);
+  const bool eq = hi == mhi && lo == mlo;
+  const int mk1 = __reduce_min_sync(full, eq ? c.k1 : 0x7fffffff);
+  const bool eq1 = eq && c.k1 == mk1;
+  const int mk2 = __reduce_min_sync(full, eq1 ? c.k2 : 0x7fffffff);
+  const unsigned who = __ballot_sync(full, eq1 && c.k2 == mk2);
+  Cand r;
+  r.v = (static_cast<unsigned long long>(mhi) << 32) | mlo;
+  r.k1 = mk1;
+  r.k2 = mk2;
+  r.aux = __shfl_sync(full, c.aux, __ffs(who) - 1);
+  return r;
 }
 
-__device__ __forceinline__ Cand warp_best(Cand c) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    Cand o = shfl_cand(c, off, 0xffffffffu);
-    if (better(o, c)) c = o;
-  }
-  return c;
-}
-
-// Sum over the 4 lanes of a row team.  Every lane receives the same bits: the xor
+// Sum over the TEAM lanes of a row team.  Every lane receives the same bits: the xor
 // butterfly adds the same pairs in each lane, only commuted.
-__device__ __forceinline__ double team_sum(double s) {
-  const unsigned mask = 0xfu << ((threadIdx.x & 31) & ~3);
-  s += __shfl_xor_sync(mask, s, 1);
-  s += __shfl_xor_sync(mask, s, 2);
+template <int TEAM>
+__device__ __forceinline__ double team_sum(double s, unsigned tmask) {
+#pragma unroll
+  for (int off = 1; off < TEAM; off <<= 1) s += __shfl_xor_sync(tmask, s, off);
   return s;
+}
+
+// (a > b) for non-negative b: signed compare of the IEEE bit patterns (a negative a, or a
+// -0, compares below every positive b; nan above).
+__device__ __forceinline__ bool gt_nonneg(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b);
 }
 
 }  // namespace
 
 // Warp-centric layout: warp k of a CTA owns a fixed slice of the CTA's rows for the whole
-// kernel, and inside a warp 8 teams of 4 lanes work on one row each.  All per-row state
-// (values, remaining squared norm, position) is touched only by its own warp, so a QRCP
-// step needs just two block-wide syncs (gathering the warps' proposals, releasing the
-// warps after the grid barrier); every warp reduces the G proposals of the tournament on
-// its own and keeps its own copy of the winning row.
+// kernel, and inside a warp teams of TEAM = W / 8 lanes work on one row each (8 entries per
+// lane at full width).  All per-row state (values, remaining squared norm, position) is
+// touched only by its own warp, so a QRCP step needs just two block-wide syncs (gathering
+// the warps' proposals, releasing the warps after the grid barrier); every warp reduces
+// the G proposals of the tournament on its own and keeps its own copy of the winning row.
+// The CTA that proposes a row also computes the reflector of that row (alpha, beta) before
+// publishing it, so the square root and division happen once per CTA and step.
 template <int W>
 __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int SP = W + 4;   // row stride: 4 mod 16 doubles keeps team accesses conflict-light
+  constexpr int TEAM = W >= 128 ? 16 : (W >= 64 ? 8 : (W >= 32 ? 4 : 2));
+  constexpr int TPW = 32 / TEAM;     // rows per warp pass
+  constexpr int SP = W + TEAM;       // row stride: a warp pass touches each bank pair evenly
   constexpr int kWarps = kPanelThreads / 32;
-  constexpr int kTeamsPerWarp = 32 / kTeam;
   __shared__ Cand s_wc[kWarps];
   __shared__ int s_ok;
 
@@ -116,8 +128,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
 
   const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int tl = lane & (kTeam - 1), tw = lane / kTeam;          // lane in team, team in warp
-  const unsigned tmask = 0xfu << (lane & ~3);
+  const int tl = lane & (TEAM - 1), tw = lane / TEAM;            // lane in team, team in warp
+  const unsigned tmask = (TEAM == 32 ? 0xffffffffu : ((1u << TEAM) - 1u)) << (lane & ~(TEAM - 1));
   const int w = p.w, m = p.m;
   const int rpc = p.rows_per_cta;
   const int r0 = cta * rpc;
@@ -129,8 +141,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   double* Rs = Ps + (size_t)rpc * SP;                     // W x W, R11 (row-major)
   double* vsw = Rs + W * W;                               // kWarps x W: each warp's winner row
   double* nrm = vsw + kWarps * W;                         // rpc remaining squared norms
-  double* nref = nrm + rpc;                               // rpc norms at their last exact value
-  int* pos = reinterpret_cast<int*>(nref + rpc);          // rpc current positions
+  double* thr = nrm + rpc;                                // rpc recompute thresholds
+  int* pos = reinterpret_cast<int*>(thr + rpc);           // rpc current positions
   double* vs = vsw + warp * W;
 
   unsigned nbar = 0;
@@ -140,25 +152,37 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     Ps[r * SP + c] = p.P[(long long)(r0 + r) * p.ldp + c];
   }
   __syncthreads();
-  for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
+  for (int r = wr0 + tw; r < wr1; r += TPW) {
     double s = 0.0;
-    for (int i = tl; i < w; i += kTeam) { const double x = Ps[r * SP + i]; s = fma(x, x, s); }
-    s = team_sum(s);
-    if (tl == 0) { nrm[r] = s; nref[r] = s; pos[r] = r0 + r; }
+    for (int i = tl; i < w; i += TEAM) { const double x = Ps[r * SP + i]; s = fma(x, x, s); }
+    s = team_sum<TEAM>(s, tmask);
+    if (tl == 0) { nrm[r] = s; thr[r] = 1e-4 * s; pos[r] = r0 + r; }
   }
   __syncwarp();
 
-  // Gather the warps' proposals, publish this CTA's best with its row values, grid barrier.
-  // Returns false when the barrier gave up (an error is recorded) and the CTA must return.
-  auto publish_and_sync = [&](Cand c, int par, unsigned site) -> bool {
-    c = warp_best(c);
+  // Gather the warps' proposals, publish this CTA's best with its row values (and, for a
+  // QRCP step t >= 0, the reflector that row would give), grid barrier.  Returns false when
+  // the barrier gave up (an error is recorded) and the CTA must return.
+  auto publish_and_sync = [&](Cand c, int par, unsigned site, int t) -> bool {
+    c = warp_argmax(c);
     if (lane == 0) s_wc[warp] = c;
     __syncthreads();
     if (warp == 0) {
       Cand d = lane < kWarps ? s_wc[lane] : Cand{0ull, 0x7fffffff, 0x7fffffff, -1};
-      d = warp_best(d);
+      d = warp_argmax(d);
       const size_t slot = (size_t)par * G + cta;
-      if (lane == 0) { p.xval[slot] = vval(d.v); p.xkey[slot] = make_int2(d.k1, d.k2); }
+      if (lane == 0) {
+        p.xval[slot * kXVal] = vval(d.v);
+        if (t >= 0 && d.aux >= 0 && d.v != 0ull) {
+          // H = I - beta v v^T with H x = alpha e_1 for x = B(t:w, row): ||x|| = sqrt of the
+          // remaining squared norm, v = x - alpha e_1, v^T v = 2 ||x|| (||x|| + |x_t|)
+          const double x0 = Ps[d.aux * SP + t];
+          const double normx = sqrt(vval(d.v));
+          p.xval[slot * kXVal + 1] = (x0 >= 0.0) ? -normx : normx;
+          p.xval[slot * kXVal + 2] = 1.0 / (normx * (normx + abs_int(x0)));
+        }
+        p.xkey[slot] = make_int2(d.k1, d.k2);
+      }
       if (d.aux >= 0)
         for (int i = lane; i < w; i += 32) p.xvec[slot * kMaxW + i] = Ps[d.aux * SP + i];
       __syncwarp();
@@ -193,10 +217,10 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     for (int q = lane; q < G; q += 32) {
       const size_t sq = (size_t)par * G + q;
       const int2 k = __ldcg(&p.xkey[sq]);
-      Cand d{vbits(__ldcg(&p.xval[sq])), k.x, k.y, q};
+      Cand d{vbits(__ldcg(&p.xval[sq * kXVal])), k.x, k.y, q};
       if (better(d, g)) g = d;
     }
-    return warp_best(g);
+    return warp_argmax(g);
   };
 
   // ---------------- QR with column pivoting ----------------
@@ -206,11 +230,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     for (int r = wr0 + lane; r < wr1; r += 32) {
       const int pr = pos[r];
       if (pr >= t) {
-        Cand d{vbits(fmax(nrm[r], 0.0)), pr, 0, r};
+        long long b = __double_as_longlong(nrm[r]);
+        Cand d{static_cast<unsigned long long>(b < 0 ? 0 : b), pr, 0, r};
         if (better(d, c)) c = d;
       }
     }
-    if (!publish_and_sync(c, par, 1)) return;
+    if (!publish_and_sync(c, par, 1, t)) return;
 
     const Cand g = global_best(par);
     if (g.v == 0ull) {            // the largest remaining norm is zero: rank < w
@@ -218,15 +243,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
       return;
     }
     const int pw = g.k1;
-    for (int i = lane; i < w; i += 32) vs[i] = __ldcg(&p.xvec[((size_t)par * G + g.aux) * kMaxW + i]);
+    const size_t gs = (size_t)par * G + g.aux;
+    for (int i = lane; i < w; i += 32) vs[i] = __ldcg(&p.xvec[gs * kMaxW + i]);
+    const double alpha = __ldcg(&p.xval[gs * kXVal + 1]);
+    const double beta = __ldcg(&p.xval[gs * kXVal + 2]);
     __syncwarp();
-    // Reflector H = I - beta v v^T with H x = alpha e_1 for x = B(t:w, p):
-    // ||x|| = sqrt of the winner's remaining squared norm, v = x - alpha e_1,
-    // v^T v = 2 ||x|| (||x|| + |x_t|), so beta = 1 / (||x|| (||x|| + |x_t|)).
     const double x0 = vs[t];
-    const double normx = sqrt(vval(g.v));
-    const double alpha = (x0 >= 0.0) ? -normx : normx;
-    const double beta = 1.0 / (normx * (normx + fabs(x0)));
     if (warp == 0) {
       for (int i = lane; i < t; i += 32) Rs[i * W + t] = vs[i];
       if (lane == 0) Rs[t * W + t] = alpha;
@@ -234,7 +256,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     __syncwarp();
     if (lane == 0) vs[t] = x0 - alpha;
     __syncwarp();
-    for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
+    for (int r = wr0 + tw; r < wr1; r += TPW) {
       const int pr = pos[r];
       if (pr < t) continue;                           // selected at an earlier step
       if (pr == pw) {                                  // the pivot row: now R(:, t)
@@ -244,29 +266,27 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
       double* x = Ps + r * SP;
       double sd0 = 0.0, sd1 = 0.0;      // two chains halve the dependent-FMA latency
       int i = t + tl;
-      for (; i + kTeam < w; i += 2 * kTeam) {
+      for (; i + TEAM < w; i += 2 * TEAM) {
         sd0 = fma(vs[i], x[i], sd0);
-        sd1 = fma(vs[i + kTeam], x[i + kTeam], sd1);
+        sd1 = fma(vs[i + TEAM], x[i + TEAM], sd1);
       }
       if (i < w) sd0 = fma(vs[i], x[i], sd0);
-      const double sdot = team_sum(sd0 + sd1);
-      const double f = beta * sdot;
+      const double f = beta * team_sum<TEAM>(sd0 + sd1, tmask);
       double xt = 0.0;
-      for (int i = t + tl; i < w; i += kTeam) {
+      for (int i = t + tl; i < w; i += TEAM) {
         const double y = fma(-f, vs[i], x[i]);
         x[i] = y;
         if (i == t) xt = y;
       }
       // remaining squared norm for step t+1: downdate, recomputed exactly when it has
       // fallen below 1e-4 of its last exact value (bounds the cancellation error)
-      xt = __shfl_sync(tmask, xt, lane & ~3);      // x[t] is handled by team lane 0
+      xt = __shfl_sync(tmask, xt, lane & ~(TEAM - 1));      // x[t] is handled by team lane 0
       double n2 = fma(-xt, xt, nrm[r]);
-      const double ref = nref[r];
-      if (!(n2 > 1e-4 * ref)) {
+      if (!gt_nonneg(n2, thr[r])) {
         double e2 = 0.0;
-        for (int i = t + 1 + tl; i < w; i += kTeam) e2 = fma(x[i], x[i], e2);
-        n2 = team_sum(e2);
-        if (tl == 0) nref[r] = n2;
+        for (int i = t + 1 + tl; i < w; i += TEAM) e2 = fma(x[i], x[i], e2);
+        n2 = team_sum<TEAM>(e2, tmask);
+        if (tl == 0) thr[r] = 1e-4 * n2;
       }
       __syncwarp(tmask);
       if (tl == 0) { nrm[r] = n2; pos[r] = (pr == t) ? pw : pr; }
@@ -280,16 +300,16 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   double* rdiag = vsw;                                    // the winner rows are no longer needed
   for (int i = tid; i < w; i += blockDim.x) rdiag[i] = 1.0 / Rs[i * W + i];
   __syncthreads();
-  for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
+  for (int r = wr0 + tw; r < wr1; r += TPW) {
     if (pos[r] < w) continue;
     double* b = Ps + r * SP;
     for (int i = w - 1; i >= 0; --i) {
-      const int owner = i & (kTeam - 1);
+      const int owner = i & (TEAM - 1);
       double mi = 0.0;
       if (tl == owner) mi = b[i] * rdiag[i];
-      mi = __shfl_sync(tmask, mi, (lane & ~3) | owner);
+      mi = __shfl_sync(tmask, mi, (lane & ~(TEAM - 1)) | owner);
       if (tl == owner) b[i] = mi;
-      for (int k = tl; k < i; k += kTeam) b[k] = fma(-Rs[k * W + i], mi, b[k]);
+      for (int k = tl; k < i; k += TEAM) b[k] = fma(-Rs[k * W + i], mi, b[k]);
     }
   }
   __syncthreads();              // rdiag shares memory with the warps' winner rows
@@ -299,21 +319,17 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   for (int it = 0;; ++it) {
     const int par = (w + it) & 1;
     Cand c{0ull, 0x7fffffff, 0x7fffffff, -1};
-    for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
+    for (int r = wr0 + tw; r < wr1; r += TPW) {
       const int pr = pos[r];
       if (pr < w) continue;
       Cand d{0ull, pr - w, 0x7fffffff, r};
-      for (int i = tl; i < w; i += kTeam) {
+      for (int i = tl; i < w; i += TEAM) {
         const unsigned long long a = abs_bits(Ps[r * SP + i]);
         if (a > d.v || d.k2 == 0x7fffffff) { d.v = a; d.k2 = i; }
       }
-      Cand o = shfl_cand(d, 1, tmask);
-      if (better(o, d)) d = o;
-      o = shfl_cand(d, 2, tmask);
-      if (better(o, d)) d = o;
       if (better(d, c)) c = d;
     }
-    if (!publish_and_sync(c, par, 2)) return;
+    if (!publish_and_sync(c, par, 2, -1)) return;
 
     const Cand g = global_best(par);
     if (g.aux < 0 || !(vval(g.v) > p.tau)) break;   // also ends when there is no remaining row
@@ -325,21 +341,21 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     for (int i = lane; i < w; i += 32) vs[i] = __ldcg(&p.xvec[((size_t)par * G + g.aux) * kMaxW + i]);
     __syncwarp();
     const double mu = vs[is];
-    for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
+    for (int r = wr0 + tw; r < wr1; r += TPW) {
       const int pr = pos[r];
       double* x = Ps + r * SP;
       if (pr == w + js) {                          // enters the selection at slot is
         if (tl == 0) pos[r] = is;
       } else if (pr == is) {                       // leaves the selection to slot js
-        for (int k = tl; k < w; k += kTeam) x[k] = (k == is) ? 1.0 / mu : -vs[k] / mu;
+        for (int k = tl; k < w; k += TEAM) x[k] = (k == is) ? 1.0 / mu : -vs[k] / mu;
         __syncwarp(tmask);
         if (tl == 0) pos[r] = w + js;
       } else if (pr >= w) {
-        const int owner = is & (kTeam - 1);
+        const int owner = is & (TEAM - 1);
         double f = 0.0;
         if (tl == owner) f = x[is] / mu;
-        f = __shfl_sync(tmask, f, (lane & ~3) | owner);
-        for (int k = tl; k < w; k += kTeam) x[k] = (k == is) ? f : fma(-f, vs[k], x[k]);
+        f = __shfl_sync(tmask, f, (lane & ~(TEAM - 1)) | owner);
+        for (int k = tl; k < w; k += TEAM) x[k] = (k == is) ? f : fma(-f, vs[k], x[k]);
       }
     }
     ++swaps;
@@ -348,11 +364,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
 
   // ---------------- outputs ----------------
   unsigned long long lmax = 0ull;
-  for (int r = wr0 + tw; r < wr1; r += kTeamsPerWarp) {
+  for (int r = wr0 + tw; r < wr1; r += TPW) {
     const int pr = pos[r];
     if (pr < w) continue;
     double* dst = p.L21 + (long long)(pr - w) * p.ldl;
-    for (int k = tl; k < w; k += kTeam) {
+    for (int k = tl; k < w; k += TEAM) {
       const double v = Ps[r * SP + k];
       dst[k] = v;
       lmax = max_bits(lmax, abs_bits(v));
@@ -378,7 +394,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
 
 template <int W>
 static size_t panel_smem_bytes(int rpc) {
-  return (size_t)rpc * (W + 4) * sizeof(double) + (size_t)W * W * sizeof(double) +
+  constexpr int TEAM = W >= 128 ? 16 : (W >= 64 ? 8 : (W >= 32 ? 4 : 2));
+  return (size_t)rpc * (W + TEAM) * sizeof(double) + (size_t)W * W * sizeof(double) +
          (size_t)(kPanelThreads / 32) * W * sizeof(double) +
          (size_t)rpc * (2 * sizeof(double) + sizeof(int)) + 16;
 }
