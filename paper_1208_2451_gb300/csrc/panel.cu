@@ -103,6 +103,38 @@ __device__ __forceinline__ bool gt_nonneg(double a, double b) {
   return __double_as_longlong(a) > __double_as_longlong(b);
 }
 
+// ---- distributed shared memory of a thread-block cluster (cluster mode) ----
+__device__ __forceinline__ uint32_t cl_map(const void* p, unsigned rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ double cl_ld_f64(uint32_t a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ int2 cl_ld_int2(uint32_t a) {
+  int2 v;
+  asm volatile("ld.shared::cluster.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void cl_arrive(uint32_t a) {
+  asm volatile("red.release.cluster.shared::cluster.add.u32 [%0], 1;" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ unsigned cl_ld_acquire(uint32_t a) {
+  unsigned v;
+  asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void cl_fence() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+// every thread of every CTA of the cluster (hardware barrier)
+__device__ __forceinline__ void cl_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 }  // namespace
 
 // Warp-centric layout: warp k of a CTA owns a fixed slice of the CTA's rows for the whole
@@ -113,7 +145,16 @@ __device__ __forceinline__ bool gt_nonneg(double a, double b) {
 // the G proposals of the tournament on its own and keeps its own copy of the winning row.
 // The CTA that proposes a row also computes the reflector of that row (alpha, beta) before
 // publishing it, so the square root and division happen once per CTA and step.
-template <int W>
+//
+// CL = false: one cooperative grid; proposals are exchanged through global memory and a
+// grid barrier.  CL = true: the grid is one thread-block cluster; every CTA publishes its
+// proposal in its own shared memory, a counter in CTA 0 (remote atomics) is the barrier,
+// and the proposals and the winning row are read from the other CTAs' shared memory.  The
+// cluster's CTAs are co-scheduled by the hardware, so cluster-mode panels from different
+// streams may run at the same time.  In cluster mode no CTA leaves before the others are
+// done reading its shared memory (a hardware cluster barrier ends the kernel), and every
+// decision that ends a loop is taken identically by all CTAs from the same exchanged data.
+template <int W, bool CL>
 __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int TEAM = W >= 128 ? 16 : (W >= 64 ? 8 : (W >= 32 ? 4 : 2));
@@ -122,9 +163,22 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   constexpr int kWarps = kPanelThreads / 32;
   __shared__ Cand s_wc[kWarps];
   __shared__ int s_ok;
+  __shared__ double s_xval[CL ? 2 * kXVal : 1];    // cluster mode: this CTA's records
+  __shared__ int2 s_xkey[CL ? 2 : 1];
+  __shared__ double s_xrow[CL ? 2 * W : 1];
+  __shared__ unsigned s_ctr;                        // cluster mode: the barrier (CTA 0's)
+  __shared__ Cand s_gbest;                          // cluster mode: this step's winner,
+  __shared__ double s_win[CL ? W : 1];              //   its row and reflector, fetched once
+  __shared__ double s_gab[2];                       //   per CTA by warp 0
 
   DevState* st = p.st;
-  if (dev_status(st) != 0) return;
+  if constexpr (!CL) {
+    if (dev_status(st) != 0) return;
+  } else {
+    if (threadIdx.x == 0) s_ctr = 0;
+    cl_sync_all();                                  // counter zeroed, every CTA running
+  }
+  {
 
   const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -171,39 +225,77 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
       Cand d = lane < kWarps ? s_wc[lane] : Cand{0ull, 0x7fffffff, 0x7fffffff, -1};
       d = warp_argmax(d);
       const size_t slot = (size_t)par * G + cta;
+      double* xv = CL ? s_xval + par * kXVal : p.xval + slot * kXVal;
+      double* xr = CL ? s_xrow + par * W : p.xvec + slot * kMaxW;
       if (lane == 0) {
-        p.xval[slot * kXVal] = vval(d.v);
+        xv[0] = vval(d.v);
         if (t >= 0 && d.aux >= 0 && d.v != 0ull) {
           // H = I - beta v v^T with H x = alpha e_1 for x = B(t:w, row): ||x|| = sqrt of the
           // remaining squared norm, v = x - alpha e_1, v^T v = 2 ||x|| (||x|| + |x_t|)
           const double x0 = Ps[d.aux * SP + t];
           const double normx = sqrt(vval(d.v));
-          p.xval[slot * kXVal + 1] = (x0 >= 0.0) ? -normx : normx;
-          p.xval[slot * kXVal + 2] = 1.0 / (normx * (normx + abs_int(x0)));
+          xv[1] = (x0 >= 0.0) ? -normx : normx;
+          xv[2] = 1.0 / (normx * (normx + abs_int(x0)));
         }
-        p.xkey[slot] = make_int2(d.k1, d.k2);
+        if (CL) s_xkey[par] = make_int2(d.k1, d.k2);
+        else p.xkey[slot] = make_int2(d.k1, d.k2);
       }
       if (d.aux >= 0)
-        for (int i = lane; i < w; i += 32) p.xvec[slot * kMaxW + i] = Ps[d.aux * SP + i];
+        for (int i = lane; i < w; i += 32) xr[i] = Ps[d.aux * SP + i];
       __syncwarp();
       if (lane == 0) {
-        __threadfence();
-        atomicAdd(&st->barrier, 1u);
         const unsigned target = (nbar + 1) * G;
         const unsigned limit = st->spin_limit ? st->spin_limit : kSpinLimit;
         unsigned spins = 0;
         int ok = 1;
-        while (ld_acquire_u32(&st->barrier) < target) {
-          if (dev_status(st) != 0) { ok = 0; break; }
-          if (++spins > limit) {
-            if (atomicCAS(&st->status, 0, PRRP_ERR_TIMEOUT) == 0) st->timeout_site = site;
-            ok = 0;
-            break;
+        if constexpr (CL) {
+          const uint32_t ctr = cl_map(&s_ctr, 0);
+          cl_fence();
+          cl_arrive(ctr);
+          while (cl_ld_acquire(ctr) < target) {
+            if (++spins > limit) {
+              if (atomicCAS(&st->status, 0, PRRP_ERR_TIMEOUT) == 0) st->timeout_site = site;
+              ok = 0;
+              break;
+            }
+            __nanosleep(20);
           }
-          __nanosleep(32);
+        } else {
+          __threadfence();
+          atomicAdd(&st->barrier, 1u);
+          while (ld_acquire_u32(&st->barrier) < target) {
+            if (dev_status(st) != 0) { ok = 0; break; }
+            if (++spins > limit) {
+              if (atomicCAS(&st->status, 0, PRRP_ERR_TIMEOUT) == 0) st->timeout_site = site;
+              ok = 0;
+              break;
+            }
+            __nanosleep(32);
+          }
+          __threadfence();
         }
-        __threadfence();
         s_ok = ok;
+      }
+      if constexpr (CL) {
+        // warp 0 reads the G records once for the whole CTA: each lane acquires the
+        // counter itself (it already holds the target value), then the winner's record
+        __syncwarp();
+        if (s_ok) {
+          const uint32_t ctr = cl_map(&s_ctr, 0);
+          (void)cl_ld_acquire(ctr);
+          Cand g{0ull, 0x7fffffff, 0x7fffffff, -1};
+          if (lane < G) {
+            const int2 k = cl_ld_int2(cl_map(&s_xkey[par], lane));
+            g = Cand{vbits(cl_ld_f64(cl_map(&s_xval[par * kXVal], lane))), k.x, k.y, lane};
+          }
+          g = warp_argmax(g);
+          if (g.aux >= 0) {
+            const uint32_t row = cl_map(&s_xrow[par * W], g.aux);
+            for (int i = lane; i < w; i += 32) s_win[i] = cl_ld_f64(row + 8u * i);
+            if (lane < 2) s_gab[lane] = cl_ld_f64(cl_map(&s_xval[par * kXVal], g.aux) + 8u * (lane + 1));
+          }
+          if (lane == 0) s_gbest = g;
+        }
       }
     }
     __syncthreads();
@@ -213,14 +305,35 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
 
   // Every warp: the tournament winner among the G proposals of parity `par`.
   auto global_best = [&](int par) -> Cand {
-    Cand g{0ull, 0x7fffffff, 0x7fffffff, -1};
-    for (int q = lane; q < G; q += 32) {
-      const size_t sq = (size_t)par * G + q;
-      const int2 k = __ldcg(&p.xkey[sq]);
-      Cand d{vbits(__ldcg(&p.xval[sq * kXVal])), k.x, k.y, q};
-      if (better(d, g)) g = d;
+    if constexpr (CL) {
+      return s_gbest;
+    } else {
+      Cand g{0ull, 0x7fffffff, 0x7fffffff, -1};
+      for (int q = lane; q < G; q += 32) {
+        const size_t sq = (size_t)par * G + q;
+        const int2 k = __ldcg(&p.xkey[sq]);
+        Cand d{vbits(__ldcg(&p.xval[sq * kXVal])), k.x, k.y, q};
+        if (better(d, g)) g = d;
+      }
+      return warp_argmax(g);
     }
-    return warp_argmax(g);
+  };
+  // the winning record of parity `par`: row into vs, and (QRCP) alpha, beta
+  auto fetch_winner = [&](int par, int q, double* alpha, double* beta) {
+    if constexpr (CL) {
+      for (int i = lane; i < w; i += 32) vs[i] = s_win[i];
+      if (alpha) {
+        *alpha = s_gab[0];
+        *beta = s_gab[1];
+      }
+    } else {
+      const size_t gs = (size_t)par * G + q;
+      for (int i = lane; i < w; i += 32) vs[i] = __ldcg(&p.xvec[gs * kMaxW + i]);
+      if (alpha) {
+        *alpha = __ldcg(&p.xval[gs * kXVal + 1]);
+        *beta = __ldcg(&p.xval[gs * kXVal + 2]);
+      }
+    }
   };
 
   // ---------------- QR with column pivoting ----------------
@@ -235,18 +348,16 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
         if (better(d, c)) c = d;
       }
     }
-    if (!publish_and_sync(c, par, 1, t)) return;
+    if (!publish_and_sync(c, par, 1, t)) goto done;
 
     const Cand g = global_best(par);
     if (g.v == 0ull) {            // the largest remaining norm is zero: rank < w
       if (cta == 0 && tid == 0) set_error(st, PRRP_ERR_SINGULAR, p.col_offset + t + 1);
-      return;
+      goto done;
     }
     const int pw = g.k1;
-    const size_t gs = (size_t)par * G + g.aux;
-    for (int i = lane; i < w; i += 32) vs[i] = __ldcg(&p.xvec[gs * kMaxW + i]);
-    const double alpha = __ldcg(&p.xval[gs * kXVal + 1]);
-    const double beta = __ldcg(&p.xval[gs * kXVal + 2]);
+    double alpha, beta;
+    fetch_winner(par, g.aux, &alpha, &beta);
     __syncwarp();
     const double x0 = vs[t];
     if (warp == 0) {
@@ -329,16 +440,16 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
       }
       if (better(d, c)) c = d;
     }
-    if (!publish_and_sync(c, par, 2, -1)) return;
+    if (!publish_and_sync(c, par, 2, -1)) goto done;
 
     const Cand g = global_best(par);
     if (g.aux < 0 || !(vval(g.v) > p.tau)) break;   // also ends when there is no remaining row
     if (swaps >= p.max_swaps) {
       if (cta == 0 && tid == 0) set_error(st, PRRP_ERR_SWAP_LIMIT, p.col_offset + 1);
-      return;
+      goto done;
     }
     const int js = g.k1, is = g.k2;
-    for (int i = lane; i < w; i += 32) vs[i] = __ldcg(&p.xvec[((size_t)par * G + g.aux) * kMaxW + i]);
+    fetch_winner(par, g.aux, nullptr, nullptr);
     __syncwarp();
     const double mu = vs[is];
     for (int r = wr0 + tw; r < wr1; r += TPW) {
@@ -390,6 +501,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     st->panel_swaps = swaps;
     st->swaps_total += swaps;
   }
+  }
+done:
+  if constexpr (CL) {
+    __syncwarp();
+    cl_sync_all();                                  // nobody leaves while others may read its records
+  }
 }
 
 template <int W>
@@ -403,11 +520,34 @@ static size_t panel_smem_bytes(int rpc) {
 template <int W>
 static cudaError_t launch_panel_w(PanelParams p, int G, cudaStream_t stream) {
   const size_t smem = panel_smem_bytes<W>(p.rows_per_cta);
-  cudaError_t e = smem_optin(panel_rrqr_kernel<W>);
+  cudaError_t e = smem_optin(panel_rrqr_kernel<W, false>);
   if (e != cudaSuccess) return e;
   void* args[] = {&p};
-  return cudaLaunchCooperativeKernel((const void*)panel_rrqr_kernel<W>, dim3(G),
+  return cudaLaunchCooperativeKernel((const void*)panel_rrqr_kernel<W, false>, dim3(G),
                                      dim3(kPanelThreads), args, smem, stream);
+}
+
+// One cluster of `cs` CTAs (cs up to 16, a non-portable cluster size).
+template <int W>
+static cudaError_t launch_panel_cluster_w(PanelParams p, int cs, cudaStream_t stream) {
+  const size_t smem = panel_smem_bytes<W>(p.rows_per_cta);
+  cudaError_t e = smem_optin(panel_rrqr_kernel<W, true>);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(panel_rrqr_kernel<W, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(kPanelThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, panel_rrqr_kernel<W, true>, p);
 }
 
 int panel_width_class(int w) { return w <= 16 ? 16 : w <= 32 ? 32 : w <= 64 ? 64 : 128; }
@@ -421,11 +561,31 @@ size_t panel_smem_for(int w, int rpc) {
   }
 }
 
+// Panels of at most kClusterRows rows run as one thread-block cluster of up to 16 CTAs of
+// at most 32 rows each (the cooperative grid's split); taller ones as a cooperative grid.
+// (More rows per CTA make each step's FP64 row updates the longest part of the step, and
+// the grid then wins by spreading them over more SMs.)
+constexpr int kClusterRows = 512;
+
 cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t stream) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (p.m <= kClusterRows) {
+    int cs = 2;
+    while (cs < 16 && cs * 32 < p.m) cs *= 2;
+    PanelParams q = p;
+    q.rows_per_cta = (p.m + cs - 1) / cs;
+    switch (panel_width_class(p.w)) {
+      case 16: e = launch_panel_cluster_w<16>(q, cs, stream); break;
+      case 32: e = launch_panel_cluster_w<32>(q, cs, stream); break;
+      case 64: e = launch_panel_cluster_w<64>(q, cs, stream); break;
+      default: e = launch_panel_cluster_w<128>(q, cs, stream); break;
+    }
+    if (e == cudaSuccess) return cudaSuccess;
+    cudaGetLastError();                 // a cluster that cannot be placed: use the grid form
+  }
   std::lock_guard<std::mutex> lock(g_coop_mu);
   if (!g_coop_done[dev]) {
     e = cudaEventCreateWithFlags(&g_coop_done[dev], cudaEventDisableTiming);

@@ -3,10 +3,10 @@
 // Requests (n x n system, 1..many right-hand sides, host buffers) are queued by
 // prrp_server_submit and admitted against an HBM budget.  `lanes` worker threads each own
 // a prrp_ctx and a CUDA stream; whenever a lane is idle it takes the next unit of work:
-//   * the queued requests with n <= 1024 that fit the remaining budget, up to 512 of them,
+//   * the queued requests with n <= 512 that fit the remaining budget, up to 512 of them,
 //     solved together by one prrp_batch_solve launch (FP32 working copy, FP64 pivot
 //     selection and refinement, or the FP64 form), or
-//   * one request with n > 1024: prrp_factor (Schur update in the configured precision,
+//   * one request with n > 512: prrp_factor (Schur update in the configured precision,
 //     FP64 pivoting) into device memory that holds its factors until prrp_solve has
 //     refined its right-hand sides in FP64 against the device copy of A.
 // Requests that arrive while every lane is busy wait in the queue and join the next unit a
@@ -34,7 +34,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr int kSmallMax = 1024;   // largest n sent to the batched kernel
+constexpr int kSmallMax = 512;    // largest n sent to the batched kernel (one CTA per system)
 constexpr int kUnitMax = 512;     // most requests in one batched unit
 
 struct Item {
@@ -71,10 +71,10 @@ struct prrp_server {
 namespace {
 
 size_t request_bytes(int n, int nrhs) {
-  // device A (+ FP64 copy of A for the refinement residual), right-hand sides, factor
-  // workspace (multipliers, solve scratch)
+  // device A (+ FP64 copy of A for the refinement residual, + FP32 copy of the factors for
+  // the correction solves), right-hand sides, factor workspace (multipliers, solve scratch)
   const size_t nn = static_cast<size_t>(n) * n;
-  return 16 * nn + 40 * static_cast<size_t>(n) * std::max(nrhs, 1) + 1024 * static_cast<size_t>(n) + 4096;
+  return 20 * nn + 40 * static_cast<size_t>(n) * std::max(nrhs, 1) + 1024 * static_cast<size_t>(n) + 4096;
 }
 
 double us_between(Clock::time_point a, Clock::time_point b) {
