@@ -1,5 +1,6 @@
 """Benchmark of LU_PRRP on GB300: the plain FP64 factorization (n = 8192, b = 64, tau = 2,
-A iid N(0,1)) followed by a one-right-hand-side solve, per step.
+A iid N(0,1)) followed by a one-right-hand-side solve with FP64 refinement to eta <= 2^-53
+(one correction, usually), per step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,7 +34,7 @@ import numpy as np  # noqa: E402
 
 N_DEFAULT, B_DEFAULT, TAU = 8192, 64, 2.0
 METRIC = "LU_PRRP TFLOP/s and solves/s at FP64-level backward error; p50/p99 solve latency"
-WORKLOAD = "LU_PRRP plain FP64, n=8192, b=64, tau=2, A iid N(0,1), 1-RHS solve per step"
+WORKLOAD = "LU_PRRP plain FP64, n=8192, b=64, tau=2, A iid N(0,1), 1-RHS solve + FP64 refinement per step"
 
 
 def _peaks():
@@ -153,11 +154,36 @@ def run_reference(args) -> None:
     }), flush=True)
 
 
-def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=1):
+def _eta_cols(torch, A, X, B):
+    r = B - A @ X
+    return float((r.abs().sum(0) / (A.abs().sum(0).max() * X.abs().sum(0) + B.abs().sum(0))).max())
+
+
+def plain_fp64(prrp, ctx, torch, dev, As, Bs, b):
+    """The plain FP64 GPU path on the same systems, one after another: prrp_factor (FP64
+    Schur update) + prrp_solve with FP64 refinement until eta <= 2^-53 (usually one
+    correction), so that it is compared at the same backward error; device-resident
+    inputs (copies made before the clock starts).  Returns solves/s and the worst
+    normwise backward error."""
+    work = [(A.clone(), B.clone()) for A, B in zip(As, Bs)]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for (A, X), A0 in zip(work, As):
+        F = prrp.prrp_factor(ctx, A, b=b, prec=0)
+        prrp.prrp_solve(ctx, F, X, A_orig=A0, refine_max_iter=10)
+        F.close()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    eta = max(_eta_cols(torch, A0, X, B0) for (A0, B0), (_, X) in zip(zip(As, Bs), work))
+    return {"solves_per_s": len(work) / dt, "s": dt, "max_eta": eta, "systems": len(work)}
+
+
+def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=1, plain=True):
     """Mixed-precision form: A = Q1 diag(sigma) Q2^T (cond kappa, Q from QR of seeded
     Gaussians), BF16X3 tensor-core Schur update with FP64 pivoting, FP64 refinement of 4
     right-hand sides.  The matrix is generated on the GPU in FP64 (torch QR).  A kappa of
-    0 stands for an iid N(0,1) matrix instead (no QR)."""
+    0 stands for an iid N(0,1) matrix instead (no QR).  The first matrix is also solved by
+    the plain FP64 path for the solves/s comparison."""
     out = {}
     for kappa in kappas:
         g = torch.Generator(device=dev)
@@ -185,12 +211,21 @@ def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=
             if it:
                 times.append(time.perf_counter() - t0)
             F.close()
-        r = B0 - A0 @ B
-        eta = float((r.abs().sum(0) / (A0.abs().sum(0).max() * B.abs().sum(0) + B0.abs().sum(0))).max())
+        eta = _eta_cols(torch, A0, B, B0)
         dt = min(times)
-        out[f"kappa={kappa:g}" if kappa > 0 else "randn"] = {"s": dt, "tflops": 2 * n ** 3 / 3 / dt / 1e12, "solves_per_s": 1.0 / dt,
-                                   "eta": eta, "iterations": info["iterations"]}
-        del A0, A, B0, B
+        key = f"kappa={kappa:g}" if kappa > 0 else "randn"
+        out[key] = {"s": dt, "tflops": 2 * n ** 3 / 3 / dt / 1e12, "solves_per_s": 1.0 / dt,
+                    "eta": eta, "iterations": info["iterations"]}
+        if plain and kappa == kappas[0]:
+            del A, B
+            torch.cuda.empty_cache()
+            pl = plain_fp64(prrp, ctx, torch, dev, [A0], [B0], 64)
+            pl["tflops"] = 2 * n ** 3 / 3 / pl["s"] / 1e12
+            out[key]["plain_fp64"] = pl
+            out[key]["speedup_vs_plain_fp64"] = out[key]["solves_per_s"] / pl["solves_per_s"]
+            del A0, B0
+        else:
+            del A0, A, B0, B
         torch.cuda.empty_cache()
     return {"workload": f"n={n}, b=64, tau=2, cond-controlled A, 4 RHS, "
                         f"{'BF16X3' if prec == 2 else 'TF32'} Schur update + FP64 refinement", "runs": out}
@@ -237,7 +272,7 @@ def form_update(prrp, ctx, torch, dev, n=16384, k=64, reps=5):
     return {"workload": f"Schur update C -= L U, C {m}x{m} FP64, k={k}", "runs": out}
 
 
-def form_batched(prrp, ctx, torch, dev, count=4096, reps=3):
+def form_batched(prrp, ctx, torch, dev, count=4096, reps=3, plain_sample=256):
     """Batched form: 4096 systems, n uniform in [32, 512], b = 16, one RHS, FP32 factor +
     FP64 refinement, in one persistent launch."""
     import prrp_inputs as pi
@@ -260,10 +295,15 @@ def form_batched(prrp, ctx, torch, dev, count=4096, reps=3):
         res[name] = {"s": best, "solves_per_s": count / best,
                      "tflops": sum(2.0 * float(k) ** 3 / 3 for k in sizes) / best / 1e12,
                      "max_eta": max(i["eta"] for i in info), "failed": sum(1 for x in st if x != 0)}
+    # plain FP64 path, one system after another, on a sample of the same systems
+    pl = plain_fp64(prrp, ctx, torch, dev, As[:plain_sample], B0[:plain_sample], 16)
+    pl["sample"] = f"first {plain_sample} of the {count} systems"
+    res["plain_fp64"] = pl
+    res["speedup_vs_plain_fp64"] = res["fp32_factor"]["solves_per_s"] / pl["solves_per_s"]
     return {"workload": f"{count} systems, n uniform in [32, 512], b=16, 1 RHS", "runs": res}
 
 
-def form_served(prrp, ctx, rates=(300.0, 3000.0), count=400, budget=64 << 30):
+def form_served(prrp, ctx, rates=(300.0, 3000.0), count=400, budget=64 << 30, plain_sample=120):
     """Served form: Poisson arrivals, n log-uniform in [64, 4096], RHS count uniform in
     1..16, iid N(0,1); a pool of 48 pre-generated matrices is cycled so request generation
     does not bound the arrival rate."""
@@ -295,6 +335,22 @@ def form_served(prrp, ctx, rates=(300.0, 3000.0), count=400, budget=64 << 30):
                                    "failed": sum(1 for r in results if r["status"] != 0),
                                    "peak_busy_lanes": st["peak_busy_lanes"],
                                    "peak_GB_in_use": st["peak_bytes_in_use"] / 2**30}
+    # plain FP64 path on the same kind of stream: one request after another through the
+    # host-buffer entry point (copies included, as in the server), FP64 refinement to the
+    # same backward error
+    sample = reqs[:plain_sample]
+    sols = []
+    t0 = time.perf_counter()
+    for A, B, X in sample:
+        sols.append(prrp.prrp_gesv_host(ctx, A, B, b=64, refine_max_iter=10)[0])
+    dt = time.perf_counter() - t0
+    worst = max(float(np.abs(B[:, c] - A @ Xs[:, c]).sum()
+                      / (np.abs(A).sum(0).max() * np.abs(Xs[:, c]).sum() + np.abs(B[:, c]).sum()))
+                for (A, B, _), Xs in zip(sample, sols) for c in range(B.shape[1]))
+    out["plain_fp64"] = {"solves_per_s": len(sample) / dt, "s": dt, "max_eta": worst,
+                         "sample": f"first {len(sample)} requests of the last stream, back to back"}
+    best = max(v["solves_per_s"] for k, v in out.items() if k.startswith("rate="))
+    out["speedup_vs_plain_fp64"] = best / out["plain_fp64"]["solves_per_s"]
     return {"workload": f"{count} requests per rate, n log-uniform [64, 4096], nrhs 1..16, "
                         f"64 GB admission budget, 4 lanes", "runs": out}
 
@@ -330,7 +386,7 @@ def run_ours(args) -> None:
         A.copy_(A0)
         B.copy_(rhs0)
         F = prrp.prrp_factor(ctx, A, b=b, tau=TAU, stream=stream)
-        prrp.prrp_solve(ctx, F, B, stream=stream)
+        prrp.prrp_solve(ctx, F, B, A_orig=A0, refine_max_iter=10, stream=stream)
         F.close()
 
     for _ in range(args.warmup):
@@ -374,12 +430,14 @@ def run_ours(args) -> None:
     hB.copy_(rhs0.cpu())
     hX = torch.empty((n, 1), dtype=torch.float64, pin_memory=True)
     e2e_steps = max(1, min(args.steps, 3))
-    prrp.prrp_gesv_host(ctx, hA.numpy(), hB.numpy(), b=b, tau=TAU, X=hX.numpy(), stream=stream)
+    prrp.prrp_gesv_host(ctx, hA.numpy(), hB.numpy(), b=b, tau=TAU, X=hX.numpy(), refine_max_iter=10,
+                        stream=stream)
     barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        prrp.prrp_gesv_host(ctx, hA.numpy(), hB.numpy(), b=b, tau=TAU, X=hX.numpy(), stream=stream)
+        prrp.prrp_gesv_host(ctx, hA.numpy(), hB.numpy(), b=b, tau=TAU, X=hX.numpy(), refine_max_iter=10,
+                            stream=stream)
     torch.cuda.synchronize(dev)
     barrier()
     e2e_s = time.perf_counter() - t0
@@ -390,6 +448,7 @@ def run_ours(args) -> None:
 
     forms = {}
     if rank == 0 and world == 1 and not args.no_forms:
+        forms["update"] = form_update(prrp, ctx, torch, dev)
         forms["mixed"] = form_mixed(prrp, ctx, torch, dev)
         forms["batched"] = form_batched(prrp, ctx, torch, dev)
         forms["served"] = form_served(prrp, ctx)
