@@ -282,8 +282,29 @@ enum {
 
 /* Enable (1) or disable (0) per-kernel-class timing: each launch of ctx is bracketed by
  * CUDA events on its stream and the elapsed times are summed per class after the call's
- * synchronize.  Launch and algorithmic-flop counters are kept whether or not it is on. */
+ * synchronize.  Launch and algorithmic-flop counters are kept whether or not it is on.
+ * enable = 2 also keeps a launch timeline (see prrp_ctx_timeline), starting from an event
+ * recorded in this call; any call to this function clears the timeline.  INVALID_ARG for
+ * other values. */
 prrp_status prrp_ctx_set_timing(prrp_ctx* ctx, int enable);
+
+/* Panel kernel placement for this context (a tuning knob; results do not change).  Panels
+ * (Algorithm 2 on an m x w panel) with m <= cluster_max_rows run as one thread-block
+ * cluster of up to 16 CTAs that the hardware co-schedules, so panels of different
+ * contexts or streams may run at the same time; taller panels run as one cooperative grid
+ * over the SMs, and cooperative panels of one device run one at a time.  For a single
+ * factorization the grid is faster above 512 rows; several factorizations sharing the GPU
+ * (the serve loop) gain from clusters.  cluster_max_rows in [0, 2048], 0 = the default
+ * (512); INVALID_ARG otherwise. */
+prrp_status prrp_ctx_set_panel_mode(prrp_ctx* ctx, int cluster_max_rows);
+
+/* The launch timeline kept under timing level 2: for each timed launch, in the order the
+ * calls collected them, its kernel class (PRRP_KIND_*) and its start and end in ms after
+ * the base event.  Launches on different streams overlap when they ran concurrently.
+ * Copies min(cap, total) entries into the host arrays kinds, t0_ms, t1_ms (each at least
+ * cap long) and stores the total in *count. */
+prrp_status prrp_ctx_timeline(prrp_ctx* ctx, int cap, int* kinds, double* t0_ms, double* t1_ms,
+                              int* count);
 
 /* Copy the per-class totals since the last reset (arrays of PRRP_KIND_COUNT; any may be
  * NULL): milliseconds (only while timing is on), kernel launches, algorithmic flops

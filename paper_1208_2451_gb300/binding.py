@@ -66,6 +66,8 @@ _SIGS = {
     "prrp_panel_select_noalloc": (_I, [_I, _I, _P, _I, _D, _I, _P, _P, C.POINTER(_I), _P]),
     "prrp_ctx_set_timing": (_I, [_P, _I]),
     "prrp_ctx_kernel_stats": (_I, [_P, _P, _P, _P, _I]),
+    "prrp_ctx_timeline": (_I, [_P, _I, _P, _P, _P, C.POINTER(_I)]),
+    "prrp_ctx_set_panel_mode": (_I, [_P, _I]),
     "prrp_server_create": (_I, [_P, C.c_size_t, C.POINTER(prrp_opts), _I, C.POINTER(_P)]),
     "prrp_server_submit": (_I, [_P, _P, C.POINTER(C.c_uint64)]),
     "prrp_server_wait": (_I, [_P, C.c_uint64, C.c_int64, _P]),
@@ -299,8 +301,28 @@ def prrp_selftest_wait(ctx: Context, spin_limit: int = 20000, stream=None) -> in
 KINDS = ["scan", "panel", "permute", "update", "diag", "u12", "lfix", "solve", "batch"]
 
 
-def prrp_ctx_set_timing(ctx: Context, enable: bool = True) -> None:
-    _check(_lib.prrp_ctx_set_timing(ctx.handle, int(bool(enable))), "prrp_ctx_set_timing")
+def prrp_ctx_set_timing(ctx: Context, enable=True) -> None:
+    """enable: False/0 off, True/1 per-class totals, 2 also a launch timeline."""
+    _check(_lib.prrp_ctx_set_timing(ctx.handle, int(enable)), "prrp_ctx_set_timing")
+
+
+def prrp_ctx_set_panel_mode(ctx: Context, cluster_max_rows: int = 0) -> None:
+    """Panels of at most cluster_max_rows rows run as one thread-block cluster (0: default)."""
+    _check(_lib.prrp_ctx_set_panel_mode(ctx.handle, int(cluster_max_rows)), "prrp_ctx_set_panel_mode")
+
+
+def prrp_ctx_timeline(ctx: Context) -> list:
+    """Launch timeline kept under timing level 2: [(kind name, start ms, end ms), ...]."""
+    cnt = C.c_int(0)
+    _check(_lib.prrp_ctx_timeline(ctx.handle, 0, None, None, None, C.byref(cnt)), "prrp_ctx_timeline")
+    n = cnt.value
+    if n == 0:
+        return []
+    k = (C.c_int * n)()
+    a = (C.c_double * n)()
+    b = (C.c_double * n)()
+    _check(_lib.prrp_ctx_timeline(ctx.handle, n, k, a, b, C.byref(cnt)), "prrp_ctx_timeline")
+    return [(KINDS[k[i]], a[i], b[i]) for i in range(min(n, cnt.value))]
 
 
 def prrp_ctx_kernel_stats(ctx: Context, reset: bool = False) -> dict:

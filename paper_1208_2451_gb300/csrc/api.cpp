@@ -98,6 +98,9 @@ struct prrp_ctx {
   size_t y32_cap = 0;
   unsigned* tcount = nullptr;
   size_t tcount_cap = 0;
+  int panel_cluster_rows = 0;       // prrp_ctx_set_panel_mode (0: the library default)
+  unsigned* gemm_ctr = nullptr;     // tile counters of the FP64 updates (critical, rest stream)
+  size_t gemm_ctr_cap = 0;
   unsigned long long factor_gen = 0;
   // batched solves: metadata, per-CTA workspace, outputs, tuned launch shapes, graphs
   unsigned char* bmeta = nullptr;
@@ -117,6 +120,10 @@ struct prrp_ctx {
   std::vector<Rec> recs;
   size_t nrec = 0;
   double kind_ms[PRRP_KIND_COUNT] = {};
+  // optional launch timeline (timing level 2): (kind, start, end) in ms after tl_base
+  cudaEvent_t tl_base = nullptr;
+  struct Span { int kind; float t0, t1; };
+  std::vector<Span> timeline;
   long long kind_launches[PRRP_KIND_COUNT] = {};
   long long kind_flops[PRRP_KIND_COUNT] = {};
 };
@@ -164,6 +171,10 @@ void collect_timing(prrp_ctx* ctx) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->recs[i].a, ctx->recs[i].b) == cudaSuccess)
       ctx->kind_ms[ctx->recs[i].kind] += ms;
+    float t0 = 0.f, t1 = 0.f;       // timeline: the launch's interval after the base event
+    if (ctx->tl_base && cudaEventElapsedTime(&t0, ctx->tl_base, ctx->recs[i].a) == cudaSuccess &&
+        cudaEventElapsedTime(&t1, ctx->tl_base, ctx->recs[i].b) == cudaSuccess)
+      ctx->timeline.push_back({ctx->recs[i].kind, t0, t1});
   }
   ctx->nrec = 0;
 }
@@ -256,6 +267,7 @@ prrp_status enqueue_panel(prrp_ctx* ctx, const double* P, long long ldp, int m, 
   p.P = P; p.ldp = ldp; p.m = m; p.w = w; p.tau = tau; p.max_swaps = max_swaps;
   p.col_offset = col_offset; p.L21 = L21; p.ldl = ldl; p.order = order; p.pairs = pairs;
   p.st = ctx->st; p.xval = ctx->xval; p.xkey = ctx->xkey; p.xvec = ctx->xvec; p.rows_per_cta = rpc;
+  p.cluster_rows = ctx->panel_cluster_rows;
   cudaError_t e = launch_panel(p, G, s);
   if (e == cudaErrorCooperativeLaunchTooLarge) return PRRP_ERR_UNSUPPORTED;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "panel launch");
@@ -350,6 +362,7 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
   if (!ctx) return PRRP_OK;
   cudaSetDevice(ctx->device);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  if (ctx->tl_base) cudaEventDestroy(ctx->tl_base);
   if (ctx->bgraph.exec) cudaGraphExecDestroy(ctx->bgraph.exec);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   if (ctx->bmeta) cudaFree(ctx->bmeta);
@@ -358,7 +371,7 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
   void* ptrs[] = {ctx->st, ctx->xval, ctx->xkey, ctx->xvec, ctx->pairs, ctx->ipiv, ctx->order,
                   ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB, ctx->tcws,
                   ctx->l21b, ctx->a12, ctx->tcws2, ctx->dinv64, ctx->dinv32, ctx->lu32, ctx->y32,
-                  ctx->tcount};
+                  ctx->tcount, ctx->gemm_ctr};
   for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
   if (ctx->s_rest) cudaStreamDestroy(ctx->s_rest);
   if (ctx->s_blk) cudaStreamDestroy(ctx->s_blk);
@@ -436,10 +449,12 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
   CK(cudaStreamWaitEvent(sb, ev_start, 0));
   cudaEvent_t ev_rest = nullptr, ev_blk = nullptr;        // of the previous panel
   // C (mm x nn) -= L (mm x kk, ld kk) * U (kk x nn, ld ldu)
+  if ((ps = grow(ctx, &ctx->gemm_ctr, &ctx->gemm_ctr_cap, 2)) != PRRP_OK) return fail(ps);
   auto update = [&](int mm, int nn, int kk, const double* L, const double* U, long long ldu, double* C,
                     unsigned char* ws, cudaStream_t st) -> cudaError_t {
-    if (o.prec == PRRP_FP64)
-      return launch_gemm_fp64(mm, nn, kk, L, kk, U, ldu, C, lda, ctx->st, 1, ctx->num_sms, st, 1);
+    if (o.prec == PRRP_FP64)   // one tile counter per stream: the narrow and rest updates overlap
+      return launch_gemm_fp64(mm, nn, kk, L, kk, U, ldu, C, lda, ctx->st, 1, ctx->num_sms, st, 1,
+                              ctx->gemm_ctr + (st == sr ? 1 : 0));
     return launch_tc_update(o.prec, mm, nn, kk, L, kk, U, ldu, C, lda, ctx->st, 1, ws, st);
   };
   for (int jp = 0, k0 = 0; k0 < n; k0 += b, ++jp) {
@@ -760,10 +775,14 @@ prrp_status prrp_panel_select(prrp_ctx* ctx, int m, int w, const double* dP, int
   if (ps != PRRP_OK) return ps;
   if ((ps = grow_i(ctx, &ctx->order, &ctx->order_cap, m)) != PRRP_OK) return ps;
   CK(cudaMemsetAsync(ctx->st, 0, sizeof(DevState), s));
-  ps = enqueue_panel(ctx, dP, ldp, m, w, tau, max_swaps, 0, dL21, w, ctx->order, nullptr, s);
+  {
+    Timed t(ctx, s, PRRP_KIND_PANEL);
+    ps = enqueue_panel(ctx, dP, ldp, m, w, tau, max_swaps, 0, dL21, w, ctx->order, nullptr, s);
+  }
   if (ps != PRRP_OK) return ps;
   DevState h{};
   if ((ps = read_state(ctx, &h, s)) != PRRP_OK) return ps;
+  collect_timing(ctx);
   if (hSwaps) *hSwaps = h.panel_swaps;
   if (h.status != 0) return (prrp_status)h.status;
   if (hOrder) CK(cudaMemcpy(hOrder, ctx->order, sizeof(int) * m, cudaMemcpyDeviceToHost));
@@ -1043,8 +1062,36 @@ prrp_status prrp_ctx_device(const prrp_ctx* ctx, int* device) {
 }
 
 prrp_status prrp_ctx_set_timing(prrp_ctx* ctx, int enable) {
-  if (!ctx) return PRRP_ERR_INVALID_ARG;
+  if (!ctx || enable < 0 || enable > 2) return PRRP_ERR_INVALID_ARG;
   ctx->timing = enable != 0;
+  ctx->timeline.clear();
+  if (enable == 2) {
+    CK(cudaSetDevice(ctx->device));
+    if (!ctx->tl_base) CK(cudaEventCreate(&ctx->tl_base));
+    CK(cudaEventRecord(ctx->tl_base, 0));
+    CK(cudaEventSynchronize(ctx->tl_base));
+  } else if (ctx->tl_base) {
+    cudaEventDestroy(ctx->tl_base);
+    ctx->tl_base = nullptr;
+  }
+  return PRRP_OK;
+}
+
+prrp_status prrp_ctx_set_panel_mode(prrp_ctx* ctx, int cluster_max_rows) {
+  if (!ctx || cluster_max_rows < 0 || cluster_max_rows > 2048) return PRRP_ERR_INVALID_ARG;
+  ctx->panel_cluster_rows = cluster_max_rows;
+  return PRRP_OK;
+}
+
+prrp_status prrp_ctx_timeline(prrp_ctx* ctx, int cap, int* kinds, double* t0_ms, double* t1_ms, int* count) {
+  if (!ctx || cap < 0 || !count || (cap > 0 && (!kinds || !t0_ms || !t1_ms))) return PRRP_ERR_INVALID_ARG;
+  const int n = static_cast<int>(std::min<size_t>(ctx->timeline.size(), static_cast<size_t>(cap)));
+  for (int i = 0; i < n; ++i) {
+    kinds[i] = ctx->timeline[i].kind;
+    t0_ms[i] = ctx->timeline[i].t0;
+    t1_ms[i] = ctx->timeline[i].t1;
+  }
+  *count = static_cast<int>(ctx->timeline.size());
   return PRRP_OK;
 }
 

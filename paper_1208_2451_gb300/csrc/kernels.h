@@ -26,6 +26,7 @@ struct PanelParams {
   int2* xkey;             // [2][G]
   double* xvec;           // [2][G][kMaxW]
   int rows_per_cta;
+  int cluster_rows;       // panels of at most this many rows run as one cluster (0: default)
 };
 
 int panel_width_class(int w);
@@ -40,10 +41,13 @@ cudaError_t launch_permute(double* A, long long lda, int n, int k0, const int* p
                            int max_pairs, int* perm, DevState* st, cudaStream_t s);
 
 // C -= L * U in FP64 (DFMA), C m x n, L m x k, U k x n, k <= kMaxW; tracks max |C| into
-// st->gmax_bits when track != 0.
+// st->gmax_bits when track != 0.  one_per_sm: 64 x 64 tiles, one persistent CTA per SM,
+// tiles claimed from the device counter tile_ctr when it is given (zeroed on stream s
+// before the launch; one counter per concurrently running update).
 cudaError_t launch_gemm_fp64(int m, int n, int k, const double* L, long long ldl,
                              const double* U, long long ldu, double* C, long long ldc,
-                             DevState* st, int track, int num_sms, cudaStream_t s, int one_per_sm = 0);
+                             DevState* st, int track, int num_sms, cudaStream_t s, int one_per_sm = 0,
+                             unsigned* tile_ctr = nullptr);
 
 // Same update on tcgen05 tensor cores, prec = PRRP_TF32 or PRRP_BF16X3 (FP32 accumulation,
 // FP64 C); ws holds the split operands (tc_workspace_bytes).

@@ -98,8 +98,10 @@ cudaError_t launch_permute(double* A, long long lda, int n, int k0, const int* p
 }
 
 // ---------------------------------------------------------------- FP64 Schur update
-// C -= L U with a BM x BN tile per CTA (persistent, strided tile loop), 256 threads each
-// owning a (BM/16) x (BN/16) register block.  The k dimension (<= 128) is staged through
+// C -= L U with a BM x BN tile per CTA (persistent tile loop), 256 threads each owning a
+// (BM/16) x (BN/16) register block.  Tiles are taken in order from a counter (one atomic
+// per tile, claimed a tile ahead) when one is given, so SMs that also host other kernels
+// of the look-ahead simply take fewer tiles; otherwise CTA c takes tiles c, c + grid, ...  The k dimension (<= 128) is staged through
 // shared memory in chunks of 64; operands are stored k-major so each thread's row and column
 // fragments are contiguous.  The FP64 pipe is the bound: a 128 x 128 x 64 tile is 1M DFMA
 // against 128 KB of operand traffic.
@@ -110,7 +112,8 @@ __global__ void __launch_bounds__(256, 1) gemm_fp64_kernel(int M, int N, int K,
                                                            const double* __restrict__ L, long long ldl,
                                                            const double* __restrict__ U, long long ldu,
                                                            double* __restrict__ C, long long ldc,
-                                                           DevState* st, int track) {
+                                                           DevState* st, int track,
+                                                           unsigned* __restrict__ tile_ctr) {
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int BMP = BM + 2;                      // padded k-major strides
   constexpr int BNP = BN + 2;
@@ -123,7 +126,16 @@ __global__ void __launch_bounds__(256, 1) gemm_fp64_kernel(int M, int N, int K,
   const int tiles_n = (N + BN - 1) / BN;
   const int tiles = ((M + BM - 1) / BM) * tiles_n;
   unsigned long long cmax = 0ull;               // max |C| as an IEEE bit pattern
-  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+  __shared__ int s_tile;
+  int tile = blockIdx.x;
+  if (tile_ctr) {
+    if (tid == 0) s_tile = static_cast<int>(atomicAdd(tile_ctr, 1u));
+    __syncthreads();
+    tile = s_tile;
+  }
+  while (tile < tiles) {
+    unsigned claim = 0;
+    if (tile_ctr && tid == 0) claim = atomicAdd(tile_ctr, 1u);   // consumed after the tile
     const int bm = (tile / tiles_n) * BM, bn = (tile % tiles_n) * BN;
     // warm L2 with this tile's C rows while the operands are staged
     for (int r = tid; r < BM; r += 256)
@@ -178,6 +190,14 @@ __global__ void __launch_bounds__(256, 1) gemm_fp64_kernel(int M, int N, int K,
         }
       }
     }
+    if (tile_ctr) {
+      __syncthreads();                  // everyone has read the previous s_tile
+      if (tid == 0) s_tile = static_cast<int>(claim);
+      __syncthreads();
+      tile = s_tile;
+    } else {
+      tile += gridDim.x;
+    }
   }
   if (track) {
     for (int off = 16; off > 0; off >>= 1) cmax = max_bits(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
@@ -188,24 +208,27 @@ __global__ void __launch_bounds__(256, 1) gemm_fp64_kernel(int M, int N, int K,
 template <int BM, int BN>
 static cudaError_t launch_gemm_tile(int m, int n, int k, const double* L, long long ldl,
                                     const double* U, long long ldu, double* C, long long ldc,
-                                    DevState* st, int track, int grid, cudaStream_t s) {
+                                    DevState* st, int track, int grid, cudaStream_t s,
+                                    unsigned* tile_ctr = nullptr) {
   const size_t smem = (size_t)kGemmKC * ((BM + 2) + (BN + 2)) * sizeof(double);
   cudaError_t e = smem_optin(gemm_fp64_kernel<BM, BN>);
   if (e != cudaSuccess) return e;
-  gemm_fp64_kernel<BM, BN><<<grid, 256, smem, s>>>(m, n, k, L, ldl, U, ldu, C, ldc, st, track);
+  if (tile_ctr && (e = cudaMemsetAsync(tile_ctr, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+  gemm_fp64_kernel<BM, BN><<<grid, 256, smem, s>>>(m, n, k, L, ldl, U, ldu, C, ldc, st, track, tile_ctr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_fp64(int m, int n, int k, const double* L, long long ldl,
                              const double* U, long long ldu, double* C, long long ldc,
-                             DevState* st, int track, int num_sms, cudaStream_t s, int one_per_sm) {
+                             DevState* st, int track, int num_sms, cudaStream_t s, int one_per_sm,
+                             unsigned* tile_ctr) {
   if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
   if (one_per_sm) {
     // leave room on every SM for a co-resident panel CTA (look-ahead): 64 x 64 tiles,
-    // one persistent CTA per SM
+    // one persistent CTA per SM, tiles claimed from tile_ctr when given
     const long long t64 = (long long)((m + 63) / 64) * ((n + 63) / 64);
     return launch_gemm_tile<64, 64>(m, n, k, L, ldl, U, ldu, C, ldc, st, track,
-                                    (int)std::min<long long>(t64, num_sms), s);
+                                    (int)std::min<long long>(t64, num_sms), s, tile_ctr);
   }
   // pick the tile whose wave count wastes least: cost ~ ceil(tiles / sms) * tile area
   const long long t128 = (long long)((m + 127) / 128) * ((n + 127) / 128);

@@ -27,6 +27,7 @@
 //
 // Outputs: L21 = M^T (row w + r of the final order -> L21 row r), the final position of
 // every panel row, and a list of (destination, source) row moves for the permute kernel.
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -261,8 +262,9 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
             __nanosleep(20);
           }
         } else {
-          __threadfence();
-          atomicAdd(&st->barrier, 1u);
+          // release: this warp's record (ordered by the warp barrier above) before the
+          // arrival; acquire: the other CTAs' records after the last arrival is seen
+          asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&st->barrier) : "memory");
           while (ld_acquire_u32(&st->barrier) < target) {
             if (dev_status(st) != 0) { ok = 0; break; }
             if (++spins > limit) {
@@ -272,7 +274,6 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
             }
             __nanosleep(32);
           }
-          __threadfence();
         }
         s_ok = ok;
       }
@@ -561,18 +562,22 @@ size_t panel_smem_for(int w, int rpc) {
   }
 }
 
-// Panels of at most kClusterRows rows run as one thread-block cluster of up to 16 CTAs of
-// at most 32 rows each (the cooperative grid's split); taller ones as a cooperative grid.
-// (More rows per CTA make each step's FP64 row updates the longest part of the step, and
-// the grid then wins by spreading them over more SMs.)
+// Panels of at most kClusterRows rows (or PanelParams::cluster_rows, at most
+// kClusterRowsMax) run as one thread-block cluster of up to 16 CTAs, 32 rows per CTA up to
+// 512 rows and m / 16 beyond; taller ones as a cooperative grid.  For a single
+// factorization the grid is faster once a cluster CTA would hold more than 32 rows (each
+// step's FP64 row updates then dominate it), but clusters do not serialize across streams,
+// which pays when several factorizations share the GPU.
 constexpr int kClusterRows = 512;
+constexpr int kClusterRowsMax = 2048;
 
 cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t stream) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (p.m <= kClusterRows) {
+  const int crows = p.cluster_rows > 0 ? std::min(p.cluster_rows, kClusterRowsMax) : kClusterRows;
+  if (p.m <= crows) {
     int cs = 2;
     while (cs < 16 && cs * 32 < p.m) cs *= 2;
     PanelParams q = p;

@@ -208,6 +208,28 @@ def test_substitution_shapes(prrp, ctx, n, nrhs):
     np.testing.assert_allclose(dB.cpu().numpy(), Xo, rtol=1e-9, atol=1e-10)
 
 
+@pytest.mark.parametrize("n,b,tau", [(2000, 64, 2.0), (1500, 128, 2.0), (900, 32, 1.05)])
+def test_cluster_panels_up_to_2048_rows(prrp, n, b, tau):
+    """Rows a1-a3 in cluster mode with up to 128 rows per CTA (the serve loop's setting):
+    the same parity bar as the default placement, and the same bits as the cooperative grid
+    (identical arithmetic, only the exchange differs)."""
+    A = pi.randn(n, 600 + n)
+    c = prrp.prrp_create(0)
+    try:
+        prrp.prrp_ctx_set_panel_mode(c, 2048)
+        check_parity(prrp, c, A, b, tau=tau)
+        LU_c, perm_c, _ = gpu_factor(prrp, c, A, b, tau)
+    finally:
+        c.close()
+    c = prrp.prrp_create(0)
+    try:
+        LU_g, perm_g, _ = gpu_factor(prrp, c, A, b, tau)
+    finally:
+        c.close()
+    assert np.array_equal(perm_c, perm_g)
+    assert np.array_equal(LU_c, LU_g)
+
+
 def test_gesv_host(prrp, ctx):
     n = 700
     A = pi.randn(n, 8)
