@@ -263,6 +263,8 @@ prrp_status enqueue_panel(prrp_ctx* ctx, const double* P, long long ldp, int m, 
   prrp_status ps = panel_grid(ctx, m, w, &G, &rpc);
   if (ps != PRRP_OK) return ps;
   CK(cudaMemsetAsync(&ctx->st->barrier, 0, 2 * sizeof(unsigned), s));
+  // the exchange keys double as the reflector-ready flags of the QRCP steps
+  CK(cudaMemsetAsync(ctx->xkey, 0, 2 * sizeof(int2) * G, s));
   PanelParams p{};
   p.P = P; p.ldp = ldp; p.m = m; p.w = w; p.tau = tau; p.max_swaps = max_swaps;
   p.col_offset = col_offset; p.L21 = L21; p.ldl = ldl; p.order = order; p.pairs = pairs;

@@ -77,9 +77,11 @@ extern "C" prrp_status prrp_panel_select_noalloc(int m, int w, const double* dP,
   if (scratch_address(dev, &base) != cudaSuccess) return PRRP_ERR_CUDA;
   DevState* st = reinterpret_cast<DevState*>(base);
   // The array keeps the previous call's contents: clear the state word (error status,
-  // barrier arrivals, counters).  The exchange records need no clearing: each is written
-  // before it is read within a call.
+  // barrier arrivals, counters) and the exchange keys (ready flags).  The other exchange
+  // records need no clearing: each is written before it is read within a call.
   if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return PRRP_ERR_CUDA;
+  // the exchange keys double as the panel's reflector-ready flags: they start at zero
+  if (cudaMemsetAsync(base + kStateBytes + kValBytes, 0, kKeyBytes, s) != cudaSuccess) return PRRP_ERR_CUDA;
   PanelParams p{};
   p.P = dP; p.ldp = ldp; p.m = m; p.w = w; p.tau = tau; p.max_swaps = max_swaps;
   p.col_offset = 0; p.L21 = dL21; p.ldl = w; p.order = dOrder; p.pairs = nullptr;

@@ -89,6 +89,36 @@ __device__ __forceinline__ Cand warp_argmax(const Cand& c) {
   return r;
 }
 
+// QRCP proposals carry one 64-bit key: the squared norm's IEEE bits with the low kPosBits
+// bits replaced by (kPosMask - position).  The largest key is the largest norm, ties (and
+// norms equal to 2^-32 relative, far inside the 1e-8 decision margin) to the smallest
+// position; a key without norm bits (zero norm) still beats "no candidate" (key 0).
+constexpr int kPosBits = 20;
+constexpr unsigned long long kPosMask = (1ull << kPosBits) - 1;
+__device__ __forceinline__ unsigned long long qrcp_key(double nrm, int pos) {
+  const long long b = __double_as_longlong(nrm);
+  return (static_cast<unsigned long long>(b < 0 ? 0 : b) & ~kPosMask) | (kPosMask - static_cast<unsigned>(pos));
+}
+__device__ __forceinline__ int key_pos(unsigned long long k) { return static_cast<int>(kPosMask - (k & kPosMask)); }
+
+// The largest key of a full warp with the payload of its lane (keys are unique or zero).
+__device__ __forceinline__ Cand warp_max_key(const Cand& c) {
+  const unsigned full = 0xffffffffu;
+  const unsigned hi = static_cast<unsigned>(c.v >> 32), lo = static_cast<unsigned>(c.v);
+  const unsigned mhi = __reduce_max_sync(full, hi);
+  const unsigned mlo = __reduce_max_sync(full, hi == mhi ? lo : 0u);
+  Cand r;
+  r.v = (static_cast<unsigned long long>(mhi) << 32) | mlo;
+  r.k1 = 0;
+  r.k2 = 0;
+  r.aux = __shfl_sync(full, c.aux, __ffs(__ballot_sync(full, c.v == r.v)) - 1);
+  return r;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Sum over the TEAM lanes of a row team.  Every lane receives the same bits: the xor
 // butterfly adds the same pairs in each lane, only commuted.
 template <int TEAM>
@@ -130,6 +160,10 @@ __device__ __forceinline__ unsigned cl_ld_acquire(uint32_t a) {
   asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
   return v;
 }
+__device__ __forceinline__ void cl_st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.cluster.shared::cta.u32 [%0], %1;"
+               ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))), "r"(v) : "memory");
+}
 __device__ __forceinline__ void cl_fence() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
 // every thread of every CTA of the cluster (hardware barrier)
 __device__ __forceinline__ void cl_sync_all() {
@@ -165,7 +199,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   __shared__ Cand s_wc[kWarps];
   __shared__ int s_ok;
   __shared__ double s_xval[CL ? 2 * kXVal : 1];    // cluster mode: this CTA's records
-  __shared__ int2 s_xkey[CL ? 2 : 1];
+  __shared__ int2 s_xkey[CL ? 2 : 1];               //   (QRCP: .x = reflector-ready flag)
   __shared__ double s_xrow[CL ? 2 * W : 1];
   __shared__ unsigned s_ctr;                        // cluster mode: the barrier (CTA 0's)
   __shared__ Cand s_gbest;                          // cluster mode: this step's winner,
@@ -176,8 +210,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   if constexpr (!CL) {
     if (dev_status(st) != 0) return;
   } else {
-    if (threadIdx.x == 0) s_ctr = 0;
-    cl_sync_all();                                  // counter zeroed, every CTA running
+    if (threadIdx.x == 0) {
+      s_ctr = 0;
+      s_xkey[0] = make_int2(0, 0);
+      if (CL) s_xkey[CL ? 1 : 0] = make_int2(0, 0);
+    }
+    cl_sync_all();                                  // counter and flags zeroed, every CTA running
   }
   {
 
@@ -218,30 +256,29 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   // Gather the warps' proposals, publish this CTA's best with its row values (and, for a
   // QRCP step t >= 0, the reflector that row would give), grid barrier.  Returns false when
   // the barrier gave up (an error is recorded) and the CTA must return.
+  // QRCP steps (t >= 0) exchange packed keys (qrcp_key); the proposing CTA arrives first
+  // and computes its row's reflector while the others arrive, publishing alpha and beta
+  // behind a ready flag (the exchange's sequence number) that readers wait for.
   auto publish_and_sync = [&](Cand c, int par, unsigned site, int t) -> bool {
-    c = warp_argmax(c);
+    const bool qr = t >= 0;
+    c = qr ? warp_max_key(c) : warp_argmax(c);
     if (lane == 0) s_wc[warp] = c;
     __syncthreads();
     if (warp == 0) {
       Cand d = lane < kWarps ? s_wc[lane] : Cand{0ull, 0x7fffffff, 0x7fffffff, -1};
-      d = warp_argmax(d);
+      d = qr ? warp_max_key(d) : warp_argmax(d);
       const size_t slot = (size_t)par * G + cta;
       double* xv = CL ? s_xval + par * kXVal : p.xval + slot * kXVal;
       double* xr = CL ? s_xrow + par * W : p.xvec + slot * kMaxW;
+      const bool has = d.v != 0ull && d.aux >= 0;
       if (lane == 0) {
         xv[0] = vval(d.v);
-        if (t >= 0 && d.aux >= 0 && d.v != 0ull) {
-          // H = I - beta v v^T with H x = alpha e_1 for x = B(t:w, row): ||x|| = sqrt of the
-          // remaining squared norm, v = x - alpha e_1, v^T v = 2 ||x|| (||x|| + |x_t|)
-          const double x0 = Ps[d.aux * SP + t];
-          const double normx = sqrt(vval(d.v));
-          xv[1] = (x0 >= 0.0) ? -normx : normx;
-          xv[2] = 1.0 / (normx * (normx + abs_int(x0)));
+        if (!qr) {
+          if (CL) s_xkey[par] = make_int2(d.k1, d.k2);
+          else p.xkey[slot] = make_int2(d.k1, d.k2);
         }
-        if (CL) s_xkey[par] = make_int2(d.k1, d.k2);
-        else p.xkey[slot] = make_int2(d.k1, d.k2);
       }
-      if (d.aux >= 0)
+      if (has)
         for (int i = lane; i < w; i += 32) xr[i] = Ps[d.aux * SP + i];
       __syncwarp();
       if (lane == 0) {
@@ -249,10 +286,26 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
         const unsigned limit = st->spin_limit ? st->spin_limit : kSpinLimit;
         unsigned spins = 0;
         int ok = 1;
+        // the reflector of this CTA's candidate, after arriving: H = I - beta v v^T with
+        // H x = alpha e_1 for x = B(t:w, row); ||x|| = sqrt of the remaining squared norm,
+        // v = x - alpha e_1, v^T v = 2 ||x|| (||x|| + |x_t|)
+        auto reflector = [&]() {
+          if (qr && has) {
+            const double x0 = Ps[d.aux * SP + t];
+            const double normx = sqrt(nrm[d.aux]);
+            xv[1] = (x0 >= 0.0) ? -normx : normx;
+            xv[2] = 1.0 / (normx * (normx + abs_int(x0)));
+          }
+          if (qr) {
+            if (CL) cl_st_release(reinterpret_cast<unsigned*>(&s_xkey[par].x), nbar + 1);
+            else st_release_u32(reinterpret_cast<unsigned*>(&p.xkey[slot].x), nbar + 1);
+          }
+        };
         if constexpr (CL) {
           const uint32_t ctr = cl_map(&s_ctr, 0);
           cl_fence();
           cl_arrive(ctr);
+          reflector();
           while (cl_ld_acquire(ctr) < target) {
             if (++spins > limit) {
               if (atomicCAS(&st->status, 0, PRRP_ERR_TIMEOUT) == 0) st->timeout_site = site;
@@ -265,6 +318,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
           // release: this warp's record (ordered by the warp barrier above) before the
           // arrival; acquire: the other CTAs' records after the last arrival is seen
           asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&st->barrier) : "memory");
+          reflector();
           while (ld_acquire_u32(&st->barrier) < target) {
             if (dev_status(st) != 0) { ok = 0; break; }
             if (++spins > limit) {
@@ -286,14 +340,37 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
           (void)cl_ld_acquire(ctr);
           Cand g{0ull, 0x7fffffff, 0x7fffffff, -1};
           if (lane < G) {
-            const int2 k = cl_ld_int2(cl_map(&s_xkey[par], lane));
-            g = Cand{vbits(cl_ld_f64(cl_map(&s_xval[par * kXVal], lane))), k.x, k.y, lane};
+            const unsigned long long v = vbits(cl_ld_f64(cl_map(&s_xval[par * kXVal], lane)));
+            if (qr) {
+              g = Cand{v, 0, 0, lane};
+            } else {
+              const int2 k = cl_ld_int2(cl_map(&s_xkey[par], lane));
+              g = Cand{v, k.x, k.y, lane};
+            }
           }
-          g = warp_argmax(g);
-          if (g.aux >= 0) {
+          g = qr ? warp_max_key(g) : warp_argmax(g);
+          if (g.aux >= 0 && g.v != 0ull) {
             const uint32_t row = cl_map(&s_xrow[par * W], g.aux);
             for (int i = lane; i < w; i += 32) s_win[i] = cl_ld_f64(row + 8u * i);
-            if (lane < 2) s_gab[lane] = cl_ld_f64(cl_map(&s_xval[par * kXVal], g.aux) + 8u * (lane + 1));
+            if (qr) {
+              // the winner's reflector: wait (bounded) for its ready flag
+              int ready = 1;
+              if (lane == 0) {
+                const uint32_t fl = cl_map(&s_xkey[par], g.aux);
+                const unsigned limit = st->spin_limit ? st->spin_limit : kSpinLimit;
+                unsigned spins = 0;
+                while (cl_ld_acquire(fl) != nbar + 1) {
+                  if (++spins > limit) {
+                    if (atomicCAS(&st->status, 0, PRRP_ERR_TIMEOUT) == 0) st->timeout_site = site + 8;
+                    ready = 0;
+                    break;
+                  }
+                }
+                if (!ready) s_ok = 0;
+              }
+              __syncwarp();
+              if (lane < 2) s_gab[lane] = cl_ld_f64(cl_map(&s_xval[par * kXVal], g.aux) + 8u * (lane + 1));
+            }
           }
           if (lane == 0) s_gbest = g;
         }
@@ -305,22 +382,27 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
   };
 
   // Every warp: the tournament winner among the G proposals of parity `par`.
-  auto global_best = [&](int par) -> Cand {
+  auto global_best = [&](int par, bool qr) -> Cand {
     if constexpr (CL) {
       return s_gbest;
     } else {
       Cand g{0ull, 0x7fffffff, 0x7fffffff, -1};
       for (int q = lane; q < G; q += 32) {
         const size_t sq = (size_t)par * G + q;
-        const int2 k = __ldcg(&p.xkey[sq]);
-        Cand d{vbits(__ldcg(&p.xval[sq * kXVal])), k.x, k.y, q};
-        if (better(d, g)) g = d;
+        const unsigned long long v = vbits(__ldcg(&p.xval[sq * kXVal]));
+        if (qr) {
+          if (v > g.v) g = Cand{v, 0, 0, q};
+        } else {
+          const int2 k = __ldcg(&p.xkey[sq]);
+          Cand d{v, k.x, k.y, q};
+          if (better(d, g)) g = d;
+        }
       }
-      return warp_argmax(g);
+      return qr ? warp_max_key(g) : warp_argmax(g);
     }
   };
   // the winning record of parity `par`: row into vs, and (QRCP) alpha, beta
-  auto fetch_winner = [&](int par, int q, double* alpha, double* beta) {
+  auto fetch_winner = [&](int par, int q, double* alpha, double* beta) -> bool {
     if constexpr (CL) {
       for (int i = lane; i < w; i += 32) vs[i] = s_win[i];
       if (alpha) {
@@ -331,34 +413,47 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
       const size_t gs = (size_t)par * G + q;
       for (int i = lane; i < w; i += 32) vs[i] = __ldcg(&p.xvec[gs * kMaxW + i]);
       if (alpha) {
+        // the winner's reflector: wait (bounded) for its ready flag, every lane
+        const unsigned limit = st->spin_limit ? st->spin_limit : kSpinLimit;
+        unsigned spins = 0;
+        bool ready = true;
+        while (ld_acquire_u32(reinterpret_cast<const unsigned*>(&p.xkey[gs].x)) != nbar) {
+          if (dev_status(st) != 0 || ++spins > limit) {
+            if (atomicCAS(&st->status, 0, PRRP_ERR_TIMEOUT) == 0) st->timeout_site = 9;
+            ready = false;
+            break;
+          }
+          __nanosleep(16);
+        }
         *alpha = __ldcg(&p.xval[gs * kXVal + 1]);
         *beta = __ldcg(&p.xval[gs * kXVal + 2]);
+        return __all_sync(0xffffffffu, ready);
       }
     }
+    return true;
   };
 
   // ---------------- QR with column pivoting ----------------
   for (int t = 0; t < w; ++t) {
     const int par = t & 1;
-    Cand c{0ull, 0x7fffffff, 0, -1};
+    Cand c{0ull, 0, 0, -1};
     for (int r = wr0 + lane; r < wr1; r += 32) {
       const int pr = pos[r];
       if (pr >= t) {
-        long long b = __double_as_longlong(nrm[r]);
-        Cand d{static_cast<unsigned long long>(b < 0 ? 0 : b), pr, 0, r};
-        if (better(d, c)) c = d;
+        const unsigned long long k = qrcp_key(nrm[r], pr);
+        if (k > c.v) c = Cand{k, 0, 0, r};
       }
     }
     if (!publish_and_sync(c, par, 1, t)) goto done;
 
-    const Cand g = global_best(par);
-    if (g.v == 0ull) {            // the largest remaining norm is zero: rank < w
+    const Cand g = global_best(par, true);
+    if ((g.v >> kPosBits) == 0ull) {  // the largest remaining norm is zero: rank < w
       if (cta == 0 && tid == 0) set_error(st, PRRP_ERR_SINGULAR, p.col_offset + t + 1);
       goto done;
     }
-    const int pw = g.k1;
+    const int pw = key_pos(g.v);
     double alpha, beta;
-    fetch_winner(par, g.aux, &alpha, &beta);
+    if (!fetch_winner(par, g.aux, &alpha, &beta)) goto done;
     __syncwarp();
     const double x0 = vs[t];
     if (warp == 0) {
@@ -443,7 +538,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_rrqr_kernel(PanelParam
     }
     if (!publish_and_sync(c, par, 2, -1)) goto done;
 
-    const Cand g = global_best(par);
+    const Cand g = global_best(par, false);
     if (g.aux < 0 || !(vval(g.v) > p.tau)) break;   // also ends when there is no remaining row
     if (swaps >= p.max_swaps) {
       if (cta == 0 && tid == 0) set_error(st, PRRP_ERR_SWAP_LIMIT, p.col_offset + 1);
