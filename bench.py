@@ -33,6 +33,9 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 N_DEFAULT, B_DEFAULT, TAU = 8192, 64, 2.0
+# dram__bytes_read.sum + dram__bytes_write.sum of gemm_fp64_kernel<64, 64> on the first rest
+# update of this workload (one-pass ncu capture of the current kernel version)
+TRAFFIC_FIRST_UPDATE = 533746176 + 468264192
 METRIC = "LU_PRRP TFLOP/s and solves/s at FP64-level backward error; p50/p99 solve latency"
 WORKLOAD = "LU_PRRP plain FP64, n=8192, b=64, tau=2, A iid N(0,1), 1-RHS solve + FP64 refinement per step"
 
@@ -484,7 +487,9 @@ def run_ours(args) -> None:
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if achieved else None,
                          "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
-                         "traffic": None},
+                         "traffic": TRAFFIC_FIRST_UPDATE if (n, b) == (8192, 64) else None,
+                         "traffic_launch": "first rest update of the n=8192 factorization (M=8128, N=8064, "
+                                           "K=64; algorithmic 16*M*N = 1048707072 B), ncu dram bytes"},
             "kernel_share": {k: round(v["ms"] / total_kernel_ms, 4) for k, v in kstats.items()
                              if total_kernel_ms > 0},
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in kstats.items()},

@@ -345,22 +345,33 @@ cudaError_t launch_residual(const double* A, long long lda, int n, const double*
   return cudaGetLastError();
 }
 
-// out = max_j sum_i |a_ij| (the matrix 1-norm), one thread per column.
-__global__ void norm1_kernel(const double* __restrict__ A, long long lda, int n, double* out) {
-  double best = 0.0;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += abs_int(A[(long long)i * lda + j]);
-    best = fmax(best, s);
+// out = max_j sum_i |a_ij| (the matrix 1-norm).  One CTA per 32 columns: warp k sums rows
+// k, k + 8, ... of the 32 columns (one coalesced 256-byte row segment per load), the eight
+// partial sums are added in a fixed order, and the column maximum is combined by an atomic
+// max on the IEEE bits (order-independent), so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) norm1_kernel(const double* __restrict__ A, long long lda, int n,
+                                                    double* out) {
+  __shared__ double part[8][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (col < n)
+    for (int i = warp; i < n; i += 8) s += abs_int(A[(long long)i * lda + col]);
+  part[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double c = 0.0;
+    for (int k = 0; k < 8; ++k) c += part[k][lane];
+    unsigned long long b = abs_bits(c);
+    for (int off = 16; off > 0; off >>= 1) b = max_bits(b, __shfl_xor_sync(0xffffffffu, b, off));
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(out), b);
   }
-  for (int off = 16; off > 0; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
-  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(reinterpret_cast<unsigned long long*>(out), best);
 }
 
 cudaError_t launch_norm1(const double* A, long long lda, int n, double* out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
   if (e != cudaSuccess || n == 0) return e;
-  norm1_kernel<<<std::max(1, std::min((n + 127) / 128, 152 * 4)), 128, 0, s>>>(A, lda, n, out);
+  norm1_kernel<<<(n + 31) / 32, 256, 0, s>>>(A, lda, n, out);
   return cudaGetLastError();
 }
 
