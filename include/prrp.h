@@ -294,8 +294,9 @@ prrp_status prrp_ctx_set_timing(prrp_ctx* ctx, int enable);
  * contexts or streams may run at the same time; taller panels run as one cooperative grid
  * over the SMs, and cooperative panels of one device run one at a time.  For a single
  * factorization the grid is faster above 512 rows; several factorizations sharing the GPU
- * (the serve loop) gain from clusters.  cluster_max_rows in [0, 2048], 0 = the default
- * (512); INVALID_ARG otherwise. */
+ * (the serve loop) gain from clusters.  A cluster's CTAs hold m / 16 rows each above 512
+ * rows; a panel whose rows do not fit a CTA's shared memory runs as a grid instead.
+ * cluster_max_rows in [0, 4096], 0 = the default (512); INVALID_ARG otherwise. */
 prrp_status prrp_ctx_set_panel_mode(prrp_ctx* ctx, int cluster_max_rows);
 
 /* The launch timeline kept under timing level 2: for each timed launch, in the order the

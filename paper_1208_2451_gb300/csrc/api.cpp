@@ -1080,7 +1080,7 @@ prrp_status prrp_ctx_set_timing(prrp_ctx* ctx, int enable) {
 }
 
 prrp_status prrp_ctx_set_panel_mode(prrp_ctx* ctx, int cluster_max_rows) {
-  if (!ctx || cluster_max_rows < 0 || cluster_max_rows > 2048) return PRRP_ERR_INVALID_ARG;
+  if (!ctx || cluster_max_rows < 0 || cluster_max_rows > 4096) return PRRP_ERR_INVALID_ARG;
   ctx->panel_cluster_rows = cluster_max_rows;
   return PRRP_OK;
 }

@@ -659,12 +659,13 @@ size_t panel_smem_for(int w, int rpc) {
 
 // Panels of at most kClusterRows rows (or PanelParams::cluster_rows, at most
 // kClusterRowsMax) run as one thread-block cluster of up to 16 CTAs, 32 rows per CTA up to
-// 512 rows and m / 16 beyond; taller ones as a cooperative grid.  For a single
+// 512 rows and m / 16 beyond (while the CTA's rows fit in shared memory); taller ones as a
+// cooperative grid.  For a single
 // factorization the grid is faster once a cluster CTA would hold more than 32 rows (each
 // step's FP64 row updates then dominate it), but clusters do not serialize across streams,
 // which pays when several factorizations share the GPU.
 constexpr int kClusterRows = 512;
-constexpr int kClusterRowsMax = 2048;
+constexpr int kClusterRowsMax = 4096;
 
 cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t stream) {
   int dev = 0;

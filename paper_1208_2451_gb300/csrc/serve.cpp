@@ -216,7 +216,7 @@ void lane_main(prrp_server* S) {
   prrp_ctx* ctx = nullptr;
   if (prrp_create(&ctx, S->device) != PRRP_OK) { S->lane_errors++; return; }
   // lanes factor side by side: panels up to 2048 rows as co-scheduled clusters, which do
-  // not wait for the other lanes' panels
+  // not wait for the other lanes' panels (taller ones are faster as a grid)
   prrp_ctx_set_panel_mode(ctx, 2048);
   cudaStream_t s;
   cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
