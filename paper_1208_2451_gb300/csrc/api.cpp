@@ -109,7 +109,7 @@ struct prrp_ctx {
   size_t bws_cap = 0;
   unsigned char* bout = nullptr;
   size_t bout_cap = 0;
-  std::map<long long, int> batch_tuned;     // (fp64, b, size bucket) -> CTAs per SM
+  std::map<long long, int> batch_tuned;     // (fp64, b, size bucket) -> 4 * CTAs per SM + tile rows
   struct BatchGraph { cudaGraphExec_t exec = nullptr; std::vector<long long> sig; };
   BatchGraph bgraph;
   cudaStream_t capture_stream = nullptr;
@@ -847,7 +847,7 @@ int batch_max_ctas_per_sm(int nmax, int b) {
 
 // Enqueue one batched launch (counter reset + kernel) over metadata already on the device.
 prrp_status enqueue_batch(prrp_ctx* ctx, bool fp64, int count, int nmax, int b, int tmp_rows,
-                          int grid, const prrp_opts& o, const int* d_order, const int* d_n,
+                          int grid, int rb, const prrp_opts& o, const int* d_order, const int* d_n,
                           const double* const* d_A, const int* d_lda, const int* d_nrhs,
                           double* const* d_B, const int* d_ldb, int* const* d_perm, int* d_status, int* d_iters,
                           double* d_eta0, double* d_eta, unsigned* d_counter, cudaStream_t s) {
@@ -869,7 +869,7 @@ prrp_status enqueue_batch(prrp_ctx* ctx, bool fp64, int count, int nmax, int b, 
   (void)per;
   L.status = d_status; L.iters = d_iters; L.eta0 = d_eta0; L.eta = d_eta; L.counter = d_counter;
   CK(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s));
-  CK(launch_batch(fp64 ? 1 : 0, grid, L, s));
+  CK(launch_batch(fp64 ? 1 : 0, grid, rb, L, s));
   return PRRP_OK;
 }
 
@@ -913,7 +913,8 @@ prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const doubl
   if (maxper == 0) return PRRP_ERR_UNSUPPORTED;
   CK(prepare_batch(std::max(nmax, 128 * ((nmax + 127) / 128)), b));
 
-  // ---- autotune the CTAs per SM for this (precision, b, size bucket), once per context
+  // ---- autotune the launch shape for this (precision, b, size bucket), once per context:
+  // CTAs per SM (1 .. maxper) x the update's register tile (1 or 2 rows of L21 per warp pass)
   const int bucket = (nmax + 127) / 128;
   const long long tkey = ((long long)fp64 << 40) | ((long long)b << 20) | bucket;
   auto tuned = ctx->batch_tuned.find(tkey);
@@ -929,9 +930,11 @@ prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const doubl
     std::vector<const double*> ha(sample);
     std::vector<double*> hb(sample);
     for (int i = 0; i < sample; ++i) { ha[i] = tA + (size_t)i * ns * ns; hb[i] = tB + (size_t)i * ns; }
-    int best = 1;
+    int best = 4 * 1 + 1;
     float best_ms = 1e30f;
-    for (int per = 1; per <= maxper; ++per) {
+    const int nrb = fp64 ? 1 : 2;                         // FP64 keeps one row per pass
+    for (int cand = 0; cand < nrb * maxper && ps == PRRP_OK; ++cand) {
+      const int per = 1 + cand / nrb, rb = 1 + cand % nrb;
       const int grid = per * ctx->num_sms;
       ps = grow(ctx, &ctx->bws, &ctx->bws_cap, batch_ws_bytes(grid, ns, std::min(ns, 2 * (b + o.max_swaps) + 2), fp64));
       if (ps != PRRP_OK) break;
@@ -963,7 +966,7 @@ prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const doubl
       for (int rep = 0; rep < 2; ++rep) {                // first run warms up
         CK(launch_batch_fill(tA, ns, sample, tB, s));
         CK(cudaEventRecord(e0, s));
-        ps = enqueue_batch(ctx, fp64, sample, ns, b, std::min(ns, 2 * (b + o.max_swaps) + 2), grid, o, mi,
+        ps = enqueue_batch(ctx, fp64, sample, ns, b, std::min(ns, 2 * (b + o.max_swaps) + 2), grid, rb, o, mi,
                            mi + sample, pa, mi + 2 * sample, mi + 3 * sample, pb, mi + 4 * sample,
                            nullptr, d_status, d_iters, d_e0, d_e, d_counter, s);
         CK(cudaEventRecord(e1, s));
@@ -973,7 +976,7 @@ prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const doubl
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       if (ps != PRRP_OK) break;
-      if (ms < best_ms) { best_ms = ms; best = per; }
+      if (ms < best_ms) { best_ms = ms; best = 4 * per + rb; }
     }
     cudaFree(tA);
     cudaFree(tB);
@@ -981,7 +984,7 @@ prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const doubl
     ctx->batch_tuned[tkey] = best;
     tuned = ctx->batch_tuned.find(tkey);
   }
-  const int grid = tuned->second * ctx->num_sms;
+  const int grid = (tuned->second / 4) * ctx->num_sms, rb = tuned->second % 4;
 
   // ---- metadata: largest systems first, so the tail of the work list is short
   std::vector<int> ord(count);
@@ -1018,7 +1021,7 @@ prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const doubl
   long long tau_bits, tgt_bits;
   std::memcpy(&tau_bits, &o.tau, 8);
   std::memcpy(&tgt_bits, &o.refine_target, 8);
-  const std::vector<long long> sig = {count, nmax, grid, fp64, b, tmp_rows, tau_bits, o.max_swaps, dPerm != nullptr,
+  const std::vector<long long> sig = {count, nmax, grid, rb, fp64, b, tmp_rows, tau_bits, o.max_swaps, dPerm != nullptr,
                                       o.refine_max_iter, tgt_bits, (long long)(uintptr_t)ctx->bws,
                                       (long long)(uintptr_t)ctx->bmeta, (long long)(uintptr_t)ctx->bout};
   if (ctx->bgraph.sig != sig || !ctx->bgraph.exec) {
@@ -1026,7 +1029,7 @@ prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const doubl
     if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-    ps = enqueue_batch(ctx, fp64, count, nmax, b, tmp_rows, grid, o, mi, mi + count, pa, mi + 2 * count,
+    ps = enqueue_batch(ctx, fp64, count, nmax, b, tmp_rows, grid, rb, o, mi, mi + count, pa, mi + 2 * count,
                        mi + 3 * count, pb, mi + 4 * count, dPerm ? pp : nullptr, d_status, d_iters, d_e0,
                        d_e, d_counter, ctx->capture_stream);
     cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &g);

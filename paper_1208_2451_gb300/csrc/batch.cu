@@ -309,7 +309,10 @@ __device__ void batch_lu_solve(const T* W, int n, const int* perm, const double*
   }
 }
 
-template <typename T>
+// RB: the Schur update's register tile, RB rows of L21 per warp pass (each staged value of
+// A12 feeds RB FMAs); chosen per workload by the autotuner together with CTAs per SM (FP32
+// working copies only: two FP64 rows of up to 32 multipliers exceed the register budget).
+template <typename T, int RB>
 __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ BKey s_w[kBT / 32];
@@ -418,18 +421,29 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
       __syncthreads();
       {
         const int lane = tid & 31, warp = tid >> 5;
-        for (int i = warp; i < m - w; i += kBT / 32) {
-          T lr[kBW];
-          const T* l = W + (long long)(k0 + w + i) * n + k0;
+        const int rows = m - w;
+        for (int i0 = warp * RB; i0 < rows; i0 += (kBT / 32) * RB) {
+          T lr[RB][kBW];
 #pragma unroll
-          for (int k = 0; k < kBW; ++k) lr[k] = k < w ? l[k] : T(0);
-          T* crow = W + (long long)(k0 + w + i) * n + k0 + w;
+          for (int r = 0; r < RB; ++r) {
+            const T* l = W + (long long)(k0 + w + i0 + r) * n + k0;
+#pragma unroll
+            for (int k = 0; k < kBW; ++k) lr[r][k] = (k < w && i0 + r < rows) ? l[k] : T(0);
+          }
           for (int j = lane; j < nc; j += 32) {
-            T acc = 0;
+            T acc[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) acc[r] = 0;
 #pragma unroll
             for (int k = 0; k < kBW; ++k)
-              if (k < w) acc = fma(lr[k], Us[k * nc + j], acc);
-            crow[j] -= acc;
+              if (k < w) {
+                const T u = Us[k * nc + j];
+#pragma unroll
+                for (int r = 0; r < RB; ++r) acc[r] = fma(lr[r][k], u, acc[r]);
+              }
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+              if (i0 + r < rows) W[(long long)(k0 + w + i0 + r) * n + k0 + w + j] -= acc[r];
           }
         }
       }
@@ -615,20 +629,21 @@ size_t batch_smem_bytes(int nmax, int b) {
   return (size_t)nmax * (b + 1) * sizeof(double) + (size_t)nmax * (2 * sizeof(double) + sizeof(int)) + 64;
 }
 
-cudaError_t launch_batch(int fp64, int grid, const BatchLaunch& L, cudaStream_t s) {
+cudaError_t launch_batch(int fp64, int grid, int rb, const BatchLaunch& L, cudaStream_t s) {
   const size_t smem = batch_smem_bytes(L.nmax, L.b);
   if (fp64) {
     BatchArgs<double> a{L.count, L.order, L.n, L.A, L.lda, L.nrhs, L.B, L.ldb, L.perm_out, L.b, L.tau, L.max_swaps,
                         L.refine_max_iter, L.refine_target, L.nmax, static_cast<double*>(L.wsW),
                         static_cast<double*>(L.wsT), L.tmp_rows, L.wsV, L.wsI, L.status, L.iters,
                         L.eta0, L.eta, L.counter};
-    batch_kernel<double><<<grid, kBT, smem, s>>>(a);
+    batch_kernel<double, 1><<<grid, kBT, smem, s>>>(a);   // two FP64 rows of L21 do not fit in registers
   } else {
     BatchArgs<float> a{L.count, L.order, L.n, L.A, L.lda, L.nrhs, L.B, L.ldb, L.perm_out, L.b, L.tau, L.max_swaps,
                        L.refine_max_iter, L.refine_target, L.nmax, static_cast<float*>(L.wsW),
                        static_cast<float*>(L.wsT), L.tmp_rows, L.wsV, L.wsI, L.status, L.iters,
                        L.eta0, L.eta, L.counter};
-    batch_kernel<float><<<grid, kBT, smem, s>>>(a);
+    if (rb == 2) batch_kernel<float, 2><<<grid, kBT, smem, s>>>(a);
+    else batch_kernel<float, 1><<<grid, kBT, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -639,9 +654,10 @@ int batch_max_width() { return kBW; }
 cudaError_t prepare_batch(int nmax, int b) {
   (void)nmax;
   (void)b;
-  cudaError_t e = smem_optin(batch_kernel<double>);
-  if (e != cudaSuccess) return e;
-  return smem_optin(batch_kernel<float>);
+  cudaError_t e;
+  if ((e = smem_optin(batch_kernel<double, 1>)) != cudaSuccess) return e;
+  if ((e = smem_optin(batch_kernel<float, 1>)) != cudaSuccess) return e;
+  return smem_optin(batch_kernel<float, 2>);
 }
 
 // Synthetic systems for the autotuner: iid entries from a counter hash (Weyl sequence,

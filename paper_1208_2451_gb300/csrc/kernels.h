@@ -103,7 +103,9 @@ struct BatchLaunch {
 size_t batch_smem_bytes(int nmax, int b);
 int batch_max_width();
 cudaError_t prepare_batch(int nmax, int b);
-cudaError_t launch_batch(int fp64, int grid, const BatchLaunch& L, cudaStream_t s);
+// rb: rows of L21 per warp pass in the Schur update (1 or 2; FP64 always 1), picked by
+// the autotuner
+cudaError_t launch_batch(int fp64, int grid, int rb, const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_batch_fill(double* A, int n, int count, double* B, cudaStream_t s);
 
 // Solve kernels (solve.cu).
