@@ -128,6 +128,22 @@ def oracle_sample(n: int, b: int, panels: int, seed: int = 0):
     return dt, fl
 
 
+def reduce_max(vals, dist=None, device=None) -> list:
+    """The per-rank values' maximum over all ranks (NCCL tensors on the GPU, gloo on the
+    CPU); a single process returns its own values."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def replica_value(flops_per_step: float, steps: int, world: int, seconds: float) -> float:
+    """Whole-job TFLOP/s of independent replicas: every rank ran `steps` steps of
+    `flops_per_step`, and the job took as long as its slowest rank (`seconds`)."""
+    return flops_per_step * steps * world / seconds / 1e12
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -419,12 +435,9 @@ def run_ours(args) -> None:
     prrp.prrp_ctx_set_timing(ctx, False)
     step_ms = [a.elapsed_time(bb) for a, bb in evs]
     dev_s = sum(step_ms) / 1e3
-    t = torch.tensor([dev_s, wall], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_s, wall = float(t[0]), float(t[1])
+    dev_s, wall = reduce_max([dev_s, wall], dist, dev)
     flops_per = 2.0 * n ** 3 / 3.0
-    value = flops_per * args.steps * world / dev_s / 1e12
+    value = replica_value(flops_per, args.steps, world, dev_s)
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     hA = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
@@ -444,10 +457,7 @@ def run_ours(args) -> None:
     torch.cuda.synchronize(dev)
     barrier()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te[0])
+    (e2e_s,) = reduce_max([e2e_s], dist, dev)
 
     forms = {}
     if rank == 0 and world == 1 and not args.no_forms:
@@ -481,7 +491,7 @@ def run_ours(args) -> None:
             "solves_per_s": args.steps * world / dev_s,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "eta_last": eta,
-            "e2e": {"value": flops_per * e2e_steps * world / e2e_s / 1e12, "unit": "TFLOP/s",
+            "e2e": {"value": replica_value(flops_per, e2e_steps, world, e2e_s), "unit": "TFLOP/s",
                     "h2d_bytes_per_step": 8 * (n * n + n), "d2h_bytes_per_step": 8 * n},
             "roofline": {"bound": "alu", "kernel": "gemm_fp64 (Schur update A22 -= L21 A12)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -230,6 +230,31 @@ def test_cluster_panels_up_to_2048_rows(prrp, n, b, tau):
     assert np.array_equal(LU_c, LU_g)
 
 
+def test_launch_timeline_and_panel_mode(prrp):
+    """Timing level 2 keeps one (kind, start, end) interval per timed launch; the panel-mode
+    knob validates its range."""
+    c = prrp.prrp_create(0)
+    try:
+        A = pi.randn(300, 5)
+        prrp.prrp_ctx_set_timing(c, 2)
+        F = prrp.prrp_factor(c, torch.from_numpy(A).cuda(), b=64)
+        F.close()
+        tl = prrp.prrp_ctx_timeline(c)
+        kinds = {k for k, _, _ in tl}
+        assert {"scan", "panel", "permute", "update", "diag"} <= kinds
+        assert all(t1 >= t0 >= 0.0 for _, t0, t1 in tl)
+        assert sum(1 for k, _, _ in tl if k == "panel") == 5          # ceil(300 / 64) panels
+        prrp.prrp_ctx_set_timing(c, 0)
+        assert prrp.prrp_ctx_timeline(c) == []
+        with pytest.raises(prrp.PrrpError):
+            prrp.prrp_ctx_set_timing(c, 3)
+        with pytest.raises(prrp.PrrpError):
+            prrp.prrp_ctx_set_panel_mode(c, 5000)
+        prrp.prrp_ctx_set_panel_mode(c, 0)
+    finally:
+        c.close()
+
+
 def test_gesv_host(prrp, ctx):
     n = 700
     A = pi.randn(n, 8)
