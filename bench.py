@@ -291,29 +291,43 @@ def form_update(prrp, ctx, torch, dev, n=16384, k=64, reps=5):
     return {"workload": f"Schur update C -= L U, C {m}x{m} FP64, k={k}", "runs": out}
 
 
-def form_batched(prrp, ctx, torch, dev, count=4096, reps=3, plain_sample=256):
+def form_batched(prrp, ctx, torch, dev, count=4096, reps=3, plain_sample=256, dist=None):
     """Batched form: 4096 systems, n uniform in [32, 512], b = 16, one RHS, FP32 factor +
-    FP64 refinement, in one persistent launch."""
+    FP64 refinement, in one persistent launch.  Under torchrun the systems are split over
+    the ranks by a flop-balanced partition (each rank solves its own shard; only the timing
+    max and the system count cross ranks) and rank 0 reports the whole-job rate."""
     import prrp_inputs as pi
     sizes = pi.batch_sizes(count, 32, 512, 0)
     g = torch.Generator(device=dev)
     g.manual_seed(0)
     As = [torch.randn(int(k), int(k), dtype=torch.float64, device=dev, generator=g) for k in sizes]
     B0 = [torch.randn(int(k), 1, dtype=torch.float64, device=dev, generator=g) for k in sizes]
+    world = dist.get_world_size() if dist is not None and dist.is_initialized() else 1
+    rank = dist.get_rank() if world > 1 else 0
+    mine = prrp.partition_systems(sizes, world)[rank] if world > 1 else list(range(count))
+    As_m, B0_m = [As[i] for i in mine], [B0[i] for i in mine]
     res = {}
     for prec, name in ((3, "fp32_factor"), (0, "fp64_factor")):
         best = None
         for _ in range(reps):
-            Bs = [b.clone() for b in B0]
+            Bs = [b.clone() for b in B0_m]
             torch.cuda.synchronize(dev)
+            if world > 1:
+                dist.barrier()
             t0 = time.perf_counter()
-            st, info = prrp.prrp_batch_solve(ctx, As, Bs, b=16, prec=prec)
+            st, info = prrp.prrp_batch_solve(ctx, As_m, Bs, b=16, prec=prec)
             torch.cuda.synchronize(dev)
             dt = time.perf_counter() - t0
+            (dt,) = reduce_max([dt], dist, dev)
             best = dt if best is None else min(best, dt)
         res[name] = {"s": best, "solves_per_s": count / best,
                      "tflops": sum(2.0 * float(k) ** 3 / 3 for k in sizes) / best / 1e12,
-                     "max_eta": max(i["eta"] for i in info), "failed": sum(1 for x in st if x != 0)}
+                     "max_eta": max(reduce_max([max(i["eta"] for i in info)], dist, dev)),
+                     "failed": int(sum(reduce_max([sum(1 for x in st if x != 0)], dist, dev))),
+                     "ranks": world}
+    if world > 1:
+        return {"workload": f"{count} systems, n uniform in [32, 512], b=16, 1 RHS, "
+                            f"flop-balanced over {world} ranks", "runs": res}
     # plain FP64 path, one system after another, on a sample of the same systems
     pl = plain_fp64(prrp, ctx, torch, dev, As[:plain_sample], B0[:plain_sample], 16)
     pl["sample"] = f"first {plain_sample} of the {count} systems"
@@ -540,16 +554,33 @@ def main():
     elif args.form:
         import torch
         import paper_1208_2451_gb300 as prrp
-        ctx = prrp.prrp_create(0)
-        fn = {"mixed": lambda: form_mixed(prrp, ctx, torch, torch.device("cuda", 0),
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        dist = None
+        if world > 1:                     # only the batched form shards; the others run on rank 0
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        ctx = prrp.prrp_create(local)
+        if world > 1 and args.form != "batched":
+            if dist.get_rank() != 0:
+                ctx.close()
+                dist.destroy_process_group()
+                return
+        fn = {"mixed": lambda: form_mixed(prrp, ctx, torch, dev,
                                           n=args.n if args.n != N_DEFAULT else 16384,
                                           kappas=(0.0,) if args.randn else (1e2, 1e6)),
-              "batched": lambda: form_batched(prrp, ctx, torch, torch.device("cuda", 0)),
+              "batched": lambda: form_batched(prrp, ctx, torch, dev, dist=dist),
               "served": lambda: form_served(prrp, ctx),
-              "update": lambda: form_update(prrp, ctx, torch, torch.device("cuda", 0),
+              "update": lambda: form_update(prrp, ctx, torch, dev,
                                             n=args.n if args.n != N_DEFAULT else 16384)}[args.form]
-        print(json.dumps({"form": args.form, **fn()}), flush=True)
+        out = fn()
+        if dist is None or dist.get_rank() == 0:
+            print(json.dumps({"form": args.form, **out}), flush=True)
         ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
     else:
         run_ours(args)
 

@@ -19,7 +19,12 @@ EPS = 2.0 ** -53     # the unit roundoff the paper's HPL tests divide by
 
 
 def growth_bound(n: int, b: int, tau: float = 2.0) -> float:
-    return float((1.0 + tau * b) ** (n / b))
+    """(1 + tau b)^(n/b); inf when the value exceeds the double range (e.g. b = 8, n = 2048:
+    17^256), where every finite growth factor satisfies it."""
+    try:
+        return float((1.0 + tau * b) ** (n / b))
+    except OverflowError:
+        return float("inf")
 
 
 def bound_base(b: int, tau: float = 2.0) -> float:

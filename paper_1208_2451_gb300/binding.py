@@ -443,5 +443,23 @@ class Server:
             pass
 
 
+def partition_systems(sizes, parts: int) -> list:
+    """Split independent systems over `parts` GPUs for the batched and served forms: largest
+    first, each to the part with the least work so far (work = n^3, the factorization's
+    order), ties to the lower part.  Returns one list of system indices per part (each in
+    ascending order).  Host logic only; every part then runs prrp_batch_solve on its own
+    systems, with no collective on the data path."""
+    if parts < 1:
+        raise ValueError("parts must be >= 1")
+    order = sorted(range(len(sizes)), key=lambda i: (-int(sizes[i]), i))
+    load = [0.0] * parts
+    out = [[] for _ in range(parts)]
+    for i in order:
+        k = min(range(parts), key=lambda p: (load[p], p))
+        out[k].append(i)
+        load[k] += float(sizes[i]) ** 3
+    return [sorted(x) for x in out]
+
+
 def prrp_server_create(ctx: Context, hbm_budget_bytes: int, lanes: int = 4, **kw) -> Server:
     return Server(ctx, hbm_budget_bytes, lanes, **kw)

@@ -162,6 +162,25 @@ def test_foster_and_wright_2048(prrp, ctx):
     assert abs(st["growth"] - 1.0) <= 0.01
 
 
+@pytest.mark.parametrize("name", ["foster", "wright", "gen_wilkinson"])
+@pytest.mark.parametrize("b", [8, 32, 128])
+def test_pathological_suite_2048(prrp, ctx, name, b):
+    """Section 2.3 / Appendix F matrices at n = 2048 across panel widths: parity with the
+    oracle (pivots, residual, statistics) and the paper's tie-independent growth figures
+    (g_W = 2.66 for Foster, Table tab_foster, b from 8 to 128; 1 for Wright, Table
+    tab_wright); the generalized Wilkinson matrix (random branch, rank 1) stays under the
+    growth bound of Section 2.2."""
+    A = {"foster": lambda: pi.foster(2048), "wright": lambda: pi.wright(2048, 0.3),
+         "gen_wilkinson": lambda: pi.gen_wilkinson(2048, 1, 3)}[name]()
+    _, _, _, st = check_parity(prrp, ctx, A, b)
+    if name == "foster":
+        assert abs(st["growth"] - 2.66) <= 0.01
+    elif name == "wright":
+        assert abs(st["growth"] - 1.0) <= 0.01
+    else:
+        assert st["growth"] <= M.growth_bound(2048, b, 2.0)
+
+
 def test_full_size_n8192_b64(prrp, ctx):
     """The benchmark configuration (n = 8192, b = 64, tau = 2): whole factorization against
     the oracle, in the same launch configuration bench.py times."""

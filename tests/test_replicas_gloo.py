@@ -71,3 +71,55 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert r.returncode == 0
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_partition_systems_is_flop_balanced():
+    """Independent systems (batched and served forms) split over GPUs: every system in
+    exactly one part, and the largest part within one system's work of the average (the
+    largest-first greedy rule)."""
+    sys.path.insert(0, ROOT)
+    import prrp_inputs as pi
+    from paper_1208_2451_gb300 import binding as B
+    sizes = [int(k) for k in pi.batch_sizes(4096, 32, 512, 0)]
+    for parts in (1, 2, 3, 4, 8):
+        split = B.partition_systems(sizes, parts)
+        flat = sorted(i for p in split for i in p)
+        assert flat == list(range(len(sizes)))
+        loads = [sum(sizes[i] ** 3 for i in p) for p in split]
+        assert max(loads) <= sum(loads) / parts + max(s ** 3 for s in sizes)
+    assert B.partition_systems([5, 5, 5], 2) == [[0, 2], [1]]
+
+
+def _shard_worker(rank, world, port, sizes, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_1208_2451_gb300 import binding as B
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        mine = B.partition_systems(sizes, world)[rank]
+        everyone = [None] * world
+        dist.all_gather_object(everyone, mine)          # host-side gather of the shards
+        out.put((rank, everyone))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_batch_covers_every_system_once():
+    import torch.multiprocessing as mp
+    pytest.importorskip("paper_1208_2451_gb300.binding", reason="libprrp.so not built")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    sizes = [37, 512, 64, 300, 129, 480, 33, 256, 200, 511]
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, sizes, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for _, everyone in res:
+        flat = sorted(i for part in everyone for i in part)
+        assert flat == list(range(len(sizes)))
+        assert everyone == res[0][1]                    # every rank agrees on the split
