@@ -921,10 +921,15 @@ prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const doubl
   if (tuned == ctx->batch_tuned.end()) {
     const int ns = 128 * bucket > 1024 ? 1024 : 128 * bucket;
     const int sample = std::min(2 * ctx->num_sms, 256);
-    double* tA = nullptr;
-    double* tB = nullptr;
-    CK(cudaMalloc(&tA, sizeof(double) * (size_t)sample * ns * ns));
-    CK(cudaMalloc(&tB, sizeof(double) * (size_t)sample * ns));
+    // owners: every return below (CK included) frees the sample and the events
+    struct DevMem { void* p = nullptr; ~DevMem() { if (p) cudaFree(p); } } mA, mB;
+    struct Ev { cudaEvent_t e = nullptr; ~Ev() { if (e) cudaEventDestroy(e); } } e0, e1;
+    CK(cudaMalloc(&mA.p, sizeof(double) * (size_t)sample * ns * ns));
+    CK(cudaMalloc(&mB.p, sizeof(double) * (size_t)sample * ns));
+    CK(cudaEventCreate(&e0.e));
+    CK(cudaEventCreate(&e1.e));
+    double* tA = static_cast<double*>(mA.p);
+    double* tB = static_cast<double*>(mB.p);
     std::vector<int> hn(sample, ns), hl(sample, ns), hr(sample, 1), hord(sample);
     std::iota(hord.begin(), hord.end(), 0);
     std::vector<const double*> ha(sample);
@@ -959,27 +964,20 @@ prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const doubl
       double* d_e0 = reinterpret_cast<double*>(ctx->bout + align256(sizeof(int) * 2 * sample));
       double* d_e = d_e0 + sample;
       unsigned* d_counter = reinterpret_cast<unsigned*>(mi + 5 * sample);
-      cudaEvent_t e0, e1;
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
       float ms = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {                // first run warms up
+      for (int rep = 0; rep < 2 && ps == PRRP_OK; ++rep) {   // first run warms up
         CK(launch_batch_fill(tA, ns, sample, tB, s));
-        CK(cudaEventRecord(e0, s));
+        CK(cudaEventRecord(e0.e, s));
         ps = enqueue_batch(ctx, fp64, sample, ns, b, std::min(ns, 2 * (b + o.max_swaps) + 2), grid, rb, o, mi,
                            mi + sample, pa, mi + 2 * sample, mi + 3 * sample, pb, mi + 4 * sample,
                            nullptr, d_status, d_iters, d_e0, d_e, d_counter, s);
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
-        cudaEventElapsedTime(&ms, e0, e1);
+        CK(cudaEventRecord(e1.e, s));
+        CK(cudaEventSynchronize(e1.e));
+        CK(cudaEventElapsedTime(&ms, e0.e, e1.e));
       }
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
       if (ps != PRRP_OK) break;
       if (ms < best_ms) { best_ms = ms; best = 4 * per + rb; }
     }
-    cudaFree(tA);
-    cudaFree(tB);
     if (ps != PRRP_OK) return ps;
     ctx->batch_tuned[tkey] = best;
     tuned = ctx->batch_tuned.find(tkey);

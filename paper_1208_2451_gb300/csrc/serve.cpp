@@ -106,23 +106,25 @@ bool try_small_unit(prrp_server* S, prrp_ctx* ctx, cudaStream_t s, std::vector<I
   std::vector<const double*> dA(cnt);
   std::vector<double*> dB(cnt);
   bool ok = true;
+  cudaError_t copy = cudaSuccess;      // first failed copy of the unit (reported per request)
+  auto track = [&](cudaError_t e) { if (copy == cudaSuccess) copy = e; };
   for (int i = 0; i < cnt && ok; ++i) {
     const prrp_request& r = unit[i]->req;
     n[i] = r.n; lda[i] = r.n; nrhs[i] = r.nrhs; ldb[i] = std::max(r.nrhs, 1);
     double* a = static_cast<double*>(db.get(sizeof(double) * r.n * r.n));
     double* b = static_cast<double*>(db.get(sizeof(double) * r.n * std::max(r.nrhs, 1)));
     if (!a || !b) { ok = false; break; }
-    cudaMemcpy2DAsync(a, sizeof(double) * r.n, r.hA, sizeof(double) * r.lda, sizeof(double) * r.n, r.n,
-                      cudaMemcpyHostToDevice, s);
+    track(cudaMemcpy2DAsync(a, sizeof(double) * r.n, r.hA, sizeof(double) * r.lda, sizeof(double) * r.n, r.n,
+                            cudaMemcpyHostToDevice, s));
     if (r.nrhs > 0)
-      cudaMemcpy2DAsync(b, sizeof(double) * r.nrhs, r.hB, sizeof(double) * r.ldb, sizeof(double) * r.nrhs,
-                        r.n, cudaMemcpyHostToDevice, s);
+      track(cudaMemcpy2DAsync(b, sizeof(double) * r.nrhs, r.hB, sizeof(double) * r.ldb, sizeof(double) * r.nrhs,
+                              r.n, cudaMemcpyHostToDevice, s));
     dA[i] = a;
     dB[i] = b;
   }
   std::vector<prrp_status> st(cnt, PRRP_ERR_OOM);
   std::vector<prrp_solve_info> info(cnt);
-  if (ok) {
+  if (ok && copy == cudaSuccess) {
     prrp_opts o = S->opts;
     if (o.prec != PRRP_FP64) o.prec = PRRP_FP32;
     o.b = std::min(o.b, 16);
@@ -136,15 +138,15 @@ bool try_small_unit(prrp_server* S, prrp_ctx* ctx, cudaStream_t s, std::vector<I
     for (int i = 0; i < cnt && ok; ++i) {
       const prrp_request& r = unit[i]->req;
       if (st[i] == PRRP_OK && r.nrhs > 0)
-        cudaMemcpy2DAsync(r.hX, sizeof(double) * r.ldx, dB[i], sizeof(double) * r.nrhs, sizeof(double) * r.nrhs,
-                          r.n, cudaMemcpyDeviceToHost, s);
+        track(cudaMemcpy2DAsync(r.hX, sizeof(double) * r.ldx, dB[i], sizeof(double) * r.nrhs,
+                                sizeof(double) * r.nrhs, r.n, cudaMemcpyDeviceToHost, s));
     }
   }
   db.release();
-  cudaStreamSynchronize(s);
+  track(cudaStreamSynchronize(s));
   if (!ok) return false;
   for (int i = 0; i < cnt; ++i) {
-    unit[i]->res.status = st[i];
+    unit[i]->res.status = copy == cudaSuccess ? st[i] : PRRP_ERR_CUDA;
     unit[i]->res.eta = info[i].eta;
     unit[i]->res.iterations = info[i].iterations;
   }
@@ -171,31 +173,34 @@ bool try_big_item(prrp_server* S, prrp_ctx* ctx, cudaStream_t s, Item* it) {
   double* b = static_cast<double*>(db.get(sizeof(double) * r.n * std::max(r.nrhs, 1)));
   prrp_status st = PRRP_ERR_OOM;
   prrp_solve_info info{0, -1.0, -1.0};
+  cudaError_t copy = cudaSuccess;      // first failed copy (the request then fails with PRRP_ERR_CUDA)
+  auto track = [&](cudaError_t e) { if (copy == cudaSuccess) copy = e; };
   if (a && a0 && b) {
-    cudaMemcpy2DAsync(a0, sizeof(double) * r.n, r.hA, sizeof(double) * r.lda, sizeof(double) * r.n, r.n,
-                      cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(a, a0, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+    track(cudaMemcpy2DAsync(a0, sizeof(double) * r.n, r.hA, sizeof(double) * r.lda, sizeof(double) * r.n, r.n,
+                            cudaMemcpyHostToDevice, s));
+    track(cudaMemcpyAsync(a, a0, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
     if (r.nrhs > 0)
-      cudaMemcpy2DAsync(b, sizeof(double) * r.nrhs, r.hB, sizeof(double) * r.ldb, sizeof(double) * r.nrhs, r.n,
-                        cudaMemcpyHostToDevice, s);
+      track(cudaMemcpy2DAsync(b, sizeof(double) * r.nrhs, r.hB, sizeof(double) * r.ldb, sizeof(double) * r.nrhs,
+                              r.n, cudaMemcpyHostToDevice, s));
     prrp_opts o = S->opts;
     if (o.prec == PRRP_FP32) o.prec = PRRP_BF16X3;
     prrp_factors* F = nullptr;
-    st = prrp_factor(ctx, r.n, a, r.n, &o, s, &F);
+    st = copy == cudaSuccess ? prrp_factor(ctx, r.n, a, r.n, &o, s, &F) : PRRP_ERR_CUDA;
     if (st == PRRP_ERR_OOM || st == PRRP_ERR_CUDA)
       std::fprintf(stderr, "prrp_server: n=%d factor: %s (%s)\n", r.n, prrp_status_string(st),
                    prrp_ctx_last_error(ctx));
     if (st == PRRP_OK && r.nrhs > 0) {
       st = prrp_solve(ctx, F, a0, r.nrhs, b, r.nrhs, &o, s, &info);
       if (st == PRRP_OK || st == PRRP_ERR_NOT_CONVERGED)
-        cudaMemcpy2DAsync(r.hX, sizeof(double) * r.ldx, b, sizeof(double) * r.nrhs, sizeof(double) * r.nrhs, r.n,
-                          cudaMemcpyDeviceToHost, s);
+        track(cudaMemcpy2DAsync(r.hX, sizeof(double) * r.ldx, b, sizeof(double) * r.nrhs, sizeof(double) * r.nrhs,
+                                r.n, cudaMemcpyDeviceToHost, s));
     }
     prrp_factors_destroy(F);
   }
   db.release();
-  cudaStreamSynchronize(s);
+  track(cudaStreamSynchronize(s));
   if (st == PRRP_ERR_OOM) return false;
+  if (copy != cudaSuccess && st == PRRP_OK) st = PRRP_ERR_CUDA;
   it->res.status = st;
   it->res.eta = info.eta;
   it->res.iterations = info.iterations;
