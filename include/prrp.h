@@ -79,7 +79,7 @@ typedef struct {
 } prrp_factor_stats;
 
 typedef struct {
-  int iterations;  /* refinement corrections applied */
+  int iterations;  /* correction solves: classic refinement steps + preconditioned GMRES steps */
   double eta0;     /* normwise backward error (1-norm) of the first solution */
   double eta;      /* normwise backward error of the returned solution */
 } prrp_solve_info;
@@ -137,6 +137,11 @@ void prrp_factors_destroy(prrp_factors* F);
  * n x n, lda of the factorization) is not NULL, FP64 iterative refinement follows
  * (Section 3.3): r = B - A X in FP64, X += (LU)^-1 P r, until eta <= opts.refine_target,
  * eta stops halving, or opts.refine_max_iter corrections (opts may be NULL: defaults).
+ * Factors from a TF32 or BF16X3 Schur update are applied in FP32 for the corrections; when
+ * such a correction lowers eta by less than 10x (ill-conditioned A), refinement continues
+ * with GMRES on the system preconditioned by the factors ((LU)^-1 A d = (LU)^-1 r, FP64
+ * except the preconditioner), restarted every 30 steps, at most opts.refine_max_iter
+ * restart cycles.  NOT_CONVERGED when the limits are reached above the target.
  * info (may be NULL) receives eta of the first and final solutions (max over columns).
  */
 prrp_status prrp_solve(prrp_ctx* ctx, const prrp_factors* F, const double* dA_orig, int nrhs,
@@ -351,6 +356,15 @@ prrp_status prrp_panel_select_noalloc(int m, int w, const double* dP, int ldp, d
  * PRRP_ERR_TIMEOUT with the context still usable.  Any other return is a failure.
  */
 prrp_status prrp_selftest_wait(prrp_ctx* ctx, unsigned spin_limit, void* stream);
+
+/*
+ * prrp_selftest_chain_wait - the same check for the one-launch substitution of prrp_solve
+ * (no counterpart in the paper): one CTA holding the ticket of row block 1 of a two-block
+ * triangle waits for block 0, which no CTA solves.  The wait gives up after `spin_limit`
+ * polls (0 = the library default) and the call returns PRRP_ERR_TIMEOUT, with the
+ * context still usable.  Any other return is a failure.
+ */
+prrp_status prrp_selftest_chain_wait(prrp_ctx* ctx, unsigned spin_limit, void* stream);
 
 #ifdef __cplusplus
 }

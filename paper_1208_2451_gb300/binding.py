@@ -63,6 +63,7 @@ _SIGS = {
     "prrp_panel_select": (_I, [_P, _I, _I, _P, _I, _D, _I, _P, _P, C.POINTER(_I), _P]),
     "prrp_schur_update": (_I, [_P, _I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _P]),
     "prrp_selftest_wait": (_I, [_P, C.c_uint, _P]),
+    "prrp_selftest_chain_wait": (_I, [_P, C.c_uint, _P]),
     "prrp_panel_select_noalloc": (_I, [_I, _I, _P, _I, _D, _I, _P, _P, C.POINTER(_I), _P]),
     "prrp_ctx_set_timing": (_I, [_P, _I]),
     "prrp_ctx_kernel_stats": (_I, [_P, _P, _P, _P, _I]),
@@ -296,6 +297,12 @@ def prrp_schur_update(ctx: Context, L, U, Cm, prec=PRRP_FP64, stream=None) -> No
 def prrp_selftest_wait(ctx: Context, spin_limit: int = 20000, stream=None) -> int:
     """Run the bounded-wait self-test; returns the status (PRRP_ERR_TIMEOUT expected)."""
     return _lib.prrp_selftest_wait(ctx.handle, int(spin_limit), _stream_ptr(stream))
+
+
+def prrp_selftest_chain_wait(ctx: Context, spin_limit: int = 20000, stream=None) -> int:
+    """Run the substitution's bounded-wait self-test; returns the status (PRRP_ERR_TIMEOUT
+    expected)."""
+    return _lib.prrp_selftest_chain_wait(ctx.handle, int(spin_limit), _stream_ptr(stream))
 
 
 KINDS = ["scan", "panel", "permute", "update", "diag", "u12", "lfix", "solve", "batch"]

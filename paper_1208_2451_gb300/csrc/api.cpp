@@ -96,9 +96,15 @@ struct prrp_ctx {
   unsigned long long lu32_gen = 0;
   float* y32 = nullptr;
   size_t y32_cap = 0;
-  unsigned* tcount = nullptr;
+  unsigned* tcount = nullptr;       // substitution counters; word 0: a chain wait that ran out
   size_t tcount_cap = 0;
+  double* zbuf = nullptr;           // second n x nrhs buffer of the one-launch substitution
+  size_t zbuf_cap = 0;
   int panel_cluster_rows = 0;       // prrp_ctx_set_panel_mode (0: the library default)
+  double* krylov = nullptr;         // GMRES-based refinement: Krylov basis, coefficients
+  size_t krylov_cap = 0;
+  double* gm_coef = nullptr;
+  size_t gm_coef_cap = 0;
   unsigned* gemm_ctr = nullptr;     // tile counters of the FP64 updates (critical, rest stream)
   size_t gemm_ctr_cap = 0;
   unsigned long long factor_gen = 0;
@@ -373,7 +379,7 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
   void* ptrs[] = {ctx->st, ctx->xval, ctx->xkey, ctx->xvec, ctx->pairs, ctx->ipiv, ctx->order,
                   ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB, ctx->tcws,
                   ctx->l21b, ctx->a12, ctx->tcws2, ctx->dinv64, ctx->dinv32, ctx->lu32, ctx->y32,
-                  ctx->tcount, ctx->gemm_ctr};
+                  ctx->tcount, ctx->zbuf, ctx->gemm_ctr, ctx->krylov, ctx->gm_coef};
   for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
   if (ctx->s_rest) cudaStreamDestroy(ctx->s_rest);
   if (ctx->s_blk) cudaStreamDestroy(ctx->s_blk);
@@ -572,9 +578,14 @@ void prrp_factors_destroy(prrp_factors* F) {
 // on first use and kept in the context until another factorization is solved.
 static prrp_status prepare_solve(prrp_ctx* ctx, const prrp_factors* F, bool fp32, cudaStream_t s) {
   const int n = F->n, nb = (n + 63) / 64;
-  prrp_status ps = grow(ctx, &ctx->tcount, &ctx->tcount_cap, (size_t)nb);
-  if (ps != PRRP_OK) return ps;
   cudaError_t e;
+  const size_t words = trsv_counter_words(n);
+  if (ctx->tcount_cap < words) {
+    prrp_status ps = grow(ctx, &ctx->tcount, &ctx->tcount_cap, words);
+    if (ps != PRRP_OK) return ps;
+    CK(cudaMemsetAsync(ctx->tcount, 0, sizeof(unsigned) * words, s));
+  }
+  prrp_status ps;
   if (!fp32) {
     if (ctx->dinv64_gen == F->gen) return PRRP_OK;
     if ((ps = grow(ctx, &ctx->dinv64, &ctx->dinv64_cap, (size_t)2 * nb * 4096)) != PRRP_OK) return ps;
@@ -598,6 +609,20 @@ static prrp_status prepare_solve(prrp_ctx* ctx, const prrp_factors* F, bool fp32
   return PRRP_OK;
 }
 
+// Waits for the stream; a one-launch substitution whose wait ran out has left the wait's
+// site in counter word 0, which is reported (PRRP_ERR_TIMEOUT) and cleared.
+static prrp_status sync_solve(prrp_ctx* ctx, cudaStream_t s) {
+  unsigned site = 0;
+  if (ctx->tcount) CK(cudaMemcpyAsync(&site, ctx->tcount, sizeof site, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (site == 0) return PRRP_OK;
+  CK(cudaMemsetAsync(ctx->tcount, 0, sizeof site, s));
+  char buf[64];
+  std::snprintf(buf, sizeof buf, "substitution wait at site %u ran out", site);
+  ctx->last_error = buf;
+  return PRRP_ERR_TIMEOUT;
+}
+
 // Y = U^-1 L^-1 P B in FP64.
 static prrp_status solve_into(prrp_ctx* ctx, const prrp_factors* F, const double* B, long long ldb,
                               int nrhs, double* Y, cudaStream_t s) {
@@ -605,12 +630,23 @@ static prrp_status solve_into(prrp_ctx* ctx, const prrp_factors* F, const double
   prrp_status ps = prepare_solve(ctx, F, false, s);
   if (ps != PRRP_OK) return ps;
   const int nb = (F->n + 63) / 64;
+  const bool chain = nrhs <= kChainRhs;
+  if (chain && (ps = grow(ctx, &ctx->zbuf, &ctx->zbuf_cap, (size_t)F->n * nrhs)) != PRRP_OK) return ps;
   Timed t(ctx, s, PRRP_KIND_SOLVE, 2LL * F->n * F->n * nrhs);
-  ctx->kind_launches[PRRP_KIND_SOLVE] += 2LL * nb;   // gather + 2 nb substitution steps
+  ctx->kind_launches[PRRP_KIND_SOLVE] += chain ? 3 : 2LL * nb;   // gather + the substitution launches
   if ((e = launch_gather_rows(B, ldb, F->perm, F->n, nrhs, Y, s)) != cudaSuccess) return cuda_fail(ctx, e, "gather");
-  if ((e = launch_trsv(F->dA, F->lda, ctx->dinv64, F->n, Y, nrhs, 1, 0, ctx->tcount, s)) != cudaSuccess)
+  if (chain) {
+    if ((e = launch_trsv_chain(F->dA, F->lda, ctx->dinv64, F->n, Y, ctx->zbuf, nrhs, 1, 0, ctx->tcount, ctx->st,
+                               s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "trsv L");
+    if ((e = launch_trsv_chain(F->dA, F->lda, ctx->dinv64, F->n, ctx->zbuf, Y, nrhs, 0, 0, ctx->tcount, ctx->st,
+                               s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "trsv U");
+    return PRRP_OK;
+  }
+  if ((e = launch_trsv(F->dA, F->lda, ctx->dinv64, F->n, Y, nrhs, 1, 0, ctx->tcount + 1, s)) != cudaSuccess)
     return cuda_fail(ctx, e, "trsv L");
-  if ((e = launch_trsv(F->dA, F->lda, ctx->dinv64, F->n, Y, nrhs, 0, 0, ctx->tcount, s)) != cudaSuccess)
+  if ((e = launch_trsv(F->dA, F->lda, ctx->dinv64, F->n, Y, nrhs, 0, 0, ctx->tcount + 1, s)) != cudaSuccess)
     return cuda_fail(ctx, e, "trsv U");
   return PRRP_OK;
 }
@@ -623,13 +659,25 @@ static prrp_status solve_into32(prrp_ctx* ctx, const prrp_factors* F, const doub
   if (ps != PRRP_OK) return ps;
   if ((ps = grow(ctx, &ctx->y32, &ctx->y32_cap, (size_t)F->n * nrhs)) != PRRP_OK) return ps;
   const int nb = (F->n + 63) / 64;
+  const bool chain = nrhs <= kChainRhs;
+  if (chain && (ps = grow(ctx, &ctx->zbuf, &ctx->zbuf_cap, ((size_t)F->n * nrhs + 1) / 2)) != PRRP_OK) return ps;
+  float* z32 = reinterpret_cast<float*>(ctx->zbuf);
   Timed t(ctx, s, PRRP_KIND_SOLVE, 2LL * F->n * F->n * nrhs);
-  ctx->kind_launches[PRRP_KIND_SOLVE] += 2LL * nb;
+  ctx->kind_launches[PRRP_KIND_SOLVE] += chain ? 3 : 2LL * nb;
   if ((e = launch_gather_rows32(B, ldb, F->perm, F->n, nrhs, ctx->y32, s)) != cudaSuccess)
     return cuda_fail(ctx, e, "gather");
-  if ((e = launch_trsv(ctx->lu32, F->n, ctx->dinv32, F->n, ctx->y32, nrhs, 1, 1, ctx->tcount, s)) != cudaSuccess)
+  if (chain) {
+    if ((e = launch_trsv_chain(ctx->lu32, F->n, ctx->dinv32, F->n, ctx->y32, z32, nrhs, 1, 1, ctx->tcount, ctx->st,
+                               s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "trsv L");
+    if ((e = launch_trsv_chain(ctx->lu32, F->n, ctx->dinv32, F->n, z32, ctx->y32, nrhs, 0, 1, ctx->tcount, ctx->st,
+                               s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "trsv U");
+    return PRRP_OK;
+  }
+  if ((e = launch_trsv(ctx->lu32, F->n, ctx->dinv32, F->n, ctx->y32, nrhs, 1, 1, ctx->tcount + 1, s)) != cudaSuccess)
     return cuda_fail(ctx, e, "trsv L");
-  if ((e = launch_trsv(ctx->lu32, F->n, ctx->dinv32, F->n, ctx->y32, nrhs, 0, 1, ctx->tcount, s)) != cudaSuccess)
+  if ((e = launch_trsv(ctx->lu32, F->n, ctx->dinv32, F->n, ctx->y32, nrhs, 0, 1, ctx->tcount + 1, s)) != cudaSuccess)
     return cuda_fail(ctx, e, "trsv U");
   return PRRP_OK;
 }
@@ -673,9 +721,9 @@ prrp_status prrp_solve(prrp_ctx* ctx, const prrp_factors* F, const double* dA_or
     CK(launch_copy_rows(Y, nrhs, dB, ldb, n, nrhs, s));
   }
   if (!refine) {
-    CK(cudaStreamSynchronize(s));
+    ps = sync_solve(ctx, s);
     collect_timing(ctx);
-    return PRRP_OK;
+    return ps;
   }
   double* anorm = ctx->norms + 3 * nrhs;
   CK(launch_norm1(dA_orig, F->lda, n, anorm, s));
@@ -697,9 +745,150 @@ prrp_status prrp_solve(prrp_ctx* ctx, const prrp_factors* F, const double* dA_or
   double eta = 0.0;
   if ((ps = eta_now(&eta)) != PRRP_OK) return ps;
   if (info) info->eta0 = eta;
+
+  // One restart cycle of GMRES-based refinement (for low-precision factors whose classic
+  // refinement contracts slowly): the correction d of A d = r is found by GMRES on the
+  // preconditioned system (LU)^-1 A d = (LU)^-1 r, with the FP32 factors applied as the
+  // preconditioner and every other operation in FP64 (products with the original A,
+  // classical Gram-Schmidt done twice, Givens rotations of the Hessenberg matrix on the
+  // host), nrhs columns side by side.  Every cycle's correction is kept and eta updated: a
+  // cycle may raise eta a little and still leave the next ones a better start, so the caller
+  // tracks the best iterate in the block after the basis.
+  constexpr int m = 30;                     // Krylov vectors per cycle
+  constexpr size_t kBest = m + 1;           // block of the krylov buffer holding the best iterate
+  int inner = 0;                            // preconditioned GMRES steps (one FP32 solve each)
+  auto gmres_cycle = [&]() -> prrp_status {
+    constexpr double tol = 1e-10;           // relative decrease of the preconditioned residual
+    prrp_status q;
+    if ((q = grow(ctx, &ctx->gm_coef, &ctx->gm_coef_cap, (size_t)(m + 1) * nrhs)) != PRRP_OK) return q;
+    double* V = ctx->krylov;
+    double* W = Y;                          // free in the low-precision path
+    double* D = R;                          // R is consumed by the first preconditioner solve
+    double* coef = ctx->gm_coef;
+    std::vector<double> hv((size_t)(m + 1) * nrhs), h2((size_t)(m + 1) * nrhs), up((size_t)(m + 1) * nrhs);
+    auto dots = [&](int nvec, const double* X, double* host) -> prrp_status {
+      CK(launch_block_dots(V, nvec, n, nrhs, X, coef, s));
+      CK(cudaMemcpyAsync(host, coef, sizeof(double) * nvec * nrhs, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      return PRRP_OK;
+    };
+    auto precondition = [&](const double* X, double* out) -> prrp_status {   // out = (LU)^-1 X
+      prrp_status r = solve_into32(ctx, F, X, nrhs, nrhs, s);
+      if (r != PRRP_OK) return r;
+      CK(launch_scale_cols(nullptr, ctx->y32, n, nrhs, nullptr, out, s));
+      return PRRP_OK;
+    };
+    if ((q = precondition(R, V)) != PRRP_OK) return q;
+    std::vector<double> beta(nrhs);
+    if ((q = dots(1, V, hv.data())) != PRRP_OK) return q;
+    for (int c = 0; c < nrhs; ++c) {
+      beta[c] = std::sqrt(std::max(hv[c], 0.0));
+      up[c] = beta[c] > 0.0 ? 1.0 / beta[c] : 0.0;
+    }
+    CK(cudaMemcpyAsync(coef, up.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    CK(launch_scale_cols(V, nullptr, n, nrhs, coef, V, s));
+    // per column: Hessenberg H ((m + 1) x m, column-major), rotations, right-hand side g
+    std::vector<double> H((size_t)nrhs * (m + 1) * m, 0.0), cs((size_t)nrhs * m), sn((size_t)nrhs * m);
+    std::vector<double> g((size_t)nrhs * (m + 1), 0.0);
+    std::vector<int> kc(nrhs, 0);
+    std::vector<char> done(nrhs, 0);
+    for (int c = 0; c < nrhs; ++c) { g[(size_t)c * (m + 1)] = beta[c]; done[c] = beta[c] == 0.0; }
+    for (int j = 0; j < m; ++j) {
+      bool all = true;
+      for (int c = 0; c < nrhs; ++c) all = all && done[c];
+      if (all) break;
+      if ((q = [&]() -> prrp_status {
+             CK(launch_matvec(dA_orig, F->lda, n, V + (size_t)j * blk, nrhs, nrhs, D, s));
+             return PRRP_OK;
+           }()) != PRRP_OK) return q;
+      if ((q = precondition(D, W)) != PRRP_OK) return q;
+      ++inner;
+      // Gram-Schmidt against V_0 .. V_j, twice
+      if ((q = dots(j + 1, W, hv.data())) != PRRP_OK) return q;
+      CK(launch_block_axpy(V, j + 1, n, nrhs, coef, -1.0, W, s));
+      if ((q = dots(j + 1, W, h2.data())) != PRRP_OK) return q;
+      CK(launch_block_axpy(V, j + 1, n, nrhs, coef, -1.0, W, s));
+      CK(launch_block_dots(W, 1, n, nrhs, W, coef, s));
+      std::vector<double> hn(nrhs);
+      CK(cudaMemcpyAsync(hn.data(), coef, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int c = 0; c < nrhs; ++c) {
+        const double nrm = std::sqrt(std::max(hn[c], 0.0));
+        up[c] = 0.0;
+        if (done[c]) continue;
+        double* Hc = H.data() + (size_t)c * (m + 1) * m + (size_t)j * (m + 1);   // column j
+        for (int i = 0; i <= j; ++i) Hc[i] = hv[(size_t)i * nrhs + c] + h2[(size_t)i * nrhs + c];
+        Hc[j + 1] = nrm;
+        for (int i = 0; i < j; ++i) {                  // earlier rotations
+          const double a = Hc[i], bb = Hc[i + 1];
+          Hc[i] = cs[(size_t)c * m + i] * a + sn[(size_t)c * m + i] * bb;
+          Hc[i + 1] = -sn[(size_t)c * m + i] * a + cs[(size_t)c * m + i] * bb;
+        }
+        const double rr = std::hypot(Hc[j], Hc[j + 1]);
+        const double cj = rr > 0.0 ? Hc[j] / rr : 1.0, sj = rr > 0.0 ? Hc[j + 1] / rr : 0.0;
+        cs[(size_t)c * m + j] = cj;
+        sn[(size_t)c * m + j] = sj;
+        Hc[j] = rr;
+        Hc[j + 1] = 0.0;
+        double* gc = g.data() + (size_t)c * (m + 1);
+        gc[j + 1] = -sj * gc[j];
+        gc[j] = cj * gc[j];
+        kc[c] = j + 1;
+        if (std::fabs(gc[j + 1]) <= tol * beta[c] || nrm <= 1e-300) done[c] = 1;
+        else up[c] = 1.0 / nrm;
+      }
+      CK(cudaMemcpyAsync(coef, up.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+      CK(launch_scale_cols(W, nullptr, n, nrhs, coef, V + (size_t)(j + 1) * blk, s));
+    }
+    // y = H^-1 g per column (upper triangular after the rotations), D = sum_i y_i V_i
+    int kmax = 0;
+    std::fill(hv.begin(), hv.end(), 0.0);
+    for (int c = 0; c < nrhs; ++c) {
+      const double* Hcol = H.data() + (size_t)c * (m + 1) * m;
+      const double* gc = g.data() + (size_t)c * (m + 1);
+      for (int i = kc[c] - 1; i >= 0; --i) {
+        double acc = gc[i];
+        for (int l = i + 1; l < kc[c]; ++l) acc -= Hcol[(size_t)l * (m + 1) + i] * hv[(size_t)l * nrhs + c];
+        hv[(size_t)i * nrhs + c] = Hcol[(size_t)i * (m + 1) + i] != 0.0 ? acc / Hcol[(size_t)i * (m + 1) + i] : 0.0;
+      }
+      kmax = std::max(kmax, kc[c]);
+    }
+    CK(cudaMemcpyAsync(coef, hv.data(), sizeof(double) * std::max(kmax, 1) * nrhs, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(D, 0, sizeof(double) * blk, s));
+    CK(launch_block_axpy(V, kmax, n, nrhs, coef, 1.0, D, s));
+    CK(launch_axpy_rows(dB, ldb, D, 1.0, n, nrhs, s));
+    return eta_now(&eta);
+  };
+
   int it = 0;
   bool exhausted = false;
+  bool gm = false;
+  int cycles = 0;
+  int stalls = 0;                           // consecutive GMRES cycles without a new best eta
+  double best = 0.0;
+  auto keep_best = [&]() -> prrp_status {
+    CK(launch_copy_rows(dB, ldb, ctx->krylov + kBest * blk, nrhs, n, nrhs, s));
+    best = eta;
+    return PRRP_OK;
+  };
   while (eta > o.refine_target) {
+    if (gm) {
+      if (cycles == o.refine_max_iter) { exhausted = true; break; }
+      if (stalls == 2) break;
+      if (cycles == 0) {                     // one allocation for the basis and the best iterate
+        if ((ps = grow(ctx, &ctx->krylov, &ctx->krylov_cap, (kBest + 1) * blk)) != PRRP_OK) return ps;
+        if ((ps = keep_best()) != PRRP_OK) return ps;
+      }
+      if ((ps = gmres_cycle()) != PRRP_OK) return ps;
+      ++cycles;
+      if (eta < best) {
+        stalls = 0;
+        if ((ps = keep_best()) != PRRP_OK) return ps;
+      } else {
+        ++stalls;
+      }
+      continue;
+    }
     if (it == o.refine_max_iter) { exhausted = true; break; }
     if (low) {
       if ((ps = solve_into32(ctx, F, R, nrhs, nrhs, s)) != PRRP_OK) return ps;
@@ -711,6 +900,15 @@ prrp_status prrp_solve(prrp_ctx* ctx, const prrp_factors* F, const double* dA_or
     double e2 = 0.0;
     if ((ps = eta_now(&e2)) != PRRP_OK) return ps;
     ++it;
+    if (low && e2 > eta / 2) {       // slow contraction: continue with GMRES-based refinement
+      if (e2 > eta) {                // diverging: back to the previous iterate and its residual
+        CK(launch_axpy_rows32(dB, ldb, ctx->y32, -1.0, n, nrhs, s));
+        if ((ps = eta_now(&e2)) != PRRP_OK) return ps;
+      }
+      eta = e2;
+      gm = true;
+      continue;
+    }
     if (e2 > eta / 2) {              // stagnation: keep the better of the last two
       if (e2 > eta) {
         if (low) CK(launch_axpy_rows32(dB, ldb, ctx->y32, -1.0, n, nrhs, s));
@@ -721,9 +919,14 @@ prrp_status prrp_solve(prrp_ctx* ctx, const prrp_factors* F, const double* dA_or
     }
     eta = e2;
   }
-  CK(cudaStreamSynchronize(s));
+  if (cycles > 0 && eta > best) {           // end on the best GMRES iterate
+    CK(launch_copy_rows(ctx->krylov + kBest * blk, nrhs, dB, ldb, n, nrhs, s));
+    eta = best;
+    exhausted = exhausted && eta > o.refine_target;
+  }
+  if ((ps = sync_solve(ctx, s)) != PRRP_OK) return ps;
   collect_timing(ctx);
-  if (info) { info->iterations = it; info->eta = eta; }
+  if (info) { info->iterations = it + inner; info->eta = eta; }
   return exhausted ? PRRP_ERR_NOT_CONVERGED : PRRP_OK;
 }
 
@@ -1123,6 +1326,25 @@ prrp_status prrp_selftest_wait(prrp_ctx* ctx, unsigned spin_limit, void* stream)
   CK(cudaMemsetAsync(ctx->st, 0, sizeof(DevState), s));
   CK(cudaStreamSynchronize(s));
   return (prrp_status)h.status;
+}
+
+prrp_status prrp_selftest_chain_wait(prrp_ctx* ctx, unsigned spin_limit, void* stream) {
+  if (!ctx) return PRRP_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaSetDevice(ctx->device));
+  const size_t words = trsv_counter_words(128);
+  prrp_status ps;
+  if (ctx->tcount_cap < words) {
+    if ((ps = grow(ctx, &ctx->tcount, &ctx->tcount_cap, words)) != PRRP_OK) return ps;
+  }
+  if ((ps = grow(ctx, &ctx->zbuf, &ctx->zbuf_cap, (kChainSelftestFloats + 1) / 2)) != PRRP_OK) return ps;
+  CK(cudaMemsetAsync(ctx->st, 0, sizeof(DevState), s));
+  CK(cudaMemcpyAsync(&ctx->st->spin_limit, &spin_limit, sizeof(unsigned), cudaMemcpyHostToDevice, s));
+  CK(launch_trsv_chain_selftest(reinterpret_cast<float*>(ctx->zbuf), ctx->tcount, ctx->st, s));
+  ps = sync_solve(ctx, s);                  // reports and clears the recorded site
+  CK(cudaMemsetAsync(ctx->st, 0, sizeof(DevState), s));
+  CK(cudaStreamSynchronize(s));
+  return ps;
 }
 
 }  // extern "C"

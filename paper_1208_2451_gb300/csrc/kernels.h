@@ -119,11 +119,35 @@ cudaError_t launch_invert_diag(const double* LU, long long lda, int n, void* din
 // inverted diagonal blocks; Y is n x nrhs row-major (T); counters: nb unsigned scratch.
 cudaError_t launch_trsv(const void* LU, long long lda, const void* dinv, int n, void* Y, int nrhs, int lower,
                         int fp32, unsigned* counters, cudaStream_t s);
+// Out <- L^-1 In (lower) or U^-1 In in one launch, for 1 <= nrhs <= kChainRhs.  In is
+// overwritten (scratch); In and Out distinct, n x nrhs row-major (T).  counters: 3 + 2 nb
+// unsigned; word 0 must be 0 on entry and is left holding the site of a wait that ran
+// out (checked and cleared by the host), the rest is reset here.
+constexpr int kChainRhs = 16;
+// One CTA of the FP32 substitution holding the ticket of block 1 of a two-block system whose
+// block 0 nobody solves: its wait runs out.  scratch: kChainSelftestFloats floats.
+constexpr size_t kChainSelftestFloats = 128 * 128 + 2 * 2 * 4096 + 2 * 128;
+cudaError_t launch_trsv_chain_selftest(float* scratch, unsigned* counters, const DevState* st, cudaStream_t s);
+inline size_t trsv_counter_words(int n) { return 3 + 2 * (size_t)((n + 63) / 64); }
+cudaError_t launch_trsv_chain(const void* LU, long long lda, const void* dinv, int n, void* In, void* Out,
+                              int nrhs, int lower, int fp32, unsigned* counters, const DevState* st,
+                              cudaStream_t s);
 cudaError_t launch_convert_lu32(const double* LU, long long lda, int n, float* out, cudaStream_t s);
 cudaError_t launch_gather_rows32(const double* B, long long ldb, const int* perm, int n, int nrhs, float* Y,
                                  cudaStream_t s);
 cudaError_t launch_axpy_rows32(double* X, long long ldx, const float* D, double alpha, int n, int nrhs,
                                cudaStream_t s);
+// GMRES-based refinement (blocks of nrhs independent columns, n x nrhs row-major):
+// Y = A X; out[i][c] = <V_i(:,c), W(:,c)> for i < nvec; W += sign * sum_i coef[i][c] V_i;
+// Y = scale[c] * X (X FP64, or FP32 when x32 is given; scale may be null).
+cudaError_t launch_matvec(const double* A, long long lda, int n, const double* X, long long ldx, int nrhs,
+                          double* Y, cudaStream_t s);
+cudaError_t launch_block_dots(const double* V, int nvec, int n, int nrhs, const double* W, double* out,
+                              cudaStream_t s);
+cudaError_t launch_block_axpy(const double* V, int nvec, int n, int nrhs, const double* coef, double sign,
+                              double* W, cudaStream_t s);
+cudaError_t launch_scale_cols(const double* X, const float* x32, int n, int nrhs, const double* scale, double* Y,
+                              cudaStream_t s);
 cudaError_t launch_residual(const double* A, long long lda, int n, const double* X, long long ldx,
                             int nrhs, const double* B, long long ldb, double* R, double* norms,
                             cudaStream_t s);

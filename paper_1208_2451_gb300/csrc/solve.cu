@@ -205,6 +205,224 @@ static cudaError_t trsv_t(const T* LU, long long lda, const T* Dinv, int n, T* Y
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- one-launch substitution
+//
+// For up to kXS right-hand sides a whole triangle is solved by one launch instead of one
+// launch per row block.  CTAs take tickets in the order they start; ticket t owns chunk
+// t % per (RC rows) of row block t / per in solve order (top down for L, bottom up for U).
+// A chunk streams its rows' off-diagonal tiles M_bj and subtracts M_bj x_j as soon as
+// block j is final (a "front" counter: the number of blocks final so far, in order, so one
+// poll can clear many tiles), then the block's chunks share their part of y_b and each
+// computes its rows of x_b = Dinv_b y_b.  A CTA waits only on smaller tickets or on the
+// other chunks of its own block, and those started before any CTA of a later block took
+// its ticket, so the chain needs no co-residency guarantee beyond one block's chunks.
+//
+// Counter words: [0] site of a wait that ran out (0: none; cleared by the host), [1] ticket,
+// [2] front, [3, 3 + nb) chunks of each block that published y, [3 + nb, 3 + 2 nb) chunks
+// that wrote x.  Every wait is bounded (DevState::spin_limit polls, else kSpinLimit): when
+// one runs out, word 0 records its site and every CTA returns at its next wait.
+
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Polls *flag until it reaches target; false when the wait runs out or another CTA's did.
+__device__ __forceinline__ bool chain_wait(const unsigned* flag, unsigned target, unsigned* err,
+                                           unsigned limit, unsigned site, unsigned* seen) {
+  unsigned v, spins = 0;
+  while ((v = ld_acquire_u32(flag)) < target) {
+    if (*((volatile unsigned*)err) != 0) return false;
+    if (++spins > limit) {
+      atomicCAS(err, 0u, site);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  *seen = v;
+  return true;
+}
+
+// Sum over the KT consecutive lanes that share one row (butterfly: fixed order).
+template <int KT, typename T>
+__device__ __forceinline__ void row_sum(T (&v)[kXS], int nrhs) {
+#pragma unroll
+  for (int cc = 0; cc < kXS; ++cc) {
+    if (cc < nrhs) {
+#pragma unroll
+      for (int off = 1; off < KT; off <<= 1) v[cc] += __shfl_xor_sync(0xffffffffu, v[cc], off);
+    }
+  }
+}
+
+template <typename T, int RC>
+__global__ void __launch_bounds__(kSolveThreads) trsv_chain_kernel(const T* __restrict__ LU, long long lda,
+                                                                   const T* __restrict__ Dinv, int n, T* In,
+                                                                   T* Out, int nrhs, int lower, unsigned* c,
+                                                                   const DevState* __restrict__ st) {
+  constexpr int KT = kSolveThreads / RC;   // threads per row, consecutive lanes
+  constexpr int KS = kSB / KT;             // columns per thread, interleaved by KT
+  constexpr int per = kSB / RC;            // chunk CTAs per row block
+  static_assert(KT <= 32 && KT * RC == kSolveThreads && KS * KT == kSB, "chunk shape");
+  __shared__ T xs[kSB * kXP];
+  __shared__ unsigned s_t, s_front;
+  __shared__ int s_ok;
+  const int nb = (n + kSB - 1) / kSB;
+  unsigned* err = c;
+  unsigned* front = c + 2;
+  unsigned* ready = c + 3;
+  unsigned* done = c + 3 + nb;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_t = atomicAdd(c + 1, 1u);
+    s_front = 0;
+  }
+  __syncthreads();
+  const int t = (int)s_t;
+  const int p = t / per, ch = t - p * per;
+  const int b = lower ? p : nb - 1 - p;
+  const int r = tid / KT, q = tid - r * KT;
+  const int rb = ch * RC + r;              // row within the block
+  const int row = b * kSB + rb;
+  const bool live = row < n;
+  const unsigned limit = st->spin_limit ? st->spin_limit : kSpinLimit;
+  // this row of the block's inverse (zero past the matrix edge), read before any wait
+  const T* drow = Dinv + ((size_t)(lower ? 0 : 1) * nb + b) * kSB * kSB + (size_t)rb * kSB;
+  T dv[KS];
+#pragma unroll
+  for (int i = 0; i < KS; ++i) dv[i] = drow[q + KT * i];
+  T acc[kXS];
+#pragma unroll
+  for (int cc = 0; cc < kXS; ++cc)
+    acc[cc] = (q == 0 && live && cc < nrhs) ? In[(long long)row * nrhs + cc] : T(0);
+  const T* lrow = LU + (long long)(live ? row : 0) * lda;
+  for (int pj = 0; pj < p; ++pj) {
+    const int j = lower ? pj : nb - 1 - pj;
+    const int c0 = j * kSB;
+    T m[KS];                               // issued before the wait: in flight while polling
+#pragma unroll
+    for (int i = 0; i < KS; ++i) {
+      const int col = c0 + q + KT * i;
+      m[i] = (live && col < n) ? lrow[col] : T(0);
+    }
+    if (tid == 0) {
+      int ok = 1;
+      if (s_front <= (unsigned)pj) {
+        unsigned v = 0;
+        ok = chain_wait(front, (unsigned)pj + 1, err, limit, 1, &v);
+        if (ok) s_front = v;
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const int kc = min(kSB, n - c0);
+    for (int e = tid; e < kSB * nrhs; e += kSolveThreads) {
+      const int k = e / nrhs, cc = e - k * nrhs;
+      xs[k * kXP + cc] = k < kc ? __ldcg(Out + (long long)(c0 + k) * nrhs + cc) : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < KS; ++i) {
+      const T* xr = xs + (q + KT * i) * kXP;
+#pragma unroll
+      for (int cc = 0; cc < kXS; ++cc)
+        if (cc < nrhs) acc[cc] = fma(-m[i], xr[cc], acc[cc]);
+    }
+    __syncthreads();                       // xs is refilled next
+  }
+  row_sum<KT>(acc, nrhs);                  // y for this row, in every lane of the row
+  if (per > 1) {                           // share the chunks' parts of y_b through In
+    if (q == 0 && live) {
+#pragma unroll
+      for (int cc = 0; cc < kXS; ++cc)
+        if (cc < nrhs) In[(long long)row * nrhs + cc] = acc[cc];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(&ready[p], 1u);
+      unsigned v = 0;
+      s_ok = chain_wait(&ready[p], per, err, limit, 2, &v);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const int kb = min(kSB, n - b * kSB);
+    for (int e = tid; e < kSB * nrhs; e += kSolveThreads) {
+      const int k = e / nrhs, cc = e - k * nrhs;
+      xs[k * kXP + cc] = k < kb ? __ldcg(In + (long long)(b * kSB + k) * nrhs + cc) : T(0);
+    }
+  } else if (q == 0) {
+#pragma unroll
+    for (int cc = 0; cc < kXS; ++cc)
+      if (cc < nrhs) xs[rb * kXP + cc] = live ? acc[cc] : T(0);
+  }
+  __syncthreads();
+  T xo[kXS];
+#pragma unroll
+  for (int cc = 0; cc < kXS; ++cc) xo[cc] = T(0);
+#pragma unroll
+  for (int i = 0; i < KS; ++i) {
+    const T* yr = xs + (q + KT * i) * kXP;
+#pragma unroll
+    for (int cc = 0; cc < kXS; ++cc)
+      if (cc < nrhs) xo[cc] = fma(dv[i], yr[cc], xo[cc]);
+  }
+  row_sum<KT>(xo, nrhs);
+  if (q == 0 && live) {
+#pragma unroll
+    for (int cc = 0; cc < kXS; ++cc)
+      if (cc < nrhs) Out[(long long)row * nrhs + cc] = xo[cc];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&done[p], 1u) == (unsigned)(per - 1)) {
+      __threadfence();
+      st_release_gpu(front, (unsigned)p + 1);   // blocks finish in order: front only grows
+    }
+  }
+}
+
+template <typename T, int RC>
+static cudaError_t trsv_chain_t(const T* LU, long long lda, const T* Dinv, int n, T* In, T* Out, int nrhs,
+                                bool lower, unsigned* counters, const DevState* st, cudaStream_t s) {
+  const int nb = (n + kSB - 1) / kSB;
+  cudaError_t e = cudaMemsetAsync(counters + 1, 0, sizeof(unsigned) * (2 + 2 * (size_t)nb), s);
+  if (e != cudaSuccess) return e;
+  trsv_chain_kernel<T, RC><<<nb * (kSB / RC), kSolveThreads, 0, s>>>(LU, lda, Dinv, n, In, Out, nrhs,
+                                                                       lower ? 1 : 0, counters, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsv_chain_selftest(float* scratch, unsigned* counters, const DevState* st, cudaStream_t s) {
+  const int n = 128, nb = 2;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(float) * kChainSelftestFloats, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * (3 + 2 * nb), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters + 1, 1, 1, s);   // the next ticket is 1
+  if (e != cudaSuccess) return e;
+  float* LU = scratch;
+  float* dinv = LU + n * n;
+  float* in = dinv + 2 * nb * kSB * kSB;
+  trsv_chain_kernel<float, 64><<<1, kSolveThreads, 0, s>>>(LU, n, dinv, n, in, in + n, 1, 1, counters, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsv_chain(const void* LU, long long lda, const void* dinv, int n, void* In, void* Out,
+                              int nrhs, int lower, int fp32, unsigned* counters, const DevState* st,
+                              cudaStream_t s) {
+  if (nrhs < 1 || nrhs > kXS || In == Out) return cudaErrorInvalidValue;
+  if (n == 0) return cudaSuccess;
+  // FP32: one CTA per block (one hop per block on the chain); FP64: 8 CTAs per block, so
+  // that the two 64-wide products on the chain are spread over 8 SMs' FP64 pipes
+  if (fp32)
+    return trsv_chain_t<float, 64>(static_cast<const float*>(LU), lda, static_cast<const float*>(dinv), n,
+                                   static_cast<float*>(In), static_cast<float*>(Out), nrhs, lower != 0,
+                                   counters, st, s);
+  return trsv_chain_t<double, 8>(static_cast<const double*>(LU), lda, static_cast<const double*>(dinv), n,
+                                 static_cast<double*>(In), static_cast<double*>(Out), nrhs, lower != 0,
+                                 counters, st, s);
+}
+
 cudaError_t launch_invert_diag(const double* LU, long long lda, int n, void* dinv, int fp32, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const dim3 grid((n + kSB - 1) / kSB, 2);
@@ -302,7 +520,7 @@ __global__ void __launch_bounds__(kSolveThreads) residual_kernel(const double* _
       if (threadIdx.x == 0) {
         double ax = 0.0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) ax += part[q];
-        R[(long long)row * nrhs + c] = B[(long long)row * ldb + c] - ax;
+        R[(long long)row * nrhs + c] = B ? B[(long long)row * ldb + c] - ax : ax;   // no B: R = A X
       }
       __syncthreads();
     }
@@ -372,6 +590,100 @@ cudaError_t launch_norm1(const double* A, long long lda, int n, double* out, cud
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
   if (e != cudaSuccess || n == 0) return e;
   norm1_kernel<<<(n + 31) / 32, 256, 0, s>>>(A, lda, n, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- GMRES-based refinement
+// Krylov vectors are n x nrhs row-major blocks, nrhs independent columns side by side; the
+// reductions run in a fixed order, so the refinement's results do not depend on scheduling.
+
+// Y = A X (FP64), one CTA per row.
+cudaError_t launch_matvec(const double* A, long long lda, int n, const double* X, long long ldx, int nrhs,
+                          double* Y, cudaStream_t s) {
+  if (n == 0 || nrhs == 0) return cudaSuccess;
+  residual_kernel<<<std::min(n, 152 * 8), kSolveThreads, 0, s>>>(A, lda, n, X, ldx, nrhs, nullptr, 0, Y);
+  return cudaGetLastError();
+}
+
+// out[i * nrhs + c] = sum_r V_i[r][c] W[r][c] for i < nvec (V_i = V + i * n * nrhs): one CTA
+// per i, each thread a fixed stride of rows, then a fixed-order tree per column.
+constexpr int kMaxGmresRhs = 16;
+__global__ void __launch_bounds__(kSolveThreads) block_dots_kernel(const double* __restrict__ V, int nvec, int n,
+                                                                   int nrhs, const double* __restrict__ W,
+                                                                   double* __restrict__ out) {
+  __shared__ double red[kSolveThreads];
+  const int i = blockIdx.x;
+  if (i >= nvec) return;
+  const double* v = V + (size_t)i * n * nrhs;
+  for (int c0 = 0; c0 < nrhs; c0 += kMaxGmresRhs) {
+    const int nc = min(kMaxGmresRhs, nrhs - c0);
+    double acc[kMaxGmresRhs];
+#pragma unroll
+    for (int c = 0; c < kMaxGmresRhs; ++c) acc[c] = 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x)
+#pragma unroll
+      for (int c = 0; c < kMaxGmresRhs; ++c)
+        if (c < nc) acc[c] = fma(v[(size_t)r * nrhs + c0 + c], W[(size_t)r * nrhs + c0 + c], acc[c]);
+#pragma unroll
+    for (int c = 0; c < kMaxGmresRhs; ++c) {
+      if (c >= nc) break;                            // uniform across the CTA
+      __syncthreads();
+      red[threadIdx.x] = acc[c];
+      __syncthreads();
+      for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) out[(size_t)i * nrhs + c0 + c] = red[0];
+    }
+  }
+}
+
+cudaError_t launch_block_dots(const double* V, int nvec, int n, int nrhs, const double* W, double* out,
+                              cudaStream_t s) {
+  if (nvec == 0 || n == 0 || nrhs == 0) return cudaSuccess;
+  block_dots_kernel<<<nvec, kSolveThreads, 0, s>>>(V, nvec, n, nrhs, W, out);
+  return cudaGetLastError();
+}
+
+// W[r][c] += sign * sum_{i < nvec} coef[i * nrhs + c] V_i[r][c]   (i in ascending order)
+__global__ void block_axpy_kernel(const double* __restrict__ V, int nvec, int n, int nrhs,
+                                  const double* __restrict__ coef, double sign, double* __restrict__ W) {
+  const long long total = (long long)n * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % nrhs);
+    double acc = 0.0;
+    for (int i = 0; i < nvec; ++i) acc = fma(coef[(size_t)i * nrhs + c], V[(size_t)i * total + e], acc);
+    W[e] = fma(sign, acc, W[e]);
+  }
+}
+
+cudaError_t launch_block_axpy(const double* V, int nvec, int n, int nrhs, const double* coef, double sign,
+                              double* W, cudaStream_t s) {
+  const long long total = (long long)n * nrhs;
+  if (total == 0 || nvec == 0) return cudaSuccess;
+  block_axpy_kernel<<<(int)std::min<long long>((total + 255) / 256, 152 * 16), 256, 0, s>>>(V, nvec, n, nrhs, coef,
+                                                                                            sign, W);
+  return cudaGetLastError();
+}
+
+// Y[r][c] = scale[c] * X[r][c] with X in FP32 or FP64 (x32 != nullptr selects FP32).
+__global__ void scale_cols_kernel(const double* __restrict__ X, const float* __restrict__ x32, int n, int nrhs,
+                                  const double* __restrict__ scale, double* __restrict__ Y) {
+  const long long total = (long long)n * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double x = x32 ? static_cast<double>(x32[e]) : X[e];
+    Y[e] = scale ? scale[e % nrhs] * x : x;
+  }
+}
+
+cudaError_t launch_scale_cols(const double* X, const float* x32, int n, int nrhs, const double* scale, double* Y,
+                              cudaStream_t s) {
+  const long long total = (long long)n * nrhs;
+  if (total == 0) return cudaSuccess;
+  scale_cols_kernel<<<(int)std::min<long long>((total + 255) / 256, 152 * 16), 256, 0, s>>>(X, x32, n, nrhs, scale, Y);
   return cudaGetLastError();
 }
 

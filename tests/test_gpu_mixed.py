@@ -100,6 +100,34 @@ def _mixed_solve(prrp, ctx, A, B, prec, b):
     return LU, perm, st, dB.cpu().numpy(), info
 
 
+@pytest.mark.parametrize("prec,n,kappa", [(1, 2048, None), (1, 1500, 1e4), (2, 1500, 1e6), (2, 400, 1e8)])
+def test_gmres_refinement_reaches_fp64(prrp, ctx, prec, n, kappa):
+    """Where the factors' precision times the conditioning leaves classic refinement slow or
+    divergent (TF32 on larger random matrices and at kappa = 1e4, where kappa u_TF32 > 1;
+    3xBF16 up to kappa = 1e8 at n = 400), refinement continues with GMRES preconditioned by
+    the factors and still reaches FP64-level backward error."""
+    A = pi.randn(n, 31) if kappa is None else pi.conditioned(n, kappa, 31)
+    B = pi.rhs(n, 3, 31)
+    LU, perm, st, X, info = _mixed_solve(prrp, ctx, A, B, prec, 64)
+    assert info["eta"] <= 1e-15, info
+    for c in range(3):
+        assert M.eta(A, X[:, c], B[:, c]) <= 1e-15
+
+
+def test_gmres_refinement_beyond_reach_keeps_best(prrp, ctx):
+    """At kappa = 1e8 and n = 1500 the FP32-accurate factors are too weak a preconditioner
+    for restarted GMRES(30) (kappa u_FP32 is about 6): refinement stops after two cycles
+    without a new best and returns the best iterate it met, never one worse than the first
+    solve, with the reported eta that of the returned X."""
+    n = 1500
+    A = pi.conditioned(n, 1e8, 31)
+    B = pi.rhs(n, 3, 31)
+    LU, perm, st, X, info = _mixed_solve(prrp, ctx, A, B, 2, 64)
+    assert info["eta"] <= info["eta0"], info
+    worst = max(M.eta(A, X[:, c], B[:, c]) for c in range(3))
+    assert abs(worst - info["eta"]) <= 1e-3 * info["eta"], (worst, info)
+
+
 @pytest.mark.parametrize("prec,n,b,kappa", [(2, 256, 16, None), (2, 1024, 64, None), (2, 1000, 64, 1e6),
                                             (1, 1024, 64, 1e2), (1, 700, 32, 1e2)])
 def test_mixed_factor_and_refine(prrp, ctx, prec, n, b, kappa):

@@ -211,17 +211,24 @@ def test_solve_and_refine(prrp, ctx):
     assert info2["eta"] == -1.0
 
 
-@pytest.mark.parametrize("n,nrhs", [(1, 1), (63, 2), (64, 1), (65, 17), (200, 33), (700, 5), (1000, 16)])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (63, 2), (64, 1), (65, 17), (200, 33), (700, 5), (1000, 16),
+                                    (2100, 4)])
 def test_substitution_shapes(prrp, ctx, n, nrhs):
     """Row a8 without refinement: blocked forward/back substitution with inverted 64 x 64
     diagonal blocks agrees with the oracle's substitution on the oracle's factors, for
-    ragged block counts and right-hand-side counts that span several staging passes."""
+    ragged block counts and right-hand-side counts on both sides of the one-launch limit
+    (16) and across several staging passes.  The one-launch form takes its row blocks in
+    whatever order the CTAs start, yet its arithmetic order is fixed: a second solve gives
+    the same bits."""
     A = pi.randn(n, 40 + n)
     B = pi.rhs(n, nrhs, 40 + n)
     F = prrp.prrp_factor(ctx, torch.from_numpy(A).cuda(), b=64)
     dB = torch.from_numpy(B).cuda()
     prrp.prrp_solve(ctx, F, dB)
+    dB2 = torch.from_numpy(B).cuda()
+    prrp.prrp_solve(ctx, F, dB2)
     F.close()
+    assert torch.equal(dB, dB2)
     ref = oracle.lu_prrp(A, b=64)
     Xo = oracle.lu_solve(ref.LU, ref.perm, B)
     np.testing.assert_allclose(dB.cpu().numpy(), Xo, rtol=1e-9, atol=1e-10)
@@ -317,3 +324,19 @@ def test_bounded_wait_times_out(prrp, ctx):
     context then still factors correctly."""
     assert prrp.prrp_selftest_wait(ctx, 20000) == prrp.binding.PRRP_ERR_TIMEOUT
     check_parity(prrp, ctx, pi.randn(128, 9), 16)
+
+
+def test_substitution_wait_times_out(prrp, ctx):
+    """The one-launch substitution's wait for an earlier row block gives up when that block
+    never becomes final, reports PRRP_ERR_TIMEOUT through the host, and the next solve on
+    the context is correct."""
+    assert prrp.prrp_selftest_chain_wait(ctx, 20000) == prrp.binding.PRRP_ERR_TIMEOUT
+    n = 300
+    A = pi.randn(n, 44)
+    B = pi.rhs(n, 2, 44)
+    F = prrp.prrp_factor(ctx, torch.from_numpy(A).cuda(), b=32)
+    dB = torch.from_numpy(B).cuda()
+    prrp.prrp_solve(ctx, F, dB)
+    F.close()
+    ref = oracle.lu_prrp(A, b=32)
+    np.testing.assert_allclose(dB.cpu().numpy(), oracle.lu_solve(ref.LU, ref.perm, B), rtol=1e-9, atol=1e-10)
