@@ -120,15 +120,16 @@ cudaError_t launch_invert_diag(const double* LU, long long lda, int n, void* din
 cudaError_t launch_trsv(const void* LU, long long lda, const void* dinv, int n, void* Y, int nrhs, int lower,
                         int fp32, unsigned* counters, cudaStream_t s);
 // Out <- L^-1 In (lower) or U^-1 In in one launch, for 1 <= nrhs <= kChainRhs.  In is
-// overwritten (scratch); In and Out distinct, n x nrhs row-major (T).  counters: 3 + 2 nb
-// unsigned; word 0 must be 0 on entry and is left holding the site of a wait that ran
-// out (checked and cleared by the host), the rest is reset here.
+// overwritten (scratch); In and Out distinct, n x nrhs row-major (T).  counters:
+// trsv_counter_words(n) unsigned; word 0 must be 0 on entry and is left holding the site
+// of a wait that ran out (checked and cleared by the host), the rest is reset here.
 constexpr int kChainRhs = 16;
+constexpr int kTrsvCounterHead = 64;   // words before the per-block counters
+inline size_t trsv_counter_words(int n) { return kTrsvCounterHead + 2 * (size_t)((n + 63) / 64); }
 // One CTA of the FP32 substitution holding the ticket of block 1 of a two-block system whose
 // block 0 nobody solves: its wait runs out.  scratch: kChainSelftestFloats floats.
 constexpr size_t kChainSelftestFloats = 128 * 128 + 2 * 2 * 4096 + 2 * 128;
 cudaError_t launch_trsv_chain_selftest(float* scratch, unsigned* counters, const DevState* st, cudaStream_t s);
-inline size_t trsv_counter_words(int n) { return 3 + 2 * (size_t)((n + 63) / 64); }
 cudaError_t launch_trsv_chain(const void* LU, long long lda, const void* dinv, int n, void* In, void* Out,
                               int nrhs, int lower, int fp32, unsigned* counters, const DevState* st,
                               cudaStream_t s);

@@ -217,36 +217,58 @@ static cudaError_t trsv_t(const T* LU, long long lda, const T* Dinv, int n, T* Y
 // other chunks of its own block, and those started before any CTA of a later block took
 // its ticket, so the chain needs no co-residency guarantee beyond one block's chunks.
 //
+// Waiting is graded by urgency: a CTA whose own block is more than two blocks past the
+// front backs off in proportion to that distance, so that the few CTAs next in line are
+// the ones polling the front's cache line.  Every wait is bounded (DevState::spin_limit,
+// else kSpinLimit, in units of 32 ns of back-off); a wait that runs out records its site
+// in counter word 0 and every CTA returns at its next wait.
+//
 // Counter words: [0] site of a wait that ran out (0: none; cleared by the host), [1] ticket,
-// [2] front, [3, 3 + nb) chunks of each block that published y, [3 + nb, 3 + 2 nb) chunks
-// that wrote x.  Every wait is bounded (DevState::spin_limit polls, else kSpinLimit): when
-// one runs out, word 0 records its site and every CTA returns at its next wait.
+// [kFrontWord] front (a cache line of its own), [kReadyWord + p] chunks of block p that
+// published y, [kReadyWord + nb + p] chunks that wrote x.
+
+constexpr int kFrontWord = 32;
+constexpr int kReadyWord = 64;
+static_assert(kReadyWord == kTrsvCounterHead, "counter layout");
 
 __device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_acq_rel_add(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
 
-// Polls *flag until it reaches target; false when the wait runs out or another CTA's did.
-__device__ __forceinline__ bool chain_wait(const unsigned* flag, unsigned target, unsigned* err,
+// Polls *flag until it reaches target.  own >= 0: the caller's own block in solve order,
+// which grades the back-off by its distance from the observed value; own < 0: poll fast.
+// Returns false when the wait runs out or another CTA's did.
+__device__ __forceinline__ bool chain_wait(const unsigned* flag, unsigned target, int own, unsigned* err,
                                            unsigned limit, unsigned site, unsigned* seen) {
-  unsigned v, spins = 0;
+  unsigned v, spent = 0;
   while ((v = ld_acquire_u32(flag)) < target) {
     if (*((volatile unsigned*)err) != 0) return false;
-    if (++spins > limit) {
+    const int gap = own - (int)v;
+    const unsigned ns = (own >= 0 && gap > 2) ? min(256u * (unsigned)gap, 4096u) : 32u;
+    spent += ns >> 5;
+    if (spent > limit) {
       atomicCAS(err, 0u, site);
       return false;
     }
-    __nanosleep(32);
+    __nanosleep(ns);
   }
   *seen = v;
   return true;
 }
 
 // Sum over the KT consecutive lanes that share one row (butterfly: fixed order).
-template <int KT, typename T>
-__device__ __forceinline__ void row_sum(T (&v)[kXS], int nrhs) {
+template <int KT, int NC, typename T>
+__device__ __forceinline__ void row_sum(T (&v)[NC], int nrhs) {
 #pragma unroll
-  for (int cc = 0; cc < kXS; ++cc) {
+  for (int cc = 0; cc < NC; ++cc) {
     if (cc < nrhs) {
 #pragma unroll
       for (int off = 1; off < KT; off <<= 1) v[cc] += __shfl_xor_sync(0xffffffffu, v[cc], off);
@@ -254,7 +276,7 @@ __device__ __forceinline__ void row_sum(T (&v)[kXS], int nrhs) {
   }
 }
 
-template <typename T, int RC>
+template <typename T, int RC, int NC>
 __global__ void __launch_bounds__(kSolveThreads) trsv_chain_kernel(const T* __restrict__ LU, long long lda,
                                                                    const T* __restrict__ Dinv, int n, T* In,
                                                                    T* Out, int nrhs, int lower, unsigned* c,
@@ -262,15 +284,15 @@ __global__ void __launch_bounds__(kSolveThreads) trsv_chain_kernel(const T* __re
   constexpr int KT = kSolveThreads / RC;   // threads per row, consecutive lanes
   constexpr int KS = kSB / KT;             // columns per thread, interleaved by KT
   constexpr int per = kSB / RC;            // chunk CTAs per row block
-  static_assert(KT <= 32 && KT * RC == kSolveThreads && KS * KT == kSB, "chunk shape");
+  static_assert(KT <= 32 && KT * RC == kSolveThreads && KS * KT == kSB && NC <= kXS, "chunk shape");
   __shared__ T xs[kSB * kXP];
   __shared__ unsigned s_t, s_front;
   __shared__ int s_ok;
   const int nb = (n + kSB - 1) / kSB;
   unsigned* err = c;
-  unsigned* front = c + 2;
-  unsigned* ready = c + 3;
-  unsigned* done = c + 3 + nb;
+  unsigned* front = c + kFrontWord;
+  unsigned* ready = c + kReadyWord;
+  unsigned* done = ready + nb;
   const int tid = threadIdx.x;
   if (tid == 0) {
     s_t = atomicAdd(c + 1, 1u);
@@ -290,9 +312,9 @@ __global__ void __launch_bounds__(kSolveThreads) trsv_chain_kernel(const T* __re
   T dv[KS];
 #pragma unroll
   for (int i = 0; i < KS; ++i) dv[i] = drow[q + KT * i];
-  T acc[kXS];
+  T acc[NC];
 #pragma unroll
-  for (int cc = 0; cc < kXS; ++cc)
+  for (int cc = 0; cc < NC; ++cc)
     acc[cc] = (q == 0 && live && cc < nrhs) ? In[(long long)row * nrhs + cc] : T(0);
   const T* lrow = LU + (long long)(live ? row : 0) * lda;
   for (int pj = 0; pj < p; ++pj) {
@@ -308,7 +330,7 @@ __global__ void __launch_bounds__(kSolveThreads) trsv_chain_kernel(const T* __re
       int ok = 1;
       if (s_front <= (unsigned)pj) {
         unsigned v = 0;
-        ok = chain_wait(front, (unsigned)pj + 1, err, limit, 1, &v);
+        ok = chain_wait(front, (unsigned)pj + 1, p, err, limit, 1, &v);
         if (ok) s_front = v;
       }
       s_ok = ok;
@@ -325,7 +347,7 @@ __global__ void __launch_bounds__(kSolveThreads) trsv_chain_kernel(const T* __re
     for (int i = 0; i < KS; ++i) {
       const T* xr = xs + (q + KT * i) * kXP;
 #pragma unroll
-      for (int cc = 0; cc < kXS; ++cc)
+      for (int cc = 0; cc < NC; ++cc)
         if (cc < nrhs) acc[cc] = fma(-m[i], xr[cc], acc[cc]);
     }
     __syncthreads();                       // xs is refilled next
@@ -334,15 +356,14 @@ __global__ void __launch_bounds__(kSolveThreads) trsv_chain_kernel(const T* __re
   if (per > 1) {                           // share the chunks' parts of y_b through In
     if (q == 0 && live) {
 #pragma unroll
-      for (int cc = 0; cc < kXS; ++cc)
+      for (int cc = 0; cc < NC; ++cc)
         if (cc < nrhs) In[(long long)row * nrhs + cc] = acc[cc];
     }
     __syncthreads();
     if (tid == 0) {
-      __threadfence();
-      atomicAdd(&ready[p], 1u);
+      red_release_add(&ready[p], 1u);
       unsigned v = 0;
-      s_ok = chain_wait(&ready[p], per, err, limit, 2, &v);
+      s_ok = chain_wait(&ready[p], per, -1, err, limit, 2, &v);
     }
     __syncthreads();
     if (!s_ok) return;
@@ -353,57 +374,71 @@ __global__ void __launch_bounds__(kSolveThreads) trsv_chain_kernel(const T* __re
     }
   } else if (q == 0) {
 #pragma unroll
-    for (int cc = 0; cc < kXS; ++cc)
+    for (int cc = 0; cc < NC; ++cc)
       if (cc < nrhs) xs[rb * kXP + cc] = live ? acc[cc] : T(0);
   }
   __syncthreads();
-  T xo[kXS];
+  T xo[NC];
 #pragma unroll
-  for (int cc = 0; cc < kXS; ++cc) xo[cc] = T(0);
+  for (int cc = 0; cc < NC; ++cc) xo[cc] = T(0);
 #pragma unroll
   for (int i = 0; i < KS; ++i) {
     const T* yr = xs + (q + KT * i) * kXP;
 #pragma unroll
-    for (int cc = 0; cc < kXS; ++cc)
+    for (int cc = 0; cc < NC; ++cc)
       if (cc < nrhs) xo[cc] = fma(dv[i], yr[cc], xo[cc]);
   }
   row_sum<KT>(xo, nrhs);
   if (q == 0 && live) {
 #pragma unroll
-    for (int cc = 0; cc < kXS; ++cc)
+    for (int cc = 0; cc < NC; ++cc)
       if (cc < nrhs) Out[(long long)row * nrhs + cc] = xo[cc];
   }
   __syncthreads();
+  // x_b's rows are written; the release orders them (cumulatively, through the barrier)
+  // before the front moves.  Blocks finish in order, so the front only grows.
   if (tid == 0) {
-    __threadfence();
-    if (atomicAdd(&done[p], 1u) == (unsigned)(per - 1)) {
-      __threadfence();
-      st_release_gpu(front, (unsigned)p + 1);   // blocks finish in order: front only grows
+    if (per == 1) {
+      st_release_gpu(front, (unsigned)p + 1);
+    } else if (atom_acq_rel_add(&done[p], 1u) == (unsigned)(per - 1)) {
+      st_release_gpu(front, (unsigned)p + 1);
     }
   }
 }
 
-template <typename T, int RC>
+template <typename T, int RC, int NC>
 static cudaError_t trsv_chain_t(const T* LU, long long lda, const T* Dinv, int n, T* In, T* Out, int nrhs,
                                 bool lower, unsigned* counters, const DevState* st, cudaStream_t s) {
   const int nb = (n + kSB - 1) / kSB;
-  cudaError_t e = cudaMemsetAsync(counters + 1, 0, sizeof(unsigned) * (2 + 2 * (size_t)nb), s);
+  cudaError_t e = cudaMemsetAsync(counters + 1, 0, sizeof(unsigned) * (trsv_counter_words(n) - 1), s);
   if (e != cudaSuccess) return e;
-  trsv_chain_kernel<T, RC><<<nb * (kSB / RC), kSolveThreads, 0, s>>>(LU, lda, Dinv, n, In, Out, nrhs,
-                                                                       lower ? 1 : 0, counters, st);
+  trsv_chain_kernel<T, RC, NC><<<nb * (kSB / RC), kSolveThreads, 0, s>>>(LU, lda, Dinv, n, In, Out, nrhs,
+                                                                           lower ? 1 : 0, counters, st);
   return cudaGetLastError();
+}
+
+template <typename T, int RC>
+static cudaError_t trsv_chain_nc(const void* LU, long long lda, const void* dinv, int n, void* In, void* Out,
+                                 int nrhs, int lower, unsigned* counters, const DevState* st, cudaStream_t s) {
+  const T* L = static_cast<const T*>(LU);
+  const T* D = static_cast<const T*>(dinv);
+  T* I = static_cast<T*>(In);
+  T* O = static_cast<T*>(Out);
+  if (nrhs == 1) return trsv_chain_t<T, RC, 1>(L, lda, D, n, I, O, nrhs, lower != 0, counters, st, s);
+  if (nrhs <= 4) return trsv_chain_t<T, RC, 4>(L, lda, D, n, I, O, nrhs, lower != 0, counters, st, s);
+  return trsv_chain_t<T, RC, kXS>(L, lda, D, n, I, O, nrhs, lower != 0, counters, st, s);
 }
 
 cudaError_t launch_trsv_chain_selftest(float* scratch, unsigned* counters, const DevState* st, cudaStream_t s) {
   const int n = 128, nb = 2;
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(float) * kChainSelftestFloats, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * (3 + 2 * nb), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * trsv_counter_words(n), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(counters + 1, 1, 1, s);   // the next ticket is 1
   if (e != cudaSuccess) return e;
   float* LU = scratch;
   float* dinv = LU + n * n;
   float* in = dinv + 2 * nb * kSB * kSB;
-  trsv_chain_kernel<float, 64><<<1, kSolveThreads, 0, s>>>(LU, n, dinv, n, in, in + n, 1, 1, counters, st);
+  trsv_chain_kernel<float, 64, 1><<<1, kSolveThreads, 0, s>>>(LU, n, dinv, n, in, in + n, 1, 1, counters, st);
   return cudaGetLastError();
 }
 
@@ -412,15 +447,10 @@ cudaError_t launch_trsv_chain(const void* LU, long long lda, const void* dinv, i
                               cudaStream_t s) {
   if (nrhs < 1 || nrhs > kXS || In == Out) return cudaErrorInvalidValue;
   if (n == 0) return cudaSuccess;
-  // FP32: one CTA per block (one hop per block on the chain); FP64: 8 CTAs per block, so
-  // that the two 64-wide products on the chain are spread over 8 SMs' FP64 pipes
-  if (fp32)
-    return trsv_chain_t<float, 64>(static_cast<const float*>(LU), lda, static_cast<const float*>(dinv), n,
-                                   static_cast<float*>(In), static_cast<float*>(Out), nrhs, lower != 0,
-                                   counters, st, s);
-  return trsv_chain_t<double, 8>(static_cast<const double*>(LU), lda, static_cast<const double*>(dinv), n,
-                                 static_cast<double*>(In), static_cast<double*>(Out), nrhs, lower != 0,
-                                 counters, st, s);
+  // FP32: one CTA per block (one hop per block on the chain); FP64: 4 CTAs per block, so
+  // that the two 64-wide products on the chain are spread over 4 SMs' FP64 pipes
+  if (fp32) return trsv_chain_nc<float, 64>(LU, lda, dinv, n, In, Out, nrhs, lower, counters, st, s);
+  return trsv_chain_nc<double, 16>(LU, lda, dinv, n, In, Out, nrhs, lower, counters, st, s);
 }
 
 cudaError_t launch_invert_diag(const double* LU, long long lda, int n, void* dinv, int fp32, cudaStream_t s) {
