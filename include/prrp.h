@@ -304,6 +304,14 @@ prrp_status prrp_ctx_set_timing(prrp_ctx* ctx, int enable);
  * cluster_max_rows in [0, 4096], 0 = the default (512); INVALID_ARG otherwise. */
 prrp_status prrp_ctx_set_panel_mode(prrp_ctx* ctx, int cluster_max_rows);
 
+/* Substitution form of prrp_solve for this context (a tuning knob).  mode 0 (the default):
+ * a triangle with at most 16 right-hand sides is solved by one launch whose CTAs wait for
+ * one another's row blocks, the lowest latency for one solve on an otherwise idle GPU;
+ * mode 1: one launch per 64-row block, which holds no SM while it waits, for contexts that
+ * share the GPU with other work.  The two differ only in the order of rounding.
+ * INVALID_ARG for other modes. */
+prrp_status prrp_ctx_set_solve_mode(prrp_ctx* ctx, int mode);
+
 /* The launch timeline kept under timing level 2: for each timed launch, in the order the
  * calls collected them, its kernel class (PRRP_KIND_*) and its start and end in ms after
  * the base event.  Launches on different streams overlap when they ran concurrently.

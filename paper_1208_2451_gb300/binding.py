@@ -64,6 +64,7 @@ _SIGS = {
     "prrp_schur_update": (_I, [_P, _I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _P]),
     "prrp_selftest_wait": (_I, [_P, C.c_uint, _P]),
     "prrp_selftest_chain_wait": (_I, [_P, C.c_uint, _P]),
+    "prrp_ctx_set_solve_mode": (_I, [_P, C.c_int]),
     "prrp_panel_select_noalloc": (_I, [_I, _I, _P, _I, _D, _I, _P, _P, C.POINTER(_I), _P]),
     "prrp_ctx_set_timing": (_I, [_P, _I]),
     "prrp_ctx_kernel_stats": (_I, [_P, _P, _P, _P, _I]),
@@ -316,6 +317,12 @@ def prrp_ctx_set_timing(ctx: Context, enable=True) -> None:
 def prrp_ctx_set_panel_mode(ctx: Context, cluster_max_rows: int = 0) -> None:
     """Panels of at most cluster_max_rows rows run as one thread-block cluster (0: default)."""
     _check(_lib.prrp_ctx_set_panel_mode(ctx.handle, int(cluster_max_rows)), "prrp_ctx_set_panel_mode")
+
+
+def prrp_ctx_set_solve_mode(ctx: Context, mode: int) -> None:
+    """0: one launch per triangle for up to 16 right-hand sides (default); 1: one launch per
+    64-row block (holds no SM while waiting; for contexts sharing the GPU)."""
+    _check(_lib.prrp_ctx_set_solve_mode(ctx.handle, int(mode)), "prrp_ctx_set_solve_mode", ctx.handle)
 
 
 def prrp_ctx_timeline(ctx: Context) -> list:

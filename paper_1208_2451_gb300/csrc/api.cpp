@@ -101,6 +101,7 @@ struct prrp_ctx {
   double* zbuf = nullptr;           // second n x nrhs buffer of the one-launch substitution
   size_t zbuf_cap = 0;
   int panel_cluster_rows = 0;       // prrp_ctx_set_panel_mode (0: the library default)
+  int solve_mode = 0;               // prrp_ctx_set_solve_mode
   double* krylov = nullptr;         // GMRES-based refinement: Krylov basis, coefficients
   size_t krylov_cap = 0;
   double* gm_coef = nullptr;
@@ -630,7 +631,7 @@ static prrp_status solve_into(prrp_ctx* ctx, const prrp_factors* F, const double
   prrp_status ps = prepare_solve(ctx, F, false, s);
   if (ps != PRRP_OK) return ps;
   const int nb = (F->n + 63) / 64;
-  const bool chain = nrhs <= kChainRhs;
+  const bool chain = nrhs <= kChainRhs && ctx->solve_mode == 0;
   if (chain && (ps = grow(ctx, &ctx->zbuf, &ctx->zbuf_cap, (size_t)F->n * nrhs)) != PRRP_OK) return ps;
   Timed t(ctx, s, PRRP_KIND_SOLVE, 2LL * F->n * F->n * nrhs);
   ctx->kind_launches[PRRP_KIND_SOLVE] += chain ? 3 : 2LL * nb;   // gather + the substitution launches
@@ -659,7 +660,7 @@ static prrp_status solve_into32(prrp_ctx* ctx, const prrp_factors* F, const doub
   if (ps != PRRP_OK) return ps;
   if ((ps = grow(ctx, &ctx->y32, &ctx->y32_cap, (size_t)F->n * nrhs)) != PRRP_OK) return ps;
   const int nb = (F->n + 63) / 64;
-  const bool chain = nrhs <= kChainRhs;
+  const bool chain = nrhs <= kChainRhs && ctx->solve_mode == 0;
   if (chain && (ps = grow(ctx, &ctx->zbuf, &ctx->zbuf_cap, ((size_t)F->n * nrhs + 1) / 2)) != PRRP_OK) return ps;
   float* z32 = reinterpret_cast<float*>(ctx->zbuf);
   Timed t(ctx, s, PRRP_KIND_SOLVE, 2LL * F->n * F->n * nrhs);
@@ -1286,6 +1287,12 @@ prrp_status prrp_ctx_set_timing(prrp_ctx* ctx, int enable) {
 prrp_status prrp_ctx_set_panel_mode(prrp_ctx* ctx, int cluster_max_rows) {
   if (!ctx || cluster_max_rows < 0 || cluster_max_rows > 4096) return PRRP_ERR_INVALID_ARG;
   ctx->panel_cluster_rows = cluster_max_rows;
+  return PRRP_OK;
+}
+
+prrp_status prrp_ctx_set_solve_mode(prrp_ctx* ctx, int mode) {
+  if (!ctx || mode < 0 || mode > 1) return PRRP_ERR_INVALID_ARG;
+  ctx->solve_mode = mode;
   return PRRP_OK;
 }
 

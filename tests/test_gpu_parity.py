@@ -326,6 +326,33 @@ def test_bounded_wait_times_out(prrp, ctx):
     check_parity(prrp, ctx, pi.randn(128, 9), 16)
 
 
+def test_solve_modes_agree(prrp, ctx):
+    """The two substitution forms (one launch per triangle; one launch per 64-row block)
+    compute the same solution up to the order of rounding, for FP64 factors and for the
+    FP32 correction solves of a low-precision factorization."""
+    n = 1100
+    A = pi.randn(n, 46)
+    B = pi.rhs(n, 3, 46)
+    out = {}
+    for prec in (prrp.binding.PRRP_FP64, prrp.binding.PRRP_TF32):
+        for mode in (0, 1):
+            c = prrp.prrp_create(0)
+            try:
+                prrp.prrp_ctx_set_solve_mode(c, mode)
+                F = prrp.prrp_factor(c, torch.from_numpy(A).cuda(), b=64, prec=prec)
+                dB = torch.from_numpy(B).cuda()
+                info = prrp.prrp_solve(c, F, dB, A_orig=torch.from_numpy(A).cuda() if prec else None)
+                F.close()
+            finally:
+                c.close()
+            out[prec, mode] = dB.cpu().numpy()
+            if prec:
+                assert info["eta"] <= 1e-15, info
+        np.testing.assert_allclose(out[prec, 0], out[prec, 1], rtol=1e-9, atol=1e-10)
+    with pytest.raises(prrp.PrrpError):
+        prrp.prrp_ctx_set_solve_mode(ctx, 2)
+
+
 def test_substitution_wait_times_out(prrp, ctx):
     """The one-launch substitution's wait for an earlier row block gives up when that block
     never becomes final, reports PRRP_ERR_TIMEOUT through the host, and the next solve on
