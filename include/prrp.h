@@ -113,6 +113,8 @@ prrp_status prrp_destroy(prrp_ctx* ctx);
  *   5. GEPP on the w x w diagonal block and U12 = L11^-1 Pi_jj^T A12 (lines 10-11);
  *   6. the rows below the block receive the final L21 Pi_jj L11, so that on return dA holds
  *      the ordinary unit-lower L (strictly below the diagonal) and U (on and above it).
+ * With prec = PRRP_TF32 or PRRP_BF16X3, steps 4, 5 (U12, through an FP32 inverse of L11)
+ * and 6 run on the tensor cores; the pivot choices of steps 1 and 5 stay FP64.
  * n = 0 is a no-op.  dA is overwritten; *F receives a handle holding the permutation and
  * statistics (and a reference to dA, which must stay alive while F is used).
  * Errors: INVALID_ARG, NONFINITE (checked before any write to dA), SINGULAR (dA then holds
@@ -266,6 +268,9 @@ prrp_status prrp_panel_select(prrp_ctx* ctx, int m, int w, const double* dP, int
  * prrp_schur_update - step 4 alone: C -= L * U with C m x n (ldc), L m x k (ldl),
  * U k x n (ldu), 1 <= k <= 128, all row-major device pointers, computed in `prec`
  * (PRRP_FP64 uses DFMA; PRRP_TF32 / PRRP_BF16X3 use tcgen05 with FP32 accumulation).
+ * In the tensor-core precisions C may alias L or U (the operands are split into the
+ * context's workspace before C is written), which is how the factorization runs U12 and
+ * the final multipliers (steps 5-6) on the tensor cores; in PRRP_FP64 they must not overlap.
  */
 prrp_status prrp_schur_update(prrp_ctx* ctx, int m, int n, int k, const double* dL, int ldl,
                               const double* dU, int ldu, double* dC, int ldc, int prec,

@@ -84,6 +84,10 @@ struct prrp_ctx {
   size_t a12_cap = 0;
   unsigned char* tcws2 = nullptr;
   size_t tcws2_cap = 0;
+  unsigned char* tcws3 = nullptr;   // tensor-core workspace of the block stream (a7)
+  size_t tcws3_cap = 0;
+  double* tri = nullptr;            // I - L11^-1 and I - L11 of the current panel
+  size_t tri_cap = 0;
   // substitution: inverted diagonal blocks (FP64 and FP32), FP32 copy of the factors, the
   // factorization they were made from (generation number), step counters
   double* dinv64 = nullptr;
@@ -380,7 +384,7 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
   void* ptrs[] = {ctx->st, ctx->xval, ctx->xkey, ctx->xvec, ctx->pairs, ctx->ipiv, ctx->order,
                   ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB, ctx->tcws,
                   ctx->l21b, ctx->a12, ctx->tcws2, ctx->dinv64, ctx->dinv32, ctx->lu32, ctx->y32,
-                  ctx->tcount, ctx->zbuf, ctx->gemm_ctr, ctx->krylov, ctx->gm_coef};
+                  ctx->tcount, ctx->zbuf, ctx->gemm_ctr, ctx->krylov, ctx->gm_coef, ctx->tcws3, ctx->tri};
   for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
   if (ctx->s_rest) cudaStreamDestroy(ctx->s_rest);
   if (ctx->s_blk) cudaStreamDestroy(ctx->s_blk);
@@ -451,6 +455,14 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
   if (o.prec != PRRP_FP64 &&
       (ps = grow(ctx, &ctx->tcws2, &ctx->tcws2_cap, tc_workspace_bytes(o.prec, n, b, b))) != PRRP_OK)
     return fail(ps);
+  // a7 on the tensor cores in the low-precision modes: U12 (w x nc) and the multipliers
+  // ((m - w) x w) share one workspace on the block stream
+  const bool tc_a7 = o.prec != PRRP_FP64;
+  if (tc_a7) {
+    const size_t ws3 = std::max(tc_workspace_bytes(o.prec, b, n, b), tc_workspace_bytes(o.prec, n, b, b));
+    if ((ps = grow(ctx, &ctx->tcws3, &ctx->tcws3_cap, ws3)) != PRRP_OK) return fail(ps);
+    if ((ps = grow(ctx, &ctx->tri, &ctx->tri_cap, 2 * (size_t)b * b)) != PRRP_OK) return fail(ps);
+  }
   cudaStream_t sr = ctx->s_rest, sb = ctx->s_blk;
   cudaEvent_t ev_start = next_event(ctx);
   CK(cudaEventRecord(ev_start, s));
@@ -464,6 +476,7 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
     if (o.prec == PRRP_FP64)   // one tile counter per stream: the narrow and rest updates overlap
       return launch_gemm_fp64(mm, nn, kk, L, kk, U, ldu, C, lda, ctx->st, 1, ctx->num_sms, st, 1,
                               ctx->gemm_ctr + (st == sr ? 1 : 0));
+    ctx->kind_launches[PRRP_KIND_UPDATE] += 2;   // the two operand splits before the MMA kernel
     return launch_tc_update(o.prec, mm, nn, kk, L, kk, U, ldu, C, lda, ctx->st, 1, ws, st);
   };
   for (int jp = 0, k0 = 0; k0 < n; k0 += b, ++jp) {
@@ -516,16 +529,40 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
       }
       CK(cudaStreamWaitEvent(sb, ev_snap, 0));
     }
-    if (n > w) {
-      Timed t(ctx, sb, PRRP_KIND_U12, 1LL * nc * w * w);
-      e = launch_u12(dA, lda, n, k0, w, ctx->ipiv, ctx->st, sb);
+    if (tc_a7 && n > w) {
+      // U12 = X - (I - L11^-1) X and (L21 Pi_jj) L11 = Y - Y (I - L11) on the tensor cores
+      {
+        Timed t(ctx, sb, PRRP_KIND_U12, 1LL * nc * w * w);
+        ctx->kind_launches[PRRP_KIND_U12] += nc > 0 ? 4 : 1;   // swaps, E, 2 splits, MMA
+        e = launch_u12(dA, lda, n, k0, w, ctx->ipiv, ctx->st, sb, 0);
+        if (e == cudaSuccess) e = launch_tri_blocks(dA, lda, k0, w, ctx->tri, ctx->st, sb);
+        if (e == cudaSuccess && nc > 0)
+          e = launch_tc_update(o.prec, w, nc, w, ctx->tri, w, Akk + w, lda, Akk + w, lda, ctx->st, 2,
+                               ctx->tcws3, sb);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "u12"));
+      if (m > w) {
+        Timed t(ctx, sb, PRRP_KIND_LFIX, 1LL * (m - w) * w * w);
+        double* Y = Akk + (long long)w * lda;
+        ctx->kind_launches[PRRP_KIND_LFIX] += 3;               // copy, 2 splits, MMA
+        e = launch_lfix_copy(dA, lda, n, k0, w, L21, w, ctx->ipiv, ctx->st, sb);
+        if (e == cudaSuccess)
+          e = launch_tc_update(o.prec, m - w, w, w, Y, lda, ctx->tri + (size_t)w * w, w, Y, lda, ctx->st, 0,
+                               ctx->tcws3, sb);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "lfix"));
+    } else {
+      if (n > w) {
+        Timed t(ctx, sb, PRRP_KIND_U12, 1LL * nc * w * w);
+        e = launch_u12(dA, lda, n, k0, w, ctx->ipiv, ctx->st, sb);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "u12"));
+      if (m > w) {
+        Timed t(ctx, sb, PRRP_KIND_LFIX, 1LL * (m - w) * w * w);
+        e = launch_lfix(dA, lda, n, k0, w, L21, w, ctx->ipiv, ctx->st, sb);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "lfix"));
     }
-    if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "u12"));
-    if (m > w) {
-      Timed t(ctx, sb, PRRP_KIND_LFIX, 1LL * (m - w) * w * w);
-      e = launch_lfix(dA, lda, n, k0, w, L21, w, ctx->ipiv, ctx->st, sb);
-    }
-    if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "lfix"));
     ev_blk = next_event(ctx);
     CK(cudaEventRecord(ev_blk, sb));
   }
@@ -634,7 +671,7 @@ static prrp_status solve_into(prrp_ctx* ctx, const prrp_factors* F, const double
   const bool chain = nrhs <= kChainRhs && ctx->solve_mode == 0;
   if (chain && (ps = grow(ctx, &ctx->zbuf, &ctx->zbuf_cap, (size_t)F->n * nrhs)) != PRRP_OK) return ps;
   Timed t(ctx, s, PRRP_KIND_SOLVE, 2LL * F->n * F->n * nrhs);
-  ctx->kind_launches[PRRP_KIND_SOLVE] += chain ? 3 : 2LL * nb;   // gather + the substitution launches
+  ctx->kind_launches[PRRP_KIND_SOLVE] += chain ? 2 : 2LL * nb;   // with the gather: 1 + 2 (or 2 nb) launches
   if ((e = launch_gather_rows(B, ldb, F->perm, F->n, nrhs, Y, s)) != cudaSuccess) return cuda_fail(ctx, e, "gather");
   if (chain) {
     if ((e = launch_trsv_chain(F->dA, F->lda, ctx->dinv64, F->n, Y, ctx->zbuf, nrhs, 1, 0, ctx->tcount, ctx->st,
@@ -664,7 +701,7 @@ static prrp_status solve_into32(prrp_ctx* ctx, const prrp_factors* F, const doub
   if (chain && (ps = grow(ctx, &ctx->zbuf, &ctx->zbuf_cap, ((size_t)F->n * nrhs + 1) / 2)) != PRRP_OK) return ps;
   float* z32 = reinterpret_cast<float*>(ctx->zbuf);
   Timed t(ctx, s, PRRP_KIND_SOLVE, 2LL * F->n * F->n * nrhs);
-  ctx->kind_launches[PRRP_KIND_SOLVE] += chain ? 3 : 2LL * nb;
+  ctx->kind_launches[PRRP_KIND_SOLVE] += chain ? 2 : 2LL * nb;
   if ((e = launch_gather_rows32(B, ldb, F->perm, F->n, nrhs, ctx->y32, s)) != cudaSuccess)
     return cuda_fail(ctx, e, "gather");
   if (chain) {

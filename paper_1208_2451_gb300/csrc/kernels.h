@@ -50,7 +50,9 @@ cudaError_t launch_gemm_fp64(int m, int n, int k, const double* L, long long ldl
                              unsigned* tile_ctr = nullptr);
 
 // Same update on tcgen05 tensor cores, prec = PRRP_TF32 or PRRP_BF16X3 (FP32 accumulation,
-// FP64 C); ws holds the split operands (tc_workspace_bytes).
+// FP64 C); ws holds the split operands (tc_workspace_bytes).  Both operands are split into
+// ws before C is touched, so C may alias L or U.  track: 0 none, 1 max |C| into
+// st->gmax_bits, 2 into st->umax_bits.
 size_t tc_workspace_bytes(int prec, int m, int n, int k);
 cudaError_t launch_tc_update(int prec, int m, int n, int k, const double* L, long long ldl,
                              const double* U, long long ldu, double* C, long long ldc, DevState* st,
@@ -62,8 +64,17 @@ cudaError_t launch_diag_gepp(double* A, long long lda, int k0, int w, int* ipiv,
                              DevState* st, cudaStream_t s);
 
 // Block rows k0..k0+w-1: apply ipiv to columns [0, k0) and [k0+w, n); U12 = L11^-1 A12.
+// solve = 0: only GEPP's interchanges, on every column outside the block (the triangular
+// solve then runs elsewhere).
 cudaError_t launch_u12(double* A, long long lda, int n, int k0, int w, const int* ipiv,
-                       DevState* st, cudaStream_t s);
+                       DevState* st, cudaStream_t s, int solve = 1);
+// E = [I - L11^-1 ; I - L11] (2 w x w, ld w) for the tensor-core form of U12 and of the
+// final multipliers (low-precision modes; L11^-1 formed in FP32).
+cudaError_t launch_tri_blocks(const double* A, long long lda, int k0, int w, double* E, DevState* st,
+                              cudaStream_t s);
+// A[k0 + w + r][k0 + c] = L21[r][src(c)]: the multipliers with GEPP's column interchanges.
+cudaError_t launch_lfix_copy(double* A, long long lda, int n, int k0, int w, const double* L21, int ldl21,
+                             const int* ipiv, DevState* st, cudaStream_t s);
 
 // Rows k0+w..n-1: A[r][k0:k0+w] = (L21buf[r] with columns interchanged by ipiv) * L11.
 cudaError_t launch_lfix(double* A, long long lda, int n, int k0, int w, const double* L21,

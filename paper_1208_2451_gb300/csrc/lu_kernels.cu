@@ -343,16 +343,17 @@ constexpr int kU12Cols = 32;
 
 __global__ void __launch_bounds__(kU12Cols) u12_kernel(double* __restrict__ A, long long lda, int n,
                                                        int k0, int w, const int* __restrict__ ipiv,
-                                                       int left_slices, DevState* st) {
+                                                       int left_slices, int solve, DevState* st) {
   if (dev_status(st) != 0) return;
   extern __shared__ double sh[];
   double* Ls = sh;                                  // w x w (L11, unit lower)
   double* X = sh + w * w;                           // w x kU12Cols
   __shared__ int piv[kMaxW];
   const int tid = threadIdx.x;
-  const bool right = blockIdx.x >= left_slices;
-  const int c0 = right ? k0 + w + (blockIdx.x - left_slices) * kU12Cols : blockIdx.x * kU12Cols;
-  const int cend = right ? n : k0;
+  const bool side = blockIdx.x >= left_slices;      // right of the block
+  const bool right = side && solve;                 // interchanges and the triangular solve
+  const int c0 = side ? k0 + w + (blockIdx.x - left_slices) * kU12Cols : blockIdx.x * kU12Cols;
+  const int cend = side ? n : k0;
   const int cw = min(kU12Cols, cend - c0);
   for (int t = tid; t < w; t += blockDim.x) piv[t] = ipiv[t];
   if (right)
@@ -401,14 +402,15 @@ __global__ void __launch_bounds__(kU12Cols) u12_kernel(double* __restrict__ A, l
 template <int W>
 __global__ void __launch_bounds__(32) u12_reg_kernel(double* __restrict__ A, long long lda, int n,
                                                      int k0, const int* __restrict__ ipiv,
-                                                     int left_slices, DevState* st) {
+                                                     int left_slices, int solve, DevState* st) {
   if (dev_status(st) != 0) return;
   __shared__ double Ls[W * W];
   __shared__ int src[W];
   const int tid = threadIdx.x;
-  const bool right = blockIdx.x >= left_slices;
-  const int c = right ? k0 + W + (blockIdx.x - left_slices) * 32 + tid : blockIdx.x * 32 + tid;
-  const int cend = right ? n : k0;
+  const bool side = blockIdx.x >= left_slices;      // right of the block
+  const bool right = side && solve;                 // interchanges and the triangular solve
+  const int c = side ? k0 + W + (blockIdx.x - left_slices) * 32 + tid : blockIdx.x * 32 + tid;
+  const int cend = side ? n : k0;
   if (tid == 0) {                                  // composed row order of the interchanges
     for (int t = 0; t < W; ++t) src[t] = t;
     for (int t = 0; t < W; ++t) {
@@ -484,22 +486,99 @@ __global__ void __launch_bounds__(32) lfix_reg_kernel(double* __restrict__ A, lo
 }
 
 cudaError_t launch_u12(double* A, long long lda, int n, int k0, int w, const int* ipiv,
-                       DevState* st, cudaStream_t s) {
+                       DevState* st, cudaStream_t s, int solve) {
   const int left = (k0 + kU12Cols - 1) / kU12Cols;
   const int right = (n - k0 - w + kU12Cols - 1) / kU12Cols;
   if (left + right == 0) return cudaSuccess;
   if (w == 64) {
-    u12_reg_kernel<64><<<left + right, 32, 0, s>>>(A, lda, n, k0, ipiv, left, st);
+    u12_reg_kernel<64><<<left + right, 32, 0, s>>>(A, lda, n, k0, ipiv, left, solve, st);
     return cudaGetLastError();
   }
   if (w == 16) {
-    u12_reg_kernel<16><<<left + right, 32, 0, s>>>(A, lda, n, k0, ipiv, left, st);
+    u12_reg_kernel<16><<<left + right, 32, 0, s>>>(A, lda, n, k0, ipiv, left, solve, st);
     return cudaGetLastError();
   }
   const size_t smem = (size_t)(w * w + w * kU12Cols) * sizeof(double);
   cudaError_t e = smem_optin(u12_kernel);
   if (e != cudaSuccess) return e;
-  u12_kernel<<<left + right, kU12Cols, smem, s>>>(A, lda, n, k0, w, ipiv, left, st);
+  u12_kernel<<<left + right, kU12Cols, smem, s>>>(A, lda, n, k0, w, ipiv, left, solve, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- a7 on the tensor cores
+//
+// In the low-precision modes U12 = L11^-1 X (X: the block row after GEPP's interchanges)
+// and the final multipliers (L21 Pi_jj) L11 run on the tensor-core update, written in its
+// form C -= L U:  U12 = X - (I - L11^-1) X  and  (L21 Pi_jj) L11 = Y - Y (I - L11)  with
+// Y = L21 Pi_jj.  This kernel forms E1 = I - L11^-1 and E2 = I - L11 (w x w each, ld w)
+// from the unit lower L11 at A[k0][k0]; L11^-1 by forward substitution in FP32, one column
+// per thread (the factors of these modes are FP32-accurate).
+__global__ void __launch_bounds__(kMaxW) tri_blocks_kernel(const double* __restrict__ A, long long lda, int k0,
+                                                           int w, double* __restrict__ E, DevState* st) {
+  if (dev_status(st) != 0) return;
+  extern __shared__ float shf[];
+  float* Ls = shf;                         // strictly lower L11, w x w
+  float* G = shf + w * w;                  // L11^-1, w x w
+  const int t = threadIdx.x;
+  for (int e = t; e < w * w; e += blockDim.x) {
+    const int i = e / w, j = e - i * w;
+    Ls[e] = j < i ? static_cast<float>(A[(long long)(k0 + i) * lda + k0 + j]) : 0.f;
+  }
+  __syncthreads();
+  if (t < w) {
+    for (int i = 0; i < w; ++i) {
+      float acc = i == t ? 1.f : 0.f;
+      for (int k = t; k < i; ++k) acc = fmaf(-Ls[i * w + k], G[k * w + t], acc);
+      G[i * w + t] = acc;
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < w * w; e += blockDim.x) {
+    const int i = e / w, j = e - i * w;
+    E[e] = (i == j ? 1.0 : 0.0) - static_cast<double>(G[e]);
+    E[w * w + e] = j < i ? -A[(long long)(k0 + i) * lda + k0 + j] : 0.0;
+  }
+}
+
+cudaError_t launch_tri_blocks(const double* A, long long lda, int k0, int w, double* E, DevState* st,
+                              cudaStream_t s) {
+  if (w <= 0 || w > kMaxW) return cudaErrorInvalidValue;
+  cudaError_t e = smem_optin(tri_blocks_kernel);
+  if (e != cudaSuccess) return e;
+  tri_blocks_kernel<<<1, kMaxW, 2 * (size_t)w * w * sizeof(float), s>>>(A, lda, k0, w, E, st);
+  return cudaGetLastError();
+}
+
+// A[k0 + w + r][k0 + c] = L21[r][src(c)]: the multipliers with GEPP's column interchanges,
+// the operand Y above.
+__global__ void lfix_copy_kernel(double* __restrict__ A, long long lda, int rows, int k0, int w,
+                                 const double* __restrict__ L21, int ldl21, const int* __restrict__ ipiv,
+                                 DevState* st) {
+  if (dev_status(st) != 0) return;
+  __shared__ int src[kMaxW];
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < w; ++t) src[t] = t;
+    for (int t = 0; t < w; ++t) {
+      const int p = ipiv[t];
+      const int x = src[t]; src[t] = src[p]; src[p] = x;
+    }
+  }
+  __syncthreads();
+  const long long total = (long long)rows * w;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / w), c = (int)(e - (long long)r * w);
+    A[(long long)(k0 + w + r) * lda + k0 + c] = L21[(long long)r * ldl21 + src[c]];
+  }
+}
+
+cudaError_t launch_lfix_copy(double* A, long long lda, int n, int k0, int w, const double* L21, int ldl21,
+                             const int* ipiv, DevState* st, cudaStream_t s) {
+  const int rows = n - k0 - w;
+  if (rows <= 0) return cudaSuccess;
+  const long long total = (long long)rows * w;
+  lfix_copy_kernel<<<(int)std::min<long long>((total + 255) / 256, 152 * 8), 256, 0, s>>>(A, lda, rows, k0, w, L21,
+                                                                                        ldl21, ipiv, st);
   return cudaGetLastError();
 }
 

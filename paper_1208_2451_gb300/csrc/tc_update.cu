@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(const __grid_con
       cmax_bits = max_bits(cmax_bits, __shfl_xor_sync(0xffffffffu, cmax_bits, off));
     }
     // NaN bit patterns sort above every finite value; the input scan rejects them earlier
-    if (lane == 0) atomicMax(&st->gmax_bits, cmax_bits);
+    if (lane == 0) atomicMax(track == 2 ? &st->umax_bits : &st->gmax_bits, cmax_bits);
   }
   tc_fence_before();
   __syncthreads();

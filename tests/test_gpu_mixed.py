@@ -62,6 +62,35 @@ def test_schur_update_tensor_cores(prrp, ctx, prec, m, n, k):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
+def test_a7_forms_with_aliased_operand(prrp, ctx, prec):
+    """Row a7 in the low-precision modes runs on the tensor-core update in its form
+    C -= L U with C aliasing an operand (both operands are split before C is written):
+    U12 = X - (I - L11^-1) X and the final multipliers Y L11 = Y - Y (I - L11).  Both agree
+    with the FP64 triangular solve / product within the update's error bound."""
+    import scipy.linalg as sl
+    w, nc, rows = 64, 1000, 777
+    g = pi.rng(7000 + prec)
+    _, L11, _ = sl.lu(g.standard_normal((w, w)))        # unit lower, |l| <= 1, as from GEPP
+    X = g.standard_normal((w, nc))
+    Y = g.uniform(-2.0, 2.0, (rows, w))
+    E1 = np.eye(w) - np.linalg.inv(L11)
+    E2 = np.eye(w) - L11
+    dX = torch.from_numpy(X).cuda()
+    prrp.prrp_schur_update(ctx, torch.from_numpy(E1).cuda(), dX, dX, prec=prec)
+    want = sl.solve_triangular(L11, X, lower=True, unit_diagonal=True)
+    S = np.abs(E1) @ np.abs(X)
+    err = np.abs(dX.cpu().numpy() - want)
+    assert np.all(err <= _bound(prec, w, S) + 64 * EPS * (np.abs(np.linalg.inv(L11)) @ np.abs(X))), \
+        float(np.max(err / S))
+    dY = torch.from_numpy(Y).cuda()
+    prrp.prrp_schur_update(ctx, dY, torch.from_numpy(E2).cuda(), dY, prec=prec)
+    want = Y @ L11
+    S = np.abs(Y) @ np.abs(E2)
+    err = np.abs(dY.cpu().numpy() - want)
+    assert np.all(err <= _bound(prec, w, S) + 4 * EPS * (np.abs(Y) @ np.abs(L11))), float(np.max(err / S))
+
+
+@pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("r0,c0,ld,n", [(3, 2, 1000, 302), (3, 2, 1000, 301), (1, 1, 1000, 302),
                                         (0, 0, 777, 301), (5, 64, 900, 302), (2, 0, 1000, 302)])
 def test_schur_update_inside_larger_matrix(prrp, ctx, prec, r0, c0, ld, n):
