@@ -177,14 +177,25 @@ prrp_status prrp_gesv_host(prrp_ctx* ctx, int n, const double* hA, int lda, int 
  * per_system (host, count, may be NULL) receives each system's status; info (host, count,
  * may be NULL) its refinement count and first/final normwise backward error (max over its
  * right-hand sides).  Returns PRRP_OK when every system succeeded, otherwise the first
- * failing status in input order.  The launch shape (CTAs per SM) is tuned on the first
- * call for each size bucket of 128 and cached in ctx; the launch sequence is replayed as a
- * captured CUDA graph while the batch shape is unchanged.
+ * failing status in input order.  The launch shape (CTAs per SM x the update's register
+ * tile) is tuned on first use of each (precision, b, size bucket of 128) and kept for the
+ * process, per device; the launch sequence is replayed as a captured CUDA graph while the
+ * batch shape is unchanged.
  */
 prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const double* const* dA,
                              const int* lda, const int* nrhs, double* const* dB, const int* ldb,
                              int* const* dPerm, const prrp_opts* opts, void* stream,
                              prrp_status* per_system, prrp_solve_info* info);
+
+/*
+ * prrp_batch_tune - tune prrp_batch_solve's launch shape ahead of use for every size
+ * bucket of 128 up to nmax (<= 1024) under opts (may be NULL: the prrp_batch_solve
+ * defaults), so that no batch waits on the tuning.  It times candidate shapes on a
+ * synthetic sample (a few hundred MB of device memory for the largest bucket) on
+ * `stream`; a shape already tuned in this process is not tuned again.  INVALID_ARG,
+ * UNSUPPORTED (nmax > 1024 or prec other than FP32 / FP64), OOM, CUDA.
+ */
+prrp_status prrp_batch_tune(prrp_ctx* ctx, int nmax, const prrp_opts* opts, void* stream);
 
 /* ---- serving: continuous batching of solve requests (serve.cpp) ---- */
 
@@ -222,7 +233,8 @@ typedef struct {
  * (1..16; each lane owns a context and a stream, so lanes' work overlaps on the GPU) and
  * an HBM admission budget in bytes for the requests' device working sets.  A request is
  * admitted when its working set fits the budget left by the requests on the device;
- * requests with n <= 1024 that are admitted together are solved by one batched launch
+ * the batched path's launch shapes are tuned during the call (prrp_batch_tune);
+ * requests with n <= 512 that are admitted together are solved by one batched launch
  * (prrp_batch_solve); larger ones by prrp_factor + prrp_solve with their factors held in
  * device memory until their FP64 refinement ends.  opts (may be NULL): prec = PRRP_FP32
  * (default; FP32 batched factors, BF16X3 tensor-core Schur update for large n) or

@@ -65,6 +65,7 @@ _SIGS = {
     "prrp_selftest_wait": (_I, [_P, C.c_uint, _P]),
     "prrp_selftest_chain_wait": (_I, [_P, C.c_uint, _P]),
     "prrp_ctx_set_solve_mode": (_I, [_P, C.c_int]),
+    "prrp_batch_tune": (_I, [_P, C.c_int, _P, _P]),
     "prrp_panel_select_noalloc": (_I, [_I, _I, _P, _I, _D, _I, _P, _P, C.POINTER(_I), _P]),
     "prrp_ctx_set_timing": (_I, [_P, _I]),
     "prrp_ctx_kernel_stats": (_I, [_P, _P, _P, _P, _I]),
@@ -365,6 +366,13 @@ def prrp_panel_select_noalloc(P, tau=2.0, max_swaps=64, stream=None):
                                         C.byref(sw), _stream_ptr(stream))
     _check(st, "prrp_panel_select_noalloc")
     return order, L21, sw.value
+
+
+def prrp_batch_tune(ctx: Context, nmax: int, b=16, prec=PRRP_FP32, stream=None) -> None:
+    """Tune prrp_batch_solve's launch shape for sizes up to nmax ahead of use."""
+    o = default_opts(b=b, prec=prec)
+    _check(_lib.prrp_batch_tune(ctx.handle, int(nmax), C.byref(o), _stream_ptr(stream)), "prrp_batch_tune",
+           ctx.handle)
 
 
 def prrp_batch_solve(ctx: Context, As, Bs, b=16, tau=2.0, prec=PRRP_FP32, max_swaps=64,

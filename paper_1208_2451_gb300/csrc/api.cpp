@@ -1122,6 +1122,130 @@ size_t batch_ws_bytes(int grid, int nmax, int tmp_rows, bool fp64) {
 
 }  // namespace
 
+// Batched launch shape: CTAs per SM (1 .. maxper) x the update's register tile (1 or 2 rows
+// of L21 per warp pass), timed on a synthetic sample of full-bucket systems.  The choice
+// depends only on the device, precision, b and size bucket, so it is kept per process (and
+// per context, for the lock-free lookup): lanes of a server and later servers reuse it.
+// Tuning holds a process-wide lock, so two contexts never time their candidates against
+// each other.
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, long long>, int> g_tuned;   // (device, key) -> 4 * per + rb
+
+static prrp_status batch_tune_run(prrp_ctx* ctx, bool fp64, int b, int bucket, const prrp_opts& o, int maxper,
+                                  cudaStream_t s, int* out) {
+  prrp_status ps = PRRP_OK;
+  const int ns = 128 * bucket > 1024 ? 1024 : 128 * bucket;
+  const int sample = std::min(2 * ctx->num_sms, 256);
+  // owners: every return below (CK included) frees the sample and the events
+  struct DevMem { void* p = nullptr; ~DevMem() { if (p) cudaFree(p); } } mA, mB;
+  struct Ev { cudaEvent_t e = nullptr; ~Ev() { if (e) cudaEventDestroy(e); } } e0, e1;
+  CK(cudaMalloc(&mA.p, sizeof(double) * (size_t)sample * ns * ns));
+  CK(cudaMalloc(&mB.p, sizeof(double) * (size_t)sample * ns));
+  CK(cudaEventCreate(&e0.e));
+  CK(cudaEventCreate(&e1.e));
+  double* tA = static_cast<double*>(mA.p);
+  double* tB = static_cast<double*>(mB.p);
+  std::vector<int> hn(sample, ns), hl(sample, ns), hr(sample, 1), hord(sample);
+  std::iota(hord.begin(), hord.end(), 0);
+  std::vector<const double*> ha(sample);
+  std::vector<double*> hb(sample);
+  for (int i = 0; i < sample; ++i) { ha[i] = tA + (size_t)i * ns * ns; hb[i] = tB + (size_t)i * ns; }
+  int best = 4 * 1 + 1;
+  float best_ms = 1e30f;
+  const int nrb = fp64 ? 1 : 2;                         // FP64 keeps one row per pass
+  for (int cand = 0; cand < nrb * maxper && ps == PRRP_OK; ++cand) {
+    const int per = 1 + cand / nrb, rb = 1 + cand % nrb;
+    const int grid = per * ctx->num_sms;
+    ps = grow(ctx, &ctx->bws, &ctx->bws_cap, batch_ws_bytes(grid, ns, std::min(ns, 2 * (b + o.max_swaps) + 2), fp64));
+    if (ps != PRRP_OK) break;
+    const size_t mb = align256(sizeof(int) * sample * 6) + align256(sizeof(void*) * sample * 2);
+    ps = grow(ctx, &ctx->bmeta, &ctx->bmeta_cap, mb + 256);
+    if (ps != PRRP_OK) break;
+    ps = grow(ctx, &ctx->bout, &ctx->bout_cap, align256(sizeof(int) * 2 * sample) + align256(sizeof(double) * 2 * sample) + 256);
+    if (ps != PRRP_OK) break;
+    int* mi = reinterpret_cast<int*>(ctx->bmeta);
+    CK(cudaMemcpyAsync(mi, hord.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(mi + sample, hn.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(mi + 2 * sample, hl.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(mi + 3 * sample, hr.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(mi + 4 * sample, hr.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
+    const double** pa = reinterpret_cast<const double**>(ctx->bmeta + align256(sizeof(int) * sample * 6));
+    double** pb = reinterpret_cast<double**>(ctx->bmeta + align256(sizeof(int) * sample * 6) +
+                                             sizeof(void*) * sample);
+    CK(cudaMemcpyAsync(pa, ha.data(), sizeof(void*) * sample, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(pb, hb.data(), sizeof(void*) * sample, cudaMemcpyHostToDevice, s));
+    int* d_status = reinterpret_cast<int*>(ctx->bout);
+    int* d_iters = d_status + sample;
+    double* d_e0 = reinterpret_cast<double*>(ctx->bout + align256(sizeof(int) * 2 * sample));
+    double* d_e = d_e0 + sample;
+    unsigned* d_counter = reinterpret_cast<unsigned*>(mi + 5 * sample);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && ps == PRRP_OK; ++rep) {   // first run warms up
+      CK(launch_batch_fill(tA, ns, sample, tB, s));
+      CK(cudaEventRecord(e0.e, s));
+      ps = enqueue_batch(ctx, fp64, sample, ns, b, std::min(ns, 2 * (b + o.max_swaps) + 2), grid, rb, o, mi,
+                         mi + sample, pa, mi + 2 * sample, mi + 3 * sample, pb, mi + 4 * sample,
+                         nullptr, d_status, d_iters, d_e0, d_e, d_counter, s);
+      CK(cudaEventRecord(e1.e, s));
+      CK(cudaEventSynchronize(e1.e));
+      CK(cudaEventElapsedTime(&ms, e0.e, e1.e));
+    }
+    if (ps != PRRP_OK) break;
+    if (ms < best_ms) { best_ms = ms; best = 4 * per + rb; }
+  }
+  if (ps != PRRP_OK) return ps;
+  *out = best;
+  return PRRP_OK;
+}
+
+static prrp_status batch_shape(prrp_ctx* ctx, bool fp64, int b, int bucket, const prrp_opts& o, int maxper,
+                               cudaStream_t s, int* out) {
+  const long long tkey = ((long long)fp64 << 40) | ((long long)b << 20) | bucket;
+  auto it = ctx->batch_tuned.find(tkey);
+  if (it != ctx->batch_tuned.end()) {
+    *out = 4 * std::min(it->second / 4, maxper) + it->second % 4;
+    return PRRP_OK;
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto g = g_tuned.find({ctx->device, tkey});
+  if (g == g_tuned.end()) {
+    int best = 0;
+    prrp_status ps = batch_tune_run(ctx, fp64, b, bucket, o, maxper, s, &best);
+    if (ps != PRRP_OK) return ps;
+    g = g_tuned.emplace(std::make_pair(ctx->device, tkey), best).first;
+  }
+  ctx->batch_tuned[tkey] = g->second;
+  // a shape tuned on full-bucket systems never asks for more CTAs per SM than fit, but
+  // one tuned first on smaller systems of the bucket may: clamp to this batch's limit
+  *out = 4 * std::min(g->second / 4, maxper) + g->second % 4;
+  return PRRP_OK;
+}
+
+prrp_status prrp_batch_tune(prrp_ctx* ctx, int nmax, const prrp_opts* opts_in, void* stream) {
+  if (!ctx || nmax < 1) return PRRP_ERR_INVALID_ARG;
+  if (nmax > 1024) return PRRP_ERR_UNSUPPORTED;
+  prrp_opts o;
+  prrp_opts_default(&o);
+  o.b = 16;
+  o.prec = PRRP_FP32;
+  if (opts_in) o = *opts_in;
+  prrp_status ps = check_opts(&o);
+  if (ps != PRRP_OK) return ps;
+  if (o.prec != PRRP_FP32 && o.prec != PRRP_FP64) return PRRP_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaSetDevice(ctx->device));
+  for (int bucket = 1; bucket <= (nmax + 127) / 128; ++bucket) {
+    const int nb = 128 * bucket;
+    const int b = std::min({o.b, batch_max_width(), nb});
+    const int maxper = batch_max_ctas_per_sm(nb, b);
+    if (maxper == 0) return PRRP_ERR_UNSUPPORTED;
+    CK(prepare_batch(nb, b));
+    int shape = 0;
+    if ((ps = batch_shape(ctx, o.prec == PRRP_FP64, b, bucket, o, maxper, s, &shape)) != PRRP_OK) return ps;
+  }
+  return PRRP_OK;
+}
+
 prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const double* const* dA,
                              const int* lda, const int* nrhs, double* const* dB, const int* ldb,
                              int* const* dPerm, const prrp_opts* opts_in, void* stream,
@@ -1154,76 +1278,10 @@ prrp_status prrp_batch_solve(prrp_ctx* ctx, int count, const int* n, const doubl
   if (maxper == 0) return PRRP_ERR_UNSUPPORTED;
   CK(prepare_batch(std::max(nmax, 128 * ((nmax + 127) / 128)), b));
 
-  // ---- autotune the launch shape for this (precision, b, size bucket), once per context:
-  // CTAs per SM (1 .. maxper) x the update's register tile (1 or 2 rows of L21 per warp pass)
-  const int bucket = (nmax + 127) / 128;
-  const long long tkey = ((long long)fp64 << 40) | ((long long)b << 20) | bucket;
-  auto tuned = ctx->batch_tuned.find(tkey);
-  if (tuned == ctx->batch_tuned.end()) {
-    const int ns = 128 * bucket > 1024 ? 1024 : 128 * bucket;
-    const int sample = std::min(2 * ctx->num_sms, 256);
-    // owners: every return below (CK included) frees the sample and the events
-    struct DevMem { void* p = nullptr; ~DevMem() { if (p) cudaFree(p); } } mA, mB;
-    struct Ev { cudaEvent_t e = nullptr; ~Ev() { if (e) cudaEventDestroy(e); } } e0, e1;
-    CK(cudaMalloc(&mA.p, sizeof(double) * (size_t)sample * ns * ns));
-    CK(cudaMalloc(&mB.p, sizeof(double) * (size_t)sample * ns));
-    CK(cudaEventCreate(&e0.e));
-    CK(cudaEventCreate(&e1.e));
-    double* tA = static_cast<double*>(mA.p);
-    double* tB = static_cast<double*>(mB.p);
-    std::vector<int> hn(sample, ns), hl(sample, ns), hr(sample, 1), hord(sample);
-    std::iota(hord.begin(), hord.end(), 0);
-    std::vector<const double*> ha(sample);
-    std::vector<double*> hb(sample);
-    for (int i = 0; i < sample; ++i) { ha[i] = tA + (size_t)i * ns * ns; hb[i] = tB + (size_t)i * ns; }
-    int best = 4 * 1 + 1;
-    float best_ms = 1e30f;
-    const int nrb = fp64 ? 1 : 2;                         // FP64 keeps one row per pass
-    for (int cand = 0; cand < nrb * maxper && ps == PRRP_OK; ++cand) {
-      const int per = 1 + cand / nrb, rb = 1 + cand % nrb;
-      const int grid = per * ctx->num_sms;
-      ps = grow(ctx, &ctx->bws, &ctx->bws_cap, batch_ws_bytes(grid, ns, std::min(ns, 2 * (b + o.max_swaps) + 2), fp64));
-      if (ps != PRRP_OK) break;
-      const size_t mb = align256(sizeof(int) * sample * 6) + align256(sizeof(void*) * sample * 2);
-      ps = grow(ctx, &ctx->bmeta, &ctx->bmeta_cap, mb + 256);
-      if (ps != PRRP_OK) break;
-      ps = grow(ctx, &ctx->bout, &ctx->bout_cap, align256(sizeof(int) * 2 * sample) + align256(sizeof(double) * 2 * sample) + 256);
-      if (ps != PRRP_OK) break;
-      int* mi = reinterpret_cast<int*>(ctx->bmeta);
-      CK(cudaMemcpyAsync(mi, hord.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(mi + sample, hn.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(mi + 2 * sample, hl.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(mi + 3 * sample, hr.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(mi + 4 * sample, hr.data(), sizeof(int) * sample, cudaMemcpyHostToDevice, s));
-      const double** pa = reinterpret_cast<const double**>(ctx->bmeta + align256(sizeof(int) * sample * 6));
-      double** pb = reinterpret_cast<double**>(ctx->bmeta + align256(sizeof(int) * sample * 6) +
-                                               sizeof(void*) * sample);
-      CK(cudaMemcpyAsync(pa, ha.data(), sizeof(void*) * sample, cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(pb, hb.data(), sizeof(void*) * sample, cudaMemcpyHostToDevice, s));
-      int* d_status = reinterpret_cast<int*>(ctx->bout);
-      int* d_iters = d_status + sample;
-      double* d_e0 = reinterpret_cast<double*>(ctx->bout + align256(sizeof(int) * 2 * sample));
-      double* d_e = d_e0 + sample;
-      unsigned* d_counter = reinterpret_cast<unsigned*>(mi + 5 * sample);
-      float ms = 0.f;
-      for (int rep = 0; rep < 2 && ps == PRRP_OK; ++rep) {   // first run warms up
-        CK(launch_batch_fill(tA, ns, sample, tB, s));
-        CK(cudaEventRecord(e0.e, s));
-        ps = enqueue_batch(ctx, fp64, sample, ns, b, std::min(ns, 2 * (b + o.max_swaps) + 2), grid, rb, o, mi,
-                           mi + sample, pa, mi + 2 * sample, mi + 3 * sample, pb, mi + 4 * sample,
-                           nullptr, d_status, d_iters, d_e0, d_e, d_counter, s);
-        CK(cudaEventRecord(e1.e, s));
-        CK(cudaEventSynchronize(e1.e));
-        CK(cudaEventElapsedTime(&ms, e0.e, e1.e));
-      }
-      if (ps != PRRP_OK) break;
-      if (ms < best_ms) { best_ms = ms; best = 4 * per + rb; }
-    }
-    if (ps != PRRP_OK) return ps;
-    ctx->batch_tuned[tkey] = best;
-    tuned = ctx->batch_tuned.find(tkey);
-  }
-  const int grid = (tuned->second / 4) * ctx->num_sms, rb = tuned->second % 4;
+  // ---- the launch shape for this (precision, b, size bucket): tuned once per process
+  int shape = 0;
+  if ((ps = batch_shape(ctx, fp64, b, (nmax + 127) / 128, o, maxper, s, &shape)) != PRRP_OK) return ps;
+  const int grid = (shape / 4) * ctx->num_sms, rb = shape % 4;
 
   // ---- metadata: largest systems first, so the tail of the work list is short
   std::vector<int> ord(count);

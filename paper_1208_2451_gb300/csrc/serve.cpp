@@ -302,6 +302,12 @@ prrp_status prrp_server_create(prrp_ctx* ctx, size_t hbm_budget_bytes, const prr
   S->opts.prec = PRRP_FP32;
   if (opts) S->opts = *opts;
   S->nlanes = lanes;
+  // the batched units' launch shapes are tuned here, before any request waits on them
+  prrp_opts bo = S->opts;
+  if (bo.prec != PRRP_FP64) bo.prec = PRRP_FP32;
+  bo.b = std::min(bo.b, 16);
+  const prrp_status ts = prrp_batch_tune(ctx, kSmallMax, &bo, nullptr);
+  if (ts != PRRP_OK) { delete S; return ts; }
   for (int i = 0; i < lanes; ++i) S->lanes.emplace_back(lane_main, S);
   *out = S;
   return PRRP_OK;

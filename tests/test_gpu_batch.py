@@ -132,3 +132,28 @@ def test_batch_4096_uneven(prrp, ctx):
         eta = float(r.abs().sum() / (A.abs().sum(0).max() * x.abs().sum() + b0.abs().sum()))
         worst = max(worst, eta)
     assert worst <= 1e-15, worst
+
+
+def test_batch_tune_ahead_and_shared(prrp):
+    """prrp_batch_tune fixes the launch shapes before any batch: a second call, from another
+    context, finds them tuned for the process and returns at once, and batches solved
+    afterwards through either context are correct."""
+    import time
+    c1, c2 = prrp.prrp_create(0), prrp.prrp_create(0)
+    try:
+        prrp.prrp_batch_tune(c1, 300, prec=3)
+        t0 = time.perf_counter()
+        prrp.prrp_batch_tune(c2, 300, prec=3)
+        assert time.perf_counter() - t0 < 0.5
+        sizes = [40, 130, 257, 300]
+        As, Bs = _systems(sizes, 4400)
+        for c in (c1, c2):
+            st, info, X, P = _run(prrp, c, As, Bs, prec=3)
+            assert all(s == 0 for s in st), st
+            for A, B, x in zip(As, Bs, X):
+                assert M.eta(A, x[:, 0], B[:, 0]) <= 1e-15
+        with pytest.raises(prrp.PrrpError):
+            prrp.prrp_batch_tune(c1, 2000)
+    finally:
+        c1.close()
+        c2.close()
