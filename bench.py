@@ -55,6 +55,22 @@ def fp64_peak_tflops(sm_mhz: float | None = None) -> float:
     return 152 * 2 * 2 * f / 1e12
 
 
+def fracs(tflops: float, prec: int | None, b: int = 64) -> dict:
+    """Whole-solve throughput as fractions of the rooflines it runs against: the FP64 FMA
+    pipe, and for a tensor-core precision the Schur update's roofline at panel width b,
+    min(HBM x 2b/16 flop/B, measured bf16 peak x nominal ratio / products); for the FP32
+    batched form the FP32 SIMT FMA peak (152 SMs x 128 FMA/clk x 2 flop x 2070 MHz)."""
+    pk = _peaks()
+    out = {"of_fp64_pipe_peak": tflops / fp64_peak_tflops()}
+    if prec in (1, 2):
+        hbm, bf16 = pk.get("hbm_gbs", 6800.0), pk.get("bf16_tflops", 1900.0)
+        tc = bf16 * 1.1 / 2.25 if prec == 1 else bf16 / 6
+        out["of_tc_update_roofline"] = tflops / min(hbm * 2 * b / 16 / 1000, tc)
+    if prec == 3:
+        out["of_fp32_simt_peak"] = tflops / (152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12)
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -234,7 +250,8 @@ def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=
         dt = min(times)
         key = f"kappa={kappa:g}" if kappa > 0 else "randn"
         out[key] = {"s": dt, "tflops": 2 * n ** 3 / 3 / dt / 1e12, "solves_per_s": 1.0 / dt,
-                    "eta": eta, "iterations": info["iterations"]}
+                    "eta": eta, "iterations": info["iterations"],
+                    "roofline_fracs": fracs(2 * n ** 3 / 3 / dt / 1e12, prec)}
         if plain and kappa == kappas[0]:
             del A, B
             torch.cuda.empty_cache()
@@ -325,6 +342,7 @@ def form_batched(prrp, ctx, torch, dev, count=4096, reps=3, plain_sample=256, di
                      "max_eta": max(reduce_max([max(i["eta"] for i in info)], dist, dev)),
                      "failed": int(sum(reduce_max([sum(1 for x in st if x != 0)], dist, dev))),
                      "ranks": world}
+        res[name]["roofline_fracs"] = fracs(res[name]["tflops"], prec)
     if world > 1:
         return {"workload": f"{count} systems, n uniform in [32, 512], b=16, 1 RHS, "
                             f"flop-balanced over {world} ranks", "runs": res}
