@@ -564,6 +564,8 @@ def main():
                     help="skip the mixed-precision, batched and served measurements")
     ap.add_argument("--form", choices=["mixed", "batched", "served", "update"],
                     help="run only one of the other forms and print its JSON")
+    ap.add_argument("--count", type=int, default=4096,
+                    help="--form batched: number of systems (smaller batches for profiling)")
     ap.add_argument("--randn", action="store_true",
                     help="--form mixed: an iid N(0,1) matrix instead of the conditioned one")
     args = ap.parse_args()
@@ -589,7 +591,7 @@ def main():
         fn = {"mixed": lambda: form_mixed(prrp, ctx, torch, dev,
                                           n=args.n if args.n != N_DEFAULT else 16384,
                                           kappas=(0.0,) if args.randn else (1e2, 1e6)),
-              "batched": lambda: form_batched(prrp, ctx, torch, dev, dist=dist),
+              "batched": lambda: form_batched(prrp, ctx, torch, dev, count=args.count, dist=dist),
               "served": lambda: form_served(prrp, ctx),
               "update": lambda: form_update(prrp, ctx, torch, dev,
                                             n=args.n if args.n != N_DEFAULT else 16384)}[args.form]

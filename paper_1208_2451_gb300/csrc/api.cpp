@@ -1079,10 +1079,11 @@ size_t batch_cta_bytes(int nmax, int tmp_rows, bool fp64) {
 
 int batch_max_ctas_per_sm(int nmax, int b) {
   int per = 0;
-  // both instantiations share the launch shape; ask for the float one
+  // every instantiation is capped at 128 registers a thread (two CTAs of 256 threads per
+  // SM) and holds at most 26 KB of static shared memory beside the dynamic panel space
   const size_t smem = batch_smem_bytes(nmax, b);
-  if (smem > 227 * 1024) return 0;
-  per = (int)std::min<size_t>(4, (228 * 1024) / (smem + 17 * 1024 + 1024));
+  if (smem > 200 * 1024) return 0;
+  per = (int)std::min<size_t>(2, (228 * 1024) / (smem + 26 * 1024 + 1024));
   return std::max(per, 1);
 }
 

@@ -27,6 +27,7 @@ namespace {
 constexpr int kBT = 256;          // threads per batch CTA
 constexpr int kBW = 32;           // largest panel width in the batched kernel
 constexpr int kBTeams = kBT / kTeam;
+constexpr int kUnroll = 4;        // global loads a thread keeps in flight in the copy and update loops
 
 struct BKey {
   unsigned long long v;
@@ -260,21 +261,44 @@ struct BatchArgs {
   unsigned* counter;         // work list head
 };
 
+// The kb x kb diagonal block at (k0, k0) of W into Db (FP64, stride kBW + 1), every thread
+// loading its share at once, so the dependent block solve reads shared memory.
+template <typename T>
+__device__ __forceinline__ void stage_block(const T* W, int n, int k0, int kb, double* Db) {
+  __syncthreads();
+  for (int e0 = threadIdx.x; e0 < kb * kb; e0 += kUnroll * kBT) {
+    T v[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int e = e0 + u * kBT, i = e / kb, k = e - i * kb;
+      v[u] = e < kb * kb ? W[(long long)(k0 + i) * n + k0 + k] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int e = e0 + u * kBT, i = e / kb, k = e - i * kb;
+      if (e < kb * kb) Db[i * (kBW + 1) + k] = static_cast<double>(v[u]);
+    }
+  }
+  __syncthreads();
+}
+
 // x (FP64, length n) <- U^-1 L^-1 P y for the T factors in W (ld n); y = b or r in v, x out.
+// Db: kBW x (kBW + 1) doubles of shared scratch.
 template <typename T>
 __device__ void batch_lu_solve(const T* W, int n, const int* perm, const double* rhs, double* x,
-                               double* s_red) {
+                               double* s_red, double* Db) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < n; i += kBT) x[i] = rhs[perm[i]];
   __syncthreads();
   // forward substitution, blocks of 32 rows: warp 0 solves the block, all update below
   for (int k0 = 0; k0 < n; k0 += 32) {
     const int kb = min(32, n - k0);
+    stage_block(W, n, k0, kb, Db);
     if (warp == 0) {
       double y = lane < kb ? x[k0 + lane] : 0.0;
       for (int k = 0; k < kb; ++k) {
         const double xk = __shfl_sync(0xffffffffu, y, k);
-        if (lane > k && lane < kb) y = fma(-static_cast<double>(W[(long long)(k0 + lane) * n + k0 + k]), xk, y);
+        if (lane > k && lane < kb) y = fma(-Db[lane * (kBW + 1) + k], xk, y);
       }
       if (lane < kb) x[k0 + lane] = y;
     }
@@ -289,12 +313,13 @@ __device__ void batch_lu_solve(const T* W, int n, const int* perm, const double*
   }
   for (int kend = n; kend > 0; kend -= 32) {
     const int k0 = max(0, kend - 32), kb = kend - k0;
+    stage_block(W, n, k0, kb, Db);
     if (warp == 0) {
       double y = lane < kb ? x[k0 + lane] : 0.0;
       for (int k = kb - 1; k >= 0; --k) {
-        if (lane == k) y = y / static_cast<double>(W[(long long)(k0 + k) * n + k0 + k]);
+        if (lane == k) y = y / Db[k * (kBW + 1) + k];
         const double xk = __shfl_sync(0xffffffffu, y, k);
-        if (lane < k) y = fma(-static_cast<double>(W[(long long)(k0 + lane) * n + k0 + k]), xk, y);
+        if (lane < k) y = fma(-Db[lane * (kBW + 1) + k], xk, y);
       }
       if (lane < kb) x[k0 + lane] = y;
     }
@@ -312,8 +337,10 @@ __device__ void batch_lu_solve(const T* W, int n, const int* perm, const double*
 // RB: the Schur update's register tile, RB rows of L21 per warp pass (each staged value of
 // A12 feeds RB FMAs); chosen per workload by the autotuner together with CTAs per SM (FP32
 // working copies only: two FP64 rows of up to 32 multipliers exceed the register budget).
-template <typename T, int RB>
-__global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
+// WB: the panel widths this instantiation serves (w <= WB; 16 or kBW), the length of the
+// per-thread register arrays of the update, U12 and the final multipliers.
+template <typename T, int RB, int WB>
+__global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ BKey s_w[kBT / 32];
   __shared__ double s_red[kBT / 32];
@@ -321,7 +348,9 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
   __shared__ double Rs[kBW * kBW];
   __shared__ double rdiag[kBW];
   __shared__ int ipiv[kBW];
+  __shared__ int s_src[kBW];                        // GEPP's interchanges composed: position <- row
   __shared__ double Dg[kBW * (kBW + 1)];
+  __shared__ T Lt[kBW * (kBW + 1)];                 // L11 in T, for U12 and the final multipliers
   const int tid = threadIdx.x;
   T* W = a.wsW + (size_t)blockIdx.x * a.nmax * a.nmax;
   T* Tmp = a.wsT + (size_t)blockIdx.x * a.tmp_rows * a.nmax;
@@ -340,11 +369,27 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
     if (tid == 0) s_status = 0;
     int swaps_total = 0;
     // ---- working copy and permutation
-    for (long long e = tid; e < (long long)n * n; e += kBT) {
-      const int i = static_cast<int>(e / n), j = static_cast<int>(e - (long long)i * n);
-      const double v = A[(long long)i * lda + j];
-      if (!isfinite(v)) s_status = PRRP_ERR_NONFINITE;
-      W[e] = static_cast<T>(v);
+    {
+      const long long nn = (long long)n * n;
+      bool bad = false;
+      for (long long e0 = tid; e0 < nn; e0 += kUnroll * kBT) {   // kUnroll loads in flight
+        double v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const long long e = e0 + (long long)u * kBT;
+          const int i = static_cast<int>(e / n), j = static_cast<int>(e - (long long)i * n);
+          v[u] = e < nn ? A[(long long)i * lda + j] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const long long e = e0 + (long long)u * kBT;
+          if (e < nn) {
+            bad |= abs_bits(v[u]) >= kInfBits;
+            W[e] = static_cast<T>(v[u]);
+          }
+        }
+      }
+      if (bad) s_status = PRRP_ERR_NONFINITE;
     }
     for (int i = tid; i < n; i += kBT) perm[i] = i;
     __syncthreads();
@@ -356,9 +401,18 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
       double* nrm = Ps + (size_t)m * sp;
       double* nref = nrm + m;
       int* pos = reinterpret_cast<int*>(nref + m);
-      for (int e = tid; e < m * w; e += kBT) {
-        const int r = e / w, c = e - r * w;
-        Ps[r * sp + c] = static_cast<double>(W[(long long)(k0 + r) * n + k0 + c]);
+      for (int e0 = tid; e0 < m * w; e0 += kUnroll * kBT) {
+        T v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int e = e0 + u * kBT, r = e / w, c = e - r * w;
+          v[u] = e < m * w ? W[(long long)(k0 + r) * n + k0 + c] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int e = e0 + u * kBT, r = e / w, c = e - r * w;
+          if (e < m * w) Ps[r * sp + c] = static_cast<double>(v[u]);
+        }
       }
       __syncthreads();
       int sw = 0;
@@ -388,14 +442,32 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
         __syncthreads();
         break;
       }
-      for (int e = tid; e < np * n; e += kBT) {
-        const int k = e / n, j = e - k * n;
-        Tmp[(long long)k * n + j] = W[(long long)(k0 + mv[2 * k + 1]) * n + j];
+      for (int e0 = tid; e0 < np * n; e0 += kUnroll * kBT) {
+        T v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int e = e0 + u * kBT, k = e / n, j = e - k * n;
+          v[u] = e < np * n ? W[(long long)(k0 + mv[2 * k + 1]) * n + j] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int e = e0 + u * kBT;
+          if (e < np * n) Tmp[e] = v[u];
+        }
       }
       __syncthreads();
-      for (int e = tid; e < np * n; e += kBT) {
-        const int k = e / n, j = e - k * n;
-        W[(long long)(k0 + mv[2 * k]) * n + j] = Tmp[(long long)k * n + j];
+      for (int e0 = tid; e0 < np * n; e0 += kUnroll * kBT) {
+        T v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int e = e0 + u * kBT;
+          v[u] = e < np * n ? Tmp[e] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int e = e0 + u * kBT, k = e / n, j = e - k * n;
+          if (e < np * n) W[(long long)(k0 + mv[2 * k]) * n + j] = v[u];
+        }
       }
       __syncthreads();
       if (tid == 0) {                          // perm follows the same moves
@@ -414,36 +486,58 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
       // along the columns
       const int nc = n - k0 - w;
       T* Us = reinterpret_cast<T*>(smem_raw);
-      for (int e = tid; e < w * nc; e += kBT) {
-        const int k = e / nc, j = e - k * nc;
-        Us[e] = W[(long long)(k0 + k) * n + k0 + w + j];
+      for (int e0 = tid; e0 < w * nc; e0 += kUnroll * kBT) {
+        T v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int e = e0 + u * kBT, k = e / max(nc, 1), j = e - k * nc;
+          v[u] = e < w * nc ? W[(long long)(k0 + k) * n + k0 + w + j] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int e = e0 + u * kBT;
+          if (e < w * nc) Us[e] = v[u];
+        }
       }
       __syncthreads();
       {
         const int lane = tid & 31, warp = tid >> 5;
         const int rows = m - w;
         for (int i0 = warp * RB; i0 < rows; i0 += (kBT / 32) * RB) {
-          T lr[RB][kBW];
+          T lr[RB][WB];
 #pragma unroll
           for (int r = 0; r < RB; ++r) {
             const T* l = W + (long long)(k0 + w + i0 + r) * n + k0;
 #pragma unroll
-            for (int k = 0; k < kBW; ++k) lr[r][k] = (k < w && i0 + r < rows) ? l[k] : T(0);
+            for (int k = 0; k < WB; ++k) lr[r][k] = (k < w && i0 + r < rows) ? l[k] : T(0);
           }
-          for (int j = lane; j < nc; j += 32) {
-            T acc[RB];
+          for (int j0 = lane; j0 < nc; j0 += 32 * kUnroll) {
+            T cv[RB][kUnroll];                       // the C values, loaded before any use
 #pragma unroll
-            for (int r = 0; r < RB; ++r) acc[r] = 0;
+            for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
-            for (int k = 0; k < kBW; ++k)
-              if (k < w) {
-                const T u = Us[k * nc + j];
-#pragma unroll
-                for (int r = 0; r < RB; ++r) acc[r] = fma(lr[r][k], u, acc[r]);
+              for (int r = 0; r < RB; ++r) {
+                const int j = j0 + 32 * u;
+                cv[r][u] = (j < nc && i0 + r < rows) ? W[(long long)(k0 + w + i0 + r) * n + k0 + w + j] : T(0);
               }
 #pragma unroll
-            for (int r = 0; r < RB; ++r)
-              if (i0 + r < rows) W[(long long)(k0 + w + i0 + r) * n + k0 + w + j] -= acc[r];
+            for (int u = 0; u < kUnroll; ++u) {
+              const int j = j0 + 32 * u;
+              if (j >= nc) break;
+              T acc[RB];
+#pragma unroll
+              for (int r = 0; r < RB; ++r) acc[r] = 0;
+#pragma unroll
+              for (int k = 0; k < WB; ++k)
+                if (k < w) {
+                  const T uk = Us[k * nc + j];
+#pragma unroll
+                  for (int r = 0; r < RB; ++r) acc[r] = fma(lr[r][k], uk, acc[r]);
+                }
+#pragma unroll
+              for (int r = 0; r < RB; ++r)
+                if (i0 + r < rows) W[(long long)(k0 + w + i0 + r) * n + k0 + w + j] = cv[r][u] - acc[r];
+            }
           }
         }
       }
@@ -494,42 +588,59 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
         W[(long long)(k0 + i) * n + k0 + j] = static_cast<T>(Dg[i * (kBW + 1) + j]);
       }
       __syncthreads();
-      if (tid == 0)
-        for (int t = 0; t < w; ++t) {
-          const int p = ipiv[t];
-          if (p != t) { const int x = perm[k0 + t]; perm[k0 + t] = perm[k0 + p]; perm[k0 + p] = x; }
-        }
-      // block-row interchanges outside the block and U12 = L11^-1 A12, one column per thread
-      for (int j = tid; j < n; j += kBT) {
-        if (j >= k0 && j < k0 + w) continue;
+      if (tid == 0) {
+        for (int t = 0; t < w; ++t) s_src[t] = t;
         for (int t = 0; t < w; ++t) {
           const int p = ipiv[t];
           if (p != t) {
-            const T x = W[(long long)(k0 + t) * n + j];
-            W[(long long)(k0 + t) * n + j] = W[(long long)(k0 + p) * n + j];
-            W[(long long)(k0 + p) * n + j] = x;
+            const int x = perm[k0 + t]; perm[k0 + t] = perm[k0 + p]; perm[k0 + p] = x;
+            const int y = s_src[t]; s_src[t] = s_src[p]; s_src[p] = y;
           }
         }
-        if (j >= k0 + w)                             // U12 = L11^-1 A12 in T
-          for (int k = 0; k < w; ++k) {
-            const T xk = W[(long long)(k0 + k) * n + j];
-            for (int i = k + 1; i < w; ++i)
-              W[(long long)(k0 + i) * n + j] =
-                  fma(-static_cast<T>(Dg[i * (kBW + 1) + k]), xk, W[(long long)(k0 + i) * n + j]);
-          }
       }
-      // final multipliers of the rows below: (L21 with GEPP's column interchanges) * L11
+      for (int e = tid; e < w * w; e += kBT) {
+        const int i = e / w, k = e - i * w;
+        Lt[i * (kBW + 1) + k] = static_cast<T>(Dg[i * (kBW + 1) + k]);
+      }
+      __syncthreads();
+      // block-row interchanges outside the block and U12 = L11^-1 A12 in T, one column per
+      // thread: the column's w values are loaded in their interchanged order into registers
+      for (int j = tid; j < n; j += kBT) {
+        if (j >= k0 && j < k0 + w) continue;
+        T x[WB];
+#pragma unroll
+        for (int t = 0; t < WB; ++t)
+          if (t < w) x[t] = W[(long long)(k0 + s_src[t]) * n + j];
+        if (j >= k0 + w) {
+#pragma unroll
+          for (int k = 0; k < WB; ++k)
+            if (k < w) {
+#pragma unroll
+              for (int i = k + 1; i < WB; ++i)
+                if (i < w) x[i] = fma(-Lt[i * (kBW + 1) + k], x[k], x[i]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < WB; ++t)
+          if (t < w) W[(long long)(k0 + t) * n + j] = x[t];
+      }
+      // final multipliers of the rows below: (L21 with GEPP's column interchanges) * L11 in T,
+      // one row per thread in registers
       for (int r = k0 + w + tid; r < n; r += kBT) {
         T* row = W + (long long)r * n + k0;
-        for (int t = 0; t < w; ++t) {
-          const int p = ipiv[t];
-          if (p != t) { const T x = row[t]; row[t] = row[p]; row[p] = x; }
-        }
-        for (int c = 0; c < w; ++c) {                // row * L11 in T
-          T acc = row[c];
-          for (int i = c + 1; i < w; ++i) acc = fma(row[i], static_cast<T>(Dg[i * (kBW + 1) + c]), acc);
-          row[c] = acc;
-        }
+        T x[WB];
+#pragma unroll
+        for (int t = 0; t < WB; ++t)
+          if (t < w) x[t] = row[s_src[t]];
+#pragma unroll
+        for (int c = 0; c < WB; ++c)
+          if (c < w) {
+            T acc = x[c];
+#pragma unroll
+            for (int i = c + 1; i < WB; ++i)
+              if (i < w) acc = fma(x[i], Lt[i * (kBW + 1) + c], acc);
+            row[c] = acc;
+          }
       }
       __syncthreads();
     }
@@ -559,7 +670,7 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
       double* bcol = dv;                                   // the right-hand side, packed
       for (int i = tid; i < n; i += kBT) bcol[i] = Bp[(long long)i * ldb + c];
       __syncthreads();
-      batch_lu_solve<T>(W, n, perm, bcol, xv, s_red);
+      batch_lu_solve<T>(W, n, perm, bcol, xv, s_red, Dg);
       double eta = 0.0, eta_first = 0.0;
       int it = 0;
       for (;;) {
@@ -601,7 +712,7 @@ __global__ void __launch_bounds__(kBT) batch_kernel(BatchArgs<T> a) {
         double* rhs_r = V + 3 * a.nmax;
         for (int i = tid; i < n; i += kBT) rhs_r[i] = rv[i];
         __syncthreads();
-        batch_lu_solve<T>(W, n, perm, rhs_r, corr, s_red);
+        batch_lu_solve<T>(W, n, perm, rhs_r, corr, s_red, Dg);
         for (int i = tid; i < n; i += kBT) xv[i] += corr[i];
         __syncthreads();
         ++it;
@@ -636,14 +747,20 @@ cudaError_t launch_batch(int fp64, int grid, int rb, const BatchLaunch& L, cudaS
                         L.refine_max_iter, L.refine_target, L.nmax, static_cast<double*>(L.wsW),
                         static_cast<double*>(L.wsT), L.tmp_rows, L.wsV, L.wsI, L.status, L.iters,
                         L.eta0, L.eta, L.counter};
-    batch_kernel<double, 1><<<grid, kBT, smem, s>>>(a);   // two FP64 rows of L21 do not fit in registers
+    if (L.b <= 16) batch_kernel<double, 1, 16><<<grid, kBT, smem, s>>>(a);   // one FP64 row of L21 per pass
+    else batch_kernel<double, 1, kBW><<<grid, kBT, smem, s>>>(a);
   } else {
     BatchArgs<float> a{L.count, L.order, L.n, L.A, L.lda, L.nrhs, L.B, L.ldb, L.perm_out, L.b, L.tau, L.max_swaps,
                        L.refine_max_iter, L.refine_target, L.nmax, static_cast<float*>(L.wsW),
                        static_cast<float*>(L.wsT), L.tmp_rows, L.wsV, L.wsI, L.status, L.iters,
                        L.eta0, L.eta, L.counter};
-    if (rb == 2) batch_kernel<float, 2><<<grid, kBT, smem, s>>>(a);
-    else batch_kernel<float, 1><<<grid, kBT, smem, s>>>(a);
+    if (L.b <= 16) {
+      if (rb == 2) batch_kernel<float, 2, 16><<<grid, kBT, smem, s>>>(a);
+      else batch_kernel<float, 1, 16><<<grid, kBT, smem, s>>>(a);
+    } else {
+      if (rb == 2) batch_kernel<float, 2, kBW><<<grid, kBT, smem, s>>>(a);
+      else batch_kernel<float, 1, kBW><<<grid, kBT, smem, s>>>(a);
+    }
   }
   return cudaGetLastError();
 }
@@ -655,9 +772,12 @@ cudaError_t prepare_batch(int nmax, int b) {
   (void)nmax;
   (void)b;
   cudaError_t e;
-  if ((e = smem_optin(batch_kernel<double, 1>)) != cudaSuccess) return e;
-  if ((e = smem_optin(batch_kernel<float, 1>)) != cudaSuccess) return e;
-  return smem_optin(batch_kernel<float, 2>);
+  if ((e = smem_optin(batch_kernel<double, 1, 16>)) != cudaSuccess) return e;
+  if ((e = smem_optin(batch_kernel<double, 1, kBW>)) != cudaSuccess) return e;
+  if ((e = smem_optin(batch_kernel<float, 1, 16>)) != cudaSuccess) return e;
+  if ((e = smem_optin(batch_kernel<float, 1, kBW>)) != cudaSuccess) return e;
+  if ((e = smem_optin(batch_kernel<float, 2, 16>)) != cudaSuccess) return e;
+  return smem_optin(batch_kernel<float, 2, kBW>);
 }
 
 // Synthetic systems for the autotuner: iid entries from a counter hash (Weyl sequence,
