@@ -104,6 +104,7 @@ __device__ __forceinline__ double block_max(double v, double* s_red) {
 __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, int max_swaps,
                                   double* nrm, double* nref, int* pos, double* Rs, double* rdiag,
                                   BKey* s_w, int* swaps_out) {
+  __shared__ double s_refl[3];                   // alpha, beta, v0 of the current reflector
   const int tid = threadIdx.x, lane = tid & 31;
   const int tl = tid & (kTeam - 1), team = tid / kTeam;
   const unsigned tmask = 0xfu << (lane & ~3);
@@ -121,21 +122,44 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
         BKey d{dbits(fmax(nrm[r], 0.0)), pos[r], r};
         if (bbetter(d, c)) c = d;
       }
-    const BKey g = block_best_key(c, s_w);
+    // block argmax, then the reflector's scalars (a square root and a division on the
+    // FP64 pipe) formed once by warp 0 and broadcast with the reduction's second barrier
+    BKey g = c;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const BKey o = bshfl(g, off, 0xffffffffu);
+      if (bbetter(o, g)) g = o;
+    }
+    if (lane == 0) s_w[tid >> 5] = g;
+    __syncthreads();
+    g = s_w[0];
+    for (int k = 1; k < kBT / 32; ++k)
+      if (bbetter(s_w[k], g)) g = s_w[k];
     if (g.v == 0ull) return PRRP_ERR_SINGULAR;
     const int rw = g.k2, pw = g.k1;
     const double* xw = Ps + rw * sp;
-    const double x0 = xw[t];
-    const double normx = sqrt(__longlong_as_double(static_cast<long long>(g.v)));
-    const double alpha = (x0 >= 0.0) ? -normx : normx;
-    const double beta = 1.0 / (normx * (normx + fabs(x0)));
-    const double v0 = x0 - alpha;
+    if (tid < 32) {
+      const double x0 = xw[t];
+      const double normx = sqrt(__longlong_as_double(static_cast<long long>(g.v)));
+      const double alpha = (x0 >= 0.0) ? -normx : normx;
+      if (tid == 0) {
+        s_refl[0] = alpha;
+        s_refl[1] = 1.0 / (normx * (normx + abs_int(x0)));
+        s_refl[2] = x0 - alpha;
+        Rs[t * kBW + t] = alpha;
+      }
+    }
     for (int i = tid; i < t; i += kBT) Rs[i * kBW + t] = xw[i];
-    if (tid == 0) Rs[t * kBW + t] = alpha;
+    __syncthreads();
+    const double beta = s_refl[1], v0 = s_refl[2];
     // the winner row's values are read by every team below; it is itself not updated
     for (int r = team; r < m; r += kBTeams) {
       const int pr = pos[r];
-      if (pr < t || r == rw) continue;
+      if (r == rw) {                                 // the winner takes position t
+        if (tl == 0) pos[r] = t;
+        continue;
+      }
+      if (pr < t) continue;
       double* x = Ps + r * sp;
       double sd = 0.0;
       for (int i = t + tl; i < w; i += kTeam) sd = fma(i == t ? v0 : xw[i], x[i], sd);
@@ -158,8 +182,6 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
       __syncwarp(tmask);
       if (tl == 0) { nrm[r] = n2; pos[r] = (pr == t) ? pw : pr; }
     }
-    __syncthreads();
-    if (tid == 0) pos[rw] = t;
     __syncthreads();
   }
   for (int i = tid; i < w; i += kBT) rdiag[i] = 1.0 / Rs[i * kBW + i];
@@ -345,6 +367,7 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
   __shared__ BKey s_w[kBT / 32];
   __shared__ double s_red[kBT / 32];
   __shared__ int s_sys, s_status, s_np;
+  __shared__ double s_rp;                           // reciprocal of the current GEPP pivot
   __shared__ double Rs[kBW * kBW];
   __shared__ double rdiag[kBW];
   __shared__ int ipiv[kBW];
@@ -557,6 +580,7 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
             if (v > bv) { bv = v; p = i; }
           }
           ipiv[t] = bv > 0ull ? p : -1;
+          s_rp = bv > 0ull ? 1.0 / Dg[p * (kBW + 1) + t] : 0.0;   // once for the CTA
         }
         __syncthreads();
         const int p = ipiv[t];
@@ -571,7 +595,7 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
             Dg[p * (kBW + 1) + j] = x;
           }
         __syncthreads();
-        const double rp = 1.0 / Dg[t * (kBW + 1) + t];
+        const double rp = s_rp;
         for (int e = tid; e < (w - t - 1) * (w - t); e += kBT) {
           const int i = t + 1 + e / (w - t), j = t + e % (w - t);
           const double l = Dg[i * (kBW + 1) + t] * rp;
