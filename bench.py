@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -267,6 +268,33 @@ def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=
                         f"{'BF16X3' if prec == 2 else 'TF32'} Schur update + FP64 refinement", "runs": out}
 
 
+def wilkinson_check(prrp, ctx, torch, dev, n=2048, taus=2.0):
+    """The n = 2048 Wilkinson matrix (1 on the diagonal, -1 strictly below, 1 in the last
+    column), on which GEPP grows as 2^(n-1): LU_PRRP's growth factor against the bound
+    (1 + tau b)^(n/b) of Section 2.2 (as log10), the backward error ||PA - LU||_F / ||A||_F
+    against 64 n 2^-53, and the refined solve's eta, for b = 64 and b = 16."""
+    import prrp_inputs as pi
+    A0 = torch.from_numpy(pi.wilkinson(n)).to(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(2048)
+    B0 = torch.randn(n, 1, dtype=torch.float64, device=dev, generator=g)
+    out = {}
+    for b in (64, 16):
+        A = A0.clone()
+        F = prrp.prrp_factor(ctx, A, b=b, tau=taus)
+        st = F.stats()
+        perm = torch.from_numpy(F.perm().astype(np.int64)).to(dev)
+        L = torch.tril(A, -1) + torch.eye(n, dtype=torch.float64, device=dev)
+        res = float(torch.linalg.norm(A0[perm] - L @ torch.triu(A)) / torch.linalg.norm(A0))
+        B = B0.clone()
+        info = prrp.prrp_solve(ctx, F, B, A_orig=A0)
+        F.close()
+        out[f"b={b}"] = {"growth": st["growth"], "log10_growth_bound": (n / b) * math.log10(1 + taus * b),
+                         "residual": res, "residual_bound": 64 * n * 2.0 ** -53, "eta": info["eta"],
+                         "swaps": st["swaps"]}
+    return {"workload": f"Wilkinson matrix n={n}, tau={taus:g}", "runs": out}
+
+
 def form_update(prrp, ctx, torch, dev, n=16384, k=64, reps=5):
     """The Schur update alone (Algorithm 1, line 7) at the first trailing shape of the
     factorization: C (m x m, m = n - k, FP64, 2 GB at n = 16384, far above L2) -= L (m x k)
@@ -491,6 +519,7 @@ def run_ours(args) -> None:
     e2e_s = time.perf_counter() - t0
     (e2e_s,) = reduce_max([e2e_s], dist, dev)
 
+    wilk = wilkinson_check(prrp, ctx, torch, dev) if rank == 0 and world == 1 else None
     forms = {}
     if rank == 0 and world == 1 and not args.no_forms:
         forms["update"] = form_update(prrp, ctx, torch, dev)
@@ -541,6 +570,8 @@ def run_ours(args) -> None:
         }
         if cpu:
             out["cpu_baseline"] = cpu
+        if wilk:
+            out["wilkinson_2048"] = wilk
         if forms:
             out["forms"] = forms
         print(json.dumps(out), flush=True)
