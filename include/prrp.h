@@ -55,7 +55,11 @@ typedef enum {
   PRRP_FP64 = 0,   /* Schur update and TRSM in FP64 (DFMA) */
   PRRP_TF32 = 1,   /* Schur update on tcgen05 tensor cores in TF32, FP32 accumulation */
   PRRP_BF16X3 = 2, /* Schur update on tcgen05 as 3-term split BF16, FP32 accumulation */
-  PRRP_FP32 = 3    /* FP32 factor (batched path) */
+  PRRP_FP32 = 3,   /* FP32 factor (batched path) */
+  PRRP_FP64_EMU = 4 /* Schur update to FP64 accuracy on the BF16 tensor cores: every operand
+                       line cut into 8 signed base-128 digits under a power-of-two scale,
+                       the 36 leading digit products accumulated exactly in FP32, assembled
+                       exactly in 64-bit integers (b <= 64); the rest of the path in FP64 */
 } prrp_precision;
 
 typedef struct {
@@ -114,7 +118,9 @@ prrp_status prrp_destroy(prrp_ctx* ctx);
  *   6. the rows below the block receive the final L21 Pi_jj L11, so that on return dA holds
  *      the ordinary unit-lower L (strictly below the diagonal) and U (on and above it).
  * With prec = PRRP_TF32 or PRRP_BF16X3, steps 4, 5 (U12, through an FP32 inverse of L11)
- * and 6 run on the tensor cores; the pivot choices of steps 1 and 5 stay FP64.
+ * and 6 run on the tensor cores; the pivot choices of steps 1 and 5 stay FP64.  With
+ * prec = PRRP_FP64_EMU only step 4 runs on the tensor cores, to FP64 accuracy (b <= 64,
+ * UNSUPPORTED otherwise), and the factors serve like FP64 ones.
  * n = 0 is a no-op.  dA is overwritten; *F receives a handle holding the permutation and
  * statistics (and a reference to dA, which must stay alive while F is used).
  * Errors: INVALID_ARG, NONFINITE (checked before any write to dA), SINGULAR (dA then holds
@@ -279,7 +285,8 @@ prrp_status prrp_panel_select(prrp_ctx* ctx, int m, int w, const double* dP, int
 /*
  * prrp_schur_update - step 4 alone: C -= L * U with C m x n (ldc), L m x k (ldl),
  * U k x n (ldu), 1 <= k <= 128, all row-major device pointers, computed in `prec`
- * (PRRP_FP64 uses DFMA; PRRP_TF32 / PRRP_BF16X3 use tcgen05 with FP32 accumulation).
+ * (PRRP_FP64 uses DFMA; PRRP_TF32 / PRRP_BF16X3 use tcgen05 with FP32 accumulation;
+ * PRRP_FP64_EMU uses tcgen05 on exact BF16 digits for an FP64-accurate result, k <= 64).
  * In the tensor-core precisions C may alias L or U (the operands are split into the
  * context's workspace before C is written), which is how the factorization runs U12 and
  * the final multipliers (steps 5-6) on the tensor cores; in PRRP_FP64 they must not overlap.

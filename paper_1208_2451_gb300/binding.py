@@ -25,7 +25,7 @@ STATUS = {0: "PRRP_OK", 1: "PRRP_ERR_INVALID_ARG", 2: "PRRP_ERR_SINGULAR", 3: "P
 PRRP_OK, PRRP_ERR_INVALID_ARG, PRRP_ERR_SINGULAR, PRRP_ERR_NONFINITE = 0, 1, 2, 3
 PRRP_ERR_OOM, PRRP_ERR_CUDA, PRRP_ERR_TIMEOUT, PRRP_ERR_SWAP_LIMIT = 4, 5, 6, 7
 PRRP_ERR_NOT_CONVERGED, PRRP_ERR_BUSY, PRRP_ERR_UNSUPPORTED = 8, 9, 10
-PRRP_FP64, PRRP_TF32, PRRP_BF16X3, PRRP_FP32 = 0, 1, 2, 3
+PRRP_FP64, PRRP_TF32, PRRP_BF16X3, PRRP_FP32, PRRP_FP64_EMU = 0, 1, 2, 3, 4
 
 
 class prrp_opts(C.Structure):

@@ -232,7 +232,7 @@ prrp_status check_opts(const prrp_opts* o) {
   if (o->b < 1 || o->b > kMaxW) return PRRP_ERR_INVALID_ARG;
   if (!(o->tau >= 1.0)) return PRRP_ERR_INVALID_ARG;
   if (o->max_swaps < 0) return PRRP_ERR_INVALID_ARG;
-  if (o->prec < PRRP_FP64 || o->prec > PRRP_FP32) return PRRP_ERR_INVALID_ARG;
+  if (o->prec < PRRP_FP64 || o->prec > PRRP_FP64_EMU) return PRRP_ERR_INVALID_ARG;
   if (o->refine_max_iter < 0) return PRRP_ERR_INVALID_ARG;
   return PRRP_OK;
 }
@@ -404,7 +404,7 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
   if (n < 0 || lda < std::max(n, 1) || (n > 0 && !dA)) return PRRP_ERR_INVALID_ARG;
   prrp_status ps = check_opts(&o);
   if (ps != PRRP_OK) return ps;
-  if (o.prec == PRRP_FP32) return PRRP_ERR_UNSUPPORTED;
+  if (o.prec == PRRP_FP32 || (o.prec == PRRP_FP64_EMU && o.b > 64)) return PRRP_ERR_UNSUPPORTED;
   if (n > 65536) return PRRP_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaSetDevice(ctx->device));
@@ -457,7 +457,7 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
     return fail(ps);
   // a7 on the tensor cores in the low-precision modes: U12 (w x nc) and the multipliers
   // ((m - w) x w) share one workspace on the block stream
-  const bool tc_a7 = o.prec != PRRP_FP64;
+  const bool tc_a7 = o.prec == PRRP_TF32 || o.prec == PRRP_BF16X3;
   if (tc_a7) {
     const size_t ws3 = std::max(tc_workspace_bytes(o.prec, b, n, b), tc_workspace_bytes(o.prec, n, b, b));
     if ((ps = grow(ctx, &ctx->tcws3, &ctx->tcws3_cap, ws3)) != PRRP_OK) return fail(ps);
@@ -746,7 +746,7 @@ prrp_status prrp_solve(prrp_ctx* ctx, const prrp_factors* F, const double* dA_or
   const bool refine = dA_orig != nullptr;
   // factors from a low-precision Schur update are only about FP32-accurate: with the FP64
   // residual of the refinement, FP32 substitution converges as fast and costs far less
-  const bool low = refine && F->opts.prec != PRRP_FP64;
+  const bool low = refine && (F->opts.prec == PRRP_TF32 || F->opts.prec == PRRP_BF16X3);
   if (refine) CK(launch_copy_rows(dB, ldb, B0, nrhs, n, nrhs, s));
   if (low) {
     if ((ps = solve_into32(ctx, F, dB, ldb, nrhs, s)) != PRRP_OK) return ps;
@@ -1039,7 +1039,9 @@ prrp_status prrp_schur_update(prrp_ctx* ctx, int m, int n, int k, const double* 
       ldc < std::max(n, 1))
     return PRRP_ERR_INVALID_ARG;
   if (m > 0 && n > 0 && (!dL || !dU || !dC)) return PRRP_ERR_INVALID_ARG;
-  if (prec != PRRP_FP64 && prec != PRRP_TF32 && prec != PRRP_BF16X3) return PRRP_ERR_UNSUPPORTED;
+  if (prec != PRRP_FP64 && prec != PRRP_TF32 && prec != PRRP_BF16X3 && prec != PRRP_FP64_EMU)
+    return PRRP_ERR_UNSUPPORTED;
+  if (prec == PRRP_FP64_EMU && k > 64) return PRRP_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaSetDevice(ctx->device));
   CK(cudaMemsetAsync(ctx->st, 0, sizeof(DevState), s));

@@ -510,14 +510,14 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D map over a [slices * rows_pad] x kpad row-major operand, box = 128 bytes x 128 rows.
-bool make_map(CUtensorMap* m, void* base, int mode, int rows_total, int kpad) {
+// 2-D map over a [slices * rows_pad] x kpad row-major operand, box = 128 bytes x box_rows.
+bool make_map(CUtensorMap* m, void* base, int mode, int rows_total, int kpad, int box_rows = 128) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const int eb = mode == 0 ? 4 : 2;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(kpad), static_cast<cuuint64_t>(rows_total)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(kpad) * eb};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / eb), 128};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / eb), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, mode == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base,
                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -580,9 +580,262 @@ cudaError_t launch_tc_mode(int M, int N, int K, const double* L, long long ldl, 
   return launch_tc_kernel<MODE, 0>(ma, mb, ma, M, N, kblocks, Mpad, Npad, C, ldc, st, track, s);
 }
 
+
+// ---------------------------------------------------------------- FP64-accurate update
+//
+// C -= L U to FP64 accuracy on the BF16 tensor cores by an exact fixed-point split (the
+// Ozaki scheme).  Row r of L is scaled by 2^-e_r, e_r the least power of two above the
+// row's max |l|, and cut into kOzS signed base-128 digits:
+//     l_rk = 2^e_r sum_p L_p[r, k] 128^-(p+1),   |L_0| <= 128,  |L_p| <= 64 (p >= 1),
+// leaving under 2^-57 of the row's scale; columns of U likewise with 2^f_c.  Digits are
+// integers of at most 8 significant bits, so for K <= 64 every BF16 product L_p U_q is an
+// integer below 2^20 that FP32 accumulation holds exactly, and the products of one
+// diagonal d = p + q share a TMEM accumulator (below 2^22, still exact).  The diagonals
+// d <= kOzS - 1 (36 products) are kept; the dropped ones and the digits' remainders are
+// below 2^-53 sum_k |l_rk| |u_kc| in practice.  The epilogue assembles
+//     sum_d acc_d 128^(7 - d) = 128 T + acc_7,   T = sum_{d <= 6} acc_d 128^(6 - d) (< 2^63)
+// exactly in 64-bit integers and applies it with the scale 2^(e_r + f_c - 63): three FP64
+// operations per element of C against 2K on the FP64 pipe.
+constexpr int kOzS = 8;                   // digits per operand
+constexpr int kOzBN = 64;                 // tile columns: kOzS accumulators x 64 = 512 TMEM columns
+constexpr int kOzEpi = 8;                 // epilogue warps: 4 TMEM lane quarters x 2 column halves
+constexpr int kOzThreads = 64 + 32 * kOzEpi;
+constexpr int kOzTileA = kBM * 128;       // one digit slice of L: 128 rows x 64 BF16
+constexpr int kOzTileB = kOzBN * 128;     // one digit slice of U: 64 rows x 64 BF16
+constexpr int kOzStage = kOzS * (kOzTileA + kOzTileB);   // every slice of a tile: 192 KB
+constexpr int kOzSmem = kOzStage + 1024;
+static_assert(kOzSmem + 512 <= kSmemOptin, "one operand stage");
+constexpr uint32_t kOzIdesc = make_idesc(1u, kBM, kOzBN);
+
+// The integer held by a float of magnitude below 2^22, by integer operations.
+__device__ __forceinline__ int f2i_small(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
+
+// 2^k as a double (0 below the normal range: an underflowing product is dropped).
+__device__ __forceinline__ double pow2i(int k) {
+  if (k < -1022) return 0.0;
+  if (k > 1023) k = 1023;
+  return __longlong_as_double(static_cast<long long>(k + 1023) << 52);
+}
+
+// BF16 bits of an integer-valued double with |d| <= 256 (at most 8 significant bits, so
+// the truncated mantissa is exact), by integer operations.
+__device__ __forceinline__ unsigned short d2bf16_int(double d) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d));
+  if ((u << 1) == 0ull) return 0;
+  const unsigned sign = static_cast<unsigned>(u >> 63);
+  const unsigned e = static_cast<unsigned>((u >> 52) & 0x7FFu) - 1023u + 127u;
+  const unsigned mant = static_cast<unsigned>((u >> 45) & 0x7Fu);
+  return static_cast<unsigned short>((sign << 15) | (e << 7) | mant);
+}
+
+// Digits of the operand lines: line r (a row of L, or with COLS a column of U) of K <= 64
+// entries, one warp per line.  dst[p][r][k] (rows_pad x 64 BF16 per slice); exps[r] = e_r.
+template <bool COLS>
+__global__ void ozaki_split_kernel(const double* __restrict__ src, long long ld, int rows, int K, int rows_pad,
+                                   unsigned short* __restrict__ dst, int* __restrict__ exps) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows_pad; r += gridDim.x * wpb) {
+    double x[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      x[h] = (r < rows && k < K) ? (COLS ? src[static_cast<long long>(k) * ld + r] : src[static_cast<long long>(r) * ld + k])
+                                 : 0.0;
+    }
+    unsigned long long m = max_bits(abs_bits(x[0]), abs_bits(x[1]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, off));
+    // max |x| < 2^e; a line whose max is 2^1023 or more is scaled by 2^-1023 (digits up to
+    // 256, still exact, but such entries lie outside any usable factorization anyway)
+    int e = m == 0ull ? 0 : static_cast<int>((m >> 52) & 0x7FFu) - 1022;
+    e = min(max(e, -1021), 1023);
+    if (lane == 0 && r < rows) exps[r] = e;
+    const double sc = pow2i(-e);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      double y = x[h] * sc;                     // exact; |y| < 1
+      unsigned short* out = dst + static_cast<long long>(r) * 64 + lane + 32 * h;
+#pragma unroll
+      for (int p = 0; p < kOzS; ++p) {
+        y *= 128.0;                             // exact
+        const double d = rint(y);
+        y -= d;                                 // exact
+        out[static_cast<long long>(p) * rows_pad * 64] = d2bf16_int(d);
+      }
+    }
+  }
+}
+
+// Persistent, warp-specialized, one 128 x 64 tile at a time: warp 0 (one lane) loads every
+// digit slice of the tile with TMA into the one operand stage; warp 1 (one lane) issues the
+// 36 slice products (4 MMAs of K = 16 each) into the 8 diagonal accumulators; warps 2..9
+// assemble and apply them.  The next tile's operands load while the epilogue drains.
+__global__ void __launch_bounds__(kOzThreads, 1) ozaki_update_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int Mpad,
+    int Npad, const int* __restrict__ rexp, const int* __restrict__ cexp, double* __restrict__ C, long long ldc,
+    DevState* st, int track) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full, empty, accf, acce;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  if (dev_status(st) != 0) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = base;
+  uint8_t* sB = base + kOzS * kOzTileA;
+  const int tiles_n = Npad / kOzBN, tiles = (Mpad / kBM) * tiles_n;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kOzS * kOzBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    mbar_init(&full, 1);
+    mbar_init(&empty, 1);
+    mbar_init(&accf, 1);
+    mbar_init(&acce, kOzEpi);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  unsigned long long cmax_bits = 0ull;
+  int p_it = 0;                                  // tiles whose operands were requested
+
+  if (warp == 0) {
+    if (lane == 0) {                                         // ---- TMA producer
+      for (int tile = blockIdx.x; tile < tiles && !s_fail; tile += gridDim.x, ++p_it) {
+        const int bm = (tile / tiles_n) * kBM, bn = (tile % tiles_n) * kOzBN;
+        if (!mbar_wait_bounded(&empty, (p_it & 1) ^ 1)) { s_fail = 1; break; }
+        mbar_expect_tx(&full, kOzStage);
+        for (int sl = 0; sl < kOzS; ++sl) {
+          tma_load_2d(sA + sl * kOzTileA, &tmA, 0, sl * Mpad + bm, &full);
+          tma_load_2d(sB + sl * kOzTileB, &tmB, 0, sl * Npad + bn, &full);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {                                         // ---- MMA issuer
+      int it = 0;
+      for (int tile = blockIdx.x; tile < tiles && !s_fail; tile += gridDim.x, ++it) {
+        if (!mbar_wait_bounded(&acce, (it & 1) ^ 1)) { s_fail = 1; break; }
+        if (!mbar_wait_bounded(&full, it & 1)) { s_fail = 1; break; }
+        tc_fence_after();
+        for (int p = 0; p < kOzS; ++p) {
+          const uint64_t ad = sw128_desc(smem_u32(sA + p * kOzTileA));
+          for (int q = 0; p + q < kOzS; ++q) {
+            const uint64_t bd = sw128_desc(smem_u32(sB + q * kOzTileB));
+            const uint32_t dt = tmem + static_cast<uint32_t>((p + q) * kOzBN);
+            // p = 0 opens diagonal q; later p add to it
+#pragma unroll
+            for (int k = 0; k < 4; ++k) umma<1>(dt, ad + 2 * k, bd + 2 * k, kOzIdesc, (p | k) != 0);
+          }
+        }
+        umma_commit(&empty);                                 // operand stage free
+        umma_commit(&accf);                                  // accumulators ready
+      }
+    }
+  } else {                                                   // ---- epilogue warps
+    // a warp reads TMEM lanes 32 (warp % 4) .. + 31: warps 2..9 cover each lane quarter
+    // twice, once per 32-column half of the tile
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    int tcount = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tcount) {
+      const int bm = (tile / tiles_n) * kBM, bn = (tile % tiles_n) * kOzBN;
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&accf, tcount & 1))) { s_fail = 1; break; }
+      tc_fence_after();
+      const uint32_t tb = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(h * 32);
+      long long T[32];
+      uint32_t r[32];
+      tmem_ld32(tb, r);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) T[j] = f2i_small(__uint_as_float(r[j]));
+#pragma unroll 1
+      for (int d = 1; d < kOzS - 1; ++d) {
+        tmem_ld32(tb + static_cast<uint32_t>(d * kOzBN), r);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) T[j] = (T[j] << 7) + f2i_small(__uint_as_float(r[j]));
+      }
+      tmem_ld32(tb + static_cast<uint32_t>((kOzS - 1) * kOzBN), r);   // the last diagonal
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce);                     // accumulators free again
+      const int row = bm + q * 32 + lane, c0 = bn + h * 32;
+      if (row < M && c0 < N) {
+        const int er = rexp[row] - 63;
+        double* cp = C + static_cast<long long>(row) * ldc + c0;
+        const int nc = min(32, N - c0);
+#pragma unroll
+        for (int j0 = 0; j0 < 32; j0 += 16) {
+          double cv[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (j0 + j < nc) cv[j] = __ldcs(cp + j0 + j);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (j0 + j < nc) {
+              const double val = fma(static_cast<double>(T[j0 + j]), 128.0, f2d_int(__uint_as_float(r[j0 + j])));
+              const double v = fma(-val, pow2i(er + __ldg(cexp + c0 + j0 + j)), cv[j]);
+              __stcs(cp + j0 + j, v);
+              cmax_bits = max_bits(cmax_bits, abs_bits(v));
+            }
+        }
+      }
+    }
+  }
+  if (track && warp >= 2) {
+    for (int off = 16; off > 0; off >>= 1) cmax_bits = max_bits(cmax_bits, __shfl_xor_sync(0xffffffffu, cmax_bits, off));
+    if (lane == 0) atomicMax(track == 2 ? &st->umax_bits : &st->gmax_bits, cmax_bits);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0 && lane == 0 && s_fail && p_it > 0) mbar_wait_bounded(&full, (p_it - 1) & 1);   // loads in flight
+  if (s_fail && tid == 0) set_error(st, PRRP_ERR_TIMEOUT);
+  __syncwarp();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOzS * kOzBN) : "memory");
+}
+
+size_t ozaki_ws_bytes(int M, int N) {
+  const size_t Mpad = static_cast<size_t>((M + kBM - 1) / kBM) * kBM;
+  const size_t Npad = static_cast<size_t>((N + kOzBN - 1) / kOzBN) * kOzBN;
+  return kOzS * 128 * (Mpad + Npad) + 4 * (Mpad + Npad) + 2048;
+}
+
+cudaError_t launch_ozaki(int M, int N, int K, const double* L, long long ldl, const double* U, long long ldu,
+                         double* C, long long ldc, DevState* st, int track, void* ws, cudaStream_t s) {
+  if (K > 64) return cudaErrorInvalidValue;
+  const int Mpad = (M + kBM - 1) / kBM * kBM, Npad = (N + kOzBN - 1) / kOzBN * kOzBN;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  unsigned short* da = reinterpret_cast<unsigned short*>(w);
+  unsigned short* db = reinterpret_cast<unsigned short*>(w + static_cast<size_t>(kOzS) * 128 * Mpad);
+  int* rexp = reinterpret_cast<int*>(w + static_cast<size_t>(kOzS) * 128 * (Mpad + Npad));
+  int* cexp = rexp + Mpad;
+  ozaki_split_kernel<false><<<std::min((Mpad + 7) / 8, 152 * 8), 256, 0, s>>>(L, ldl, M, K, Mpad, da, rexp);
+  ozaki_split_kernel<true><<<std::min((Npad + 7) / 8, 152 * 8), 256, 0, s>>>(U, ldu, N, K, Npad, db, cexp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, da, 1, kOzS * Mpad, 64, kBM) || !make_map(&mb, db, 1, kOzS * Npad, 64, kOzBN))
+    return cudaErrorInvalidValue;
+  if ((e = smem_optin(ozaki_update_kernel)) != cudaSuccess) return e;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = (Mpad / kBM) * (Npad / kOzBN);
+  ozaki_update_kernel<<<std::min(tiles, sms), kOzThreads, kOzSmem, s>>>(ma, mb, M, N, Mpad, Npad, rexp, cexp, C,
+                                                                         ldc, st, track);
+  return cudaGetLastError();
+}
 }  // namespace
 
 size_t tc_workspace_bytes(int prec, int M, int N, int K) {
+  if (prec == PRRP_FP64_EMU) return ozaki_ws_bytes(M, N);
   const int mode = prec == PRRP_TF32 ? 0 : 1;
   const int ns = mode == 0 ? 1 : 3, eb = mode == 0 ? 4 : 2;
   const size_t kpad = static_cast<size_t>((K + 63) / 64) * 64;
@@ -595,6 +848,7 @@ cudaError_t launch_tc_update(int prec, int M, int N, int K, const double* L, lon
                              long long ldu, double* C, long long ldc, DevState* st, int track, void* ws,
                              cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  if (prec == PRRP_FP64_EMU) return launch_ozaki(M, N, K, L, ldl, U, ldu, C, ldc, st, track, ws, s);
   const int mode = prec == PRRP_TF32 ? 0 : 1;
   const int ns = mode == 0 ? 1 : 3, eb = mode == 0 ? 4 : 2;
   const size_t kpad = static_cast<size_t>((K + 63) / 64) * 64;
