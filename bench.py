@@ -63,10 +63,13 @@ def fracs(tflops: float, prec: int | None, b: int = 64) -> dict:
     batched form the FP32 SIMT FMA peak (152 SMs x 128 FMA/clk x 2 flop x 2070 MHz)."""
     pk = _peaks()
     out = {"of_fp64_pipe_peak": tflops / fp64_peak_tflops()}
-    if prec in (1, 2):
+    if prec in (1, 2, 4):
         hbm, bf16 = pk.get("hbm_gbs", 6800.0), pk.get("bf16_tflops", 1900.0)
-        tc = bf16 * 1.1 / 2.25 if prec == 1 else bf16 / 6
-        out["of_tc_update_roofline"] = tflops / min(hbm * 2 * b / 16 / 1000, tc)
+        tc = {1: bf16 * 1.1 / 2.25, 2: bf16 / 6, 4: bf16 / 36}[prec]
+        roof = min(hbm * 2 * b / 16 / 1000, tc)
+        if prec == 4:                      # the exact split's epilogue: 3 FP64 ops per entry
+            roof = min(roof, fp64_peak_tflops() / 2 / 3 * 2 * b)
+        out["of_tc_update_roofline"] = tflops / roof
     if prec == 3:
         out["of_fp32_simt_peak"] = tflops / (152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12)
     return out
@@ -264,8 +267,9 @@ def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=
         else:
             del A0, A, B0, B
         torch.cuda.empty_cache()
-    return {"workload": f"n={n}, b=64, tau=2, cond-controlled A, 4 RHS, "
-                        f"{'BF16X3' if prec == 2 else 'TF32'} Schur update + FP64 refinement", "runs": out}
+    upd = {1: "TF32", 2: "BF16X3", 4: "FP64-accurate (8-digit BF16 split)"}[prec]
+    mat = "cond-controlled A" if any(k > 0 for k in kappas) else "A iid N(0,1)"
+    return {"workload": f"n={n}, b=64, tau=2, {mat}, 4 RHS, {upd} Schur update + FP64 refinement", "runs": out}
 
 
 def wilkinson_check(prrp, ctx, torch, dev, n=2048, taus=2.0):
@@ -313,7 +317,8 @@ def form_update(prrp, ctx, torch, dev, n=16384, k=64, reps=5):
     Cm = torch.randn(m, m, dtype=torch.float64, device=dev, generator=g)
     prrp.prrp_ctx_set_timing(ctx, True)
     out = {}
-    for prec, name, tc_peak in ((1, "tf32", bf16 * 1.1 / 2.25), (2, "bf16x3", bf16 / 6), (0, "fp64", None)):
+    for prec, name, tc_peak in ((1, "tf32", bf16 * 1.1 / 2.25), (2, "bf16x3", bf16 / 6), (4, "fp64_emu", bf16 / 36),
+                                (0, "fp64", None)):
         best = None
         for _ in range(reps + 1):
             prrp.prrp_ctx_kernel_stats(ctx, reset=True)
@@ -323,6 +328,15 @@ def form_update(prrp, ctx, torch, dev, n=16384, k=64, reps=5):
         tf = 2.0 * m * m * k / best / 1e9
         if tc_peak is None:
             peak, bound, src = fp64_peak_tflops(), "alu", "FP64 FMA pipe at 2070 MHz"
+        elif prec == 4:
+            # exact 8-digit split: 36 BF16 products on the tensor cores, and an epilogue of
+            # three FP64-pipe operations per entry of C (int64 -> double, two FMAs)
+            hb = hbm * 2 * k / 16 / 1000
+            ep = fp64_peak_tflops() / 2 / 3 * 2 * k          # DFMA slots/s / 3 per entry x 2k flop
+            peak = min(hb, tc_peak, ep)
+            bound = "alu" if peak == ep else ("hbm" if peak == hb else "tensor")
+            src = (f"min(HBM {hbm:g} GB/s x {2 * k}/16 flop/B, tensor {tc_peak:.0f} TFLOP/s (bf16 / 36 products), "
+                   f"FP64-pipe epilogue {ep:.1f} TFLOP/s (3 ops per entry)) of measured")
         else:
             hb = hbm * 2 * k / 16 / 1000
             peak, bound = min(hb, tc_peak), ("hbm" if hb < tc_peak else "tensor")
@@ -526,6 +540,7 @@ def run_ours(args) -> None:
         forms["mixed"] = form_mixed(prrp, ctx, torch, dev)
         forms["batched"] = form_batched(prrp, ctx, torch, dev)
         forms["served"] = form_served(prrp, ctx)
+        forms["fp64_emu"] = form_mixed(prrp, ctx, torch, dev, n=n, kappas=(0.0,), prec=4)
     if rank == 0:
         csum = clocks.summary()
         up = kstats["update"]
@@ -593,7 +608,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the mixed-precision, batched and served measurements")
-    ap.add_argument("--form", choices=["mixed", "batched", "served", "update"],
+    ap.add_argument("--form", choices=["mixed", "batched", "served", "update", "fp64_emu"],
                     help="run only one of the other forms and print its JSON")
     ap.add_argument("--count", type=int, default=4096,
                     help="--form batched: number of systems (smaller batches for profiling)")
@@ -625,7 +640,8 @@ def main():
               "batched": lambda: form_batched(prrp, ctx, torch, dev, count=args.count, dist=dist),
               "served": lambda: form_served(prrp, ctx),
               "update": lambda: form_update(prrp, ctx, torch, dev,
-                                            n=args.n if args.n != N_DEFAULT else 16384)}[args.form]
+                                            n=args.n if args.n != N_DEFAULT else 16384),
+              "fp64_emu": lambda: form_mixed(prrp, ctx, torch, dev, n=args.n, kappas=(0.0,), prec=4)}[args.form]
         out = fn()
         if dist is None or dist.get_rank() == 0:
             print(json.dumps({"form": args.form, **out}), flush=True)
