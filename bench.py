@@ -67,8 +67,8 @@ def fracs(tflops: float, prec: int | None, b: int = 64) -> dict:
         hbm, bf16 = pk.get("hbm_gbs", 6800.0), pk.get("bf16_tflops", 1900.0)
         tc = {1: bf16 * 1.1 / 2.25, 2: bf16 / 6, 4: bf16 / 36}[prec]
         roof = min(hbm * 2 * b / 16 / 1000, tc)
-        if prec == 4:                      # the exact split's epilogue: 3 FP64 ops per entry
-            roof = min(roof, fp64_peak_tflops() / 2 / 3 * 2 * b)
+        if prec == 4:                      # the exact split's epilogue: 2 FP64 ops per entry
+            roof = min(roof, fp64_peak_tflops() / 2 / 2 * 2 * b)
         out["of_tc_update_roofline"] = tflops / roof
     if prec == 3:
         out["of_fp32_simt_peak"] = tflops / (152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12)
@@ -330,13 +330,13 @@ def form_update(prrp, ctx, torch, dev, n=16384, k=64, reps=5):
             peak, bound, src = fp64_peak_tflops(), "alu", "FP64 FMA pipe at 2070 MHz"
         elif prec == 4:
             # exact 8-digit split: 36 BF16 products on the tensor cores, and an epilogue of
-            # three FP64-pipe operations per entry of C (int64 -> double, two FMAs)
+            # two FP64-pipe operations per entry of C (int64 -> double, one FMA)
             hb = hbm * 2 * k / 16 / 1000
-            ep = fp64_peak_tflops() / 2 / 3 * 2 * k          # DFMA slots/s / 3 per entry x 2k flop
+            ep = fp64_peak_tflops() / 2 / 2 * 2 * k          # DFMA slots/s / 2 per entry x 2k flop
             peak = min(hb, tc_peak, ep)
             bound = "alu" if peak == ep else ("hbm" if peak == hb else "tensor")
             src = (f"min(HBM {hbm:g} GB/s x {2 * k}/16 flop/B, tensor {tc_peak:.0f} TFLOP/s (bf16 / 36 products), "
-                   f"FP64-pipe epilogue {ep:.1f} TFLOP/s (3 ops per entry)) of measured")
+                   f"FP64-pipe epilogue {ep:.1f} TFLOP/s (2 ops per entry)) of measured")
         else:
             hb = hbm * 2 * k / 16 / 1000
             peak, bound = min(hb, tc_peak), ("hbm" if hb < tc_peak else "tensor")

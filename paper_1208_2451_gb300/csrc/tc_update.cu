@@ -593,9 +593,11 @@ cudaError_t launch_tc_mode(int M, int N, int K, const double* L, long long ldl, 
 // diagonal d = p + q share a TMEM accumulator (below 2^22, still exact).  The diagonals
 // d <= kOzS - 1 (36 products) are kept; the dropped ones and the digits' remainders are
 // below 2^-53 sum_k |l_rk| |u_kc| in practice.  The epilogue assembles
-//     sum_d acc_d 128^(7 - d) = 128 T + acc_7,   T = sum_{d <= 6} acc_d 128^(6 - d) (< 2^63)
-// exactly in 64-bit integers and applies it with the scale 2^(e_r + f_c - 63): three FP64
-// operations per element of C against 2K on the FP64 pipe.
+//     T = sum_d acc_d 2^(7 (7 - d) - 8)    (|T| < 2^62)
+// in 64-bit integers, exactly for d <= 5 and with the last two diagonals shifted down by
+// 1 and 8 bits (floor: under 2 units of T, i.e. 2^(e_r + f_c - 54)), and applies it with
+// the scale 2^(e_r + f_c - 55): one conversion and one FMA on the FP64 pipe per element
+// of C, against 2K for the plain product.
 constexpr int kOzS = 8;                   // digits per operand
 constexpr int kOzBN = 64;                 // tile columns: kOzS accumulators x 64 = 512 TMEM columns
 constexpr int kOzEpi = 8;                 // epilogue warps: 4 TMEM lane quarters x 2 column halves
@@ -756,18 +758,23 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_update_kernel(
 #pragma unroll
       for (int j = 0; j < 32; ++j) T[j] = f2i_small(__uint_as_float(r[j]));
 #pragma unroll 1
-      for (int d = 1; d < kOzS - 1; ++d) {
+      for (int d = 1; d < kOzS - 2; ++d) {                   // T = sum_{d <= 5} acc_d 128^(5 - d)
         tmem_ld32(tb + static_cast<uint32_t>(d * kOzBN), r);
 #pragma unroll
         for (int j = 0; j < 32; ++j) T[j] = (T[j] << 7) + f2i_small(__uint_as_float(r[j]));
       }
-      tmem_ld32(tb + static_cast<uint32_t>((kOzS - 1) * kOzBN), r);   // the last diagonal
+      tmem_ld32(tb + static_cast<uint32_t>((kOzS - 2) * kOzBN), r);   // diagonal 6: 2^-1
+#pragma unroll
+      for (int j = 0; j < 32; ++j) T[j] = (T[j] << 6) + (f2i_small(__uint_as_float(r[j])) >> 1);
+      tmem_ld32(tb + static_cast<uint32_t>((kOzS - 1) * kOzBN), r);   // diagonal 7: 2^-8
+#pragma unroll
+      for (int j = 0; j < 32; ++j) T[j] += f2i_small(__uint_as_float(r[j])) >> 8;
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce);                     // accumulators free again
       const int row = bm + q * 32 + lane, c0 = bn + h * 32;
       if (row < M && c0 < N) {
-        const int er = rexp[row] - 63;
+        const int er = rexp[row] - 55;
         double* cp = C + static_cast<long long>(row) * ldc + c0;
         const int nc = min(32, N - c0);
 #pragma unroll
@@ -779,8 +786,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_update_kernel(
 #pragma unroll
           for (int j = 0; j < 16; ++j)
             if (j0 + j < nc) {
-              const double val = fma(static_cast<double>(T[j0 + j]), 128.0, f2d_int(__uint_as_float(r[j0 + j])));
-              const double v = fma(-val, pow2i(er + __ldg(cexp + c0 + j0 + j)), cv[j]);
+              const double v = fma(-static_cast<double>(T[j0 + j]), pow2i(er + __ldg(cexp + c0 + j0 + j)), cv[j]);
               __stcs(cp + j0 + j, v);
               cmax_bits = max_bits(cmax_bits, abs_bits(v));
             }
