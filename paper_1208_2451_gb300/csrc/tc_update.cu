@@ -605,7 +605,8 @@ constexpr int kOzThreads = 64 + 32 * kOzEpi;
 constexpr int kOzTileA = kBM * 128;       // one digit slice of L: 128 rows x 64 BF16
 constexpr int kOzTileB = kOzBN * 128;     // one digit slice of U: 64 rows x 64 BF16
 constexpr int kOzStage = kOzS * (kOzTileA + kOzTileB);   // every slice of a tile: 192 KB
-constexpr int kOzSmem = kOzStage + 1024;
+constexpr int kOzXP = 9;                  // padded row (doubles) of an epilogue warp's 32 x 8 stage
+constexpr int kOzSmem = kOzStage + kOzEpi * 32 * kOzXP * 8 + 1024;
 static_assert(kOzSmem + 512 <= kSmemOptin, "one operand stage");
 constexpr uint32_t kOzIdesc = make_idesc(1u, kBM, kOzBN);
 
@@ -772,24 +773,39 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_update_kernel(
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce);                     // accumulators free again
-      const int row = bm + q * 32 + lane, c0 = bn + h * 32;
-      if (row < M && c0 < N) {
-        const int er = rexp[row] - 55;
-        double* cp = C + static_cast<long long>(row) * ldc + c0;
-        const int nc = min(32, N - c0);
+      // lane = row of the 32 x 32 block; C is updated through a 32 x 8 shared-memory stage
+      // per chunk of columns, so that a warp's load or store touches 4 rows x 8 columns
+      // (4 x 64 contiguous bytes) rather than 32 rows
+      const int row0 = bm + q * 32, c0 = bn + h * 32;
+      const int nrows = min(32, M - row0), ncols = min(32, N - c0);
+      if (nrows > 0 && ncols > 0) {
+        double* stg = reinterpret_cast<double*>(base + kOzStage) + (warp - 2) * 32 * kOzXP;
+        const int cl = lane & 7, rl = lane >> 3;          // this lane: column cl, rows rl + 4 i
+        int er[8];
 #pragma unroll
-        for (int j0 = 0; j0 < 32; j0 += 16) {
-          double cv[16];
+        for (int i = 0; i < 8; ++i) er[i] = rl + 4 * i < nrows ? __ldg(rexp + row0 + rl + 4 * i) - 55 : 0;
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (j0 + j < nc) cv[j] = __ldcs(cp + j0 + j);
+        for (int j0 = 0; j0 < 32; j0 += 8) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (j0 + j < nc) {
-              const double v = fma(-static_cast<double>(T[j0 + j]), pow2i(er + __ldg(cexp + c0 + j0 + j)), cv[j]);
-              __stcs(cp + j0 + j, v);
-              cmax_bits = max_bits(cmax_bits, abs_bits(v));
-            }
+          for (int jj = 0; jj < 8; ++jj) stg[lane * kOzXP + jj] = static_cast<double>(T[j0 + jj]);
+          __syncwarp();
+          const int col = c0 + j0 + cl;
+          if (j0 + cl < ncols) {
+            const int ec = __ldg(cexp + col);
+            double cv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (rl + 4 * i < nrows) cv[i] = __ldcs(C + static_cast<long long>(row0 + rl + 4 * i) * ldc + col);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (rl + 4 * i < nrows) {
+                const int r = rl + 4 * i;
+                const double v = fma(-stg[r * kOzXP + cl], pow2i(er[i] + ec), cv[i]);
+                __stcs(C + static_cast<long long>(row0 + r) * ldc + col, v);
+                cmax_bits = max_bits(cmax_bits, abs_bits(v));
+              }
+          }
+          __syncwarp();
         }
       }
     }
