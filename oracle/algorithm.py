@@ -20,7 +20,7 @@ What it computes, in the paper's order:
 * ``lu_solve``, ``refine``   forward/back substitution and FP64 iterative refinement
                     (Section 2.3 solver tests; Section 3.3 refinement).
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
   g_W is the largest entry of A and of the block Schur complements A^(k) after each panel
   update, over max|A|: the a^(k)_ij of Section 2.2 are the entries after k block steps,
   whose induction gives (1 + tau b)^(n/b); the diagonal-block GEPP is bounded separately

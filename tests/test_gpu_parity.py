@@ -1,6 +1,6 @@
 """GPU parity: the CUDA LU_PRRP path (through the C ABI) against the CPU oracle.
 
-Bar (the benchmark spec's tolerances):
+Bar:
 * pivots: the permutation is identical whenever the oracle's smallest decision margin
   (QRCP top-two gap, swap-test distance to tau, swap-choice gap, GEPP gap) exceeds 1e-8;
   otherwise the GPU's own pivots must be a valid LU_PRRP selection, checked in FP64 on the
