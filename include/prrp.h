@@ -48,7 +48,7 @@ typedef enum {
   PRRP_ERR_SWAP_LIMIT = 7,    /* a panel needed more than opts.max_swaps interchanges */
   PRRP_ERR_NOT_CONVERGED = 8, /* iterative refinement stopped above its target */
   PRRP_ERR_BUSY = 9,          /* server: request can never fit the admission budget */
-  PRRP_ERR_UNSUPPORTED = 10   /* size or option outside what this build supports */
+  PRRP_ERR_UNSUPPORTED = 10   /* size or option outside what the library supports */
 } prrp_status;
 
 typedef enum {
