@@ -613,9 +613,11 @@ constexpr uint32_t kOzIdesc = make_idesc(1u, kBM, kOzBN);
 // The integer held by a float of magnitude below 2^22, by integer operations.
 __device__ __forceinline__ int f2i_small(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
 
-// 2^k as a double (0 below the normal range: an underflowing product is dropped).
+// 2^k as a double: subnormal down to 2^-1074, 0 below (an underflowing product is dropped),
+// 2^1023 above the range.
 __device__ __forceinline__ double pow2i(int k) {
-  if (k < -1022) return 0.0;
+  if (k < -1074) return 0.0;
+  if (k < -1022) return __longlong_as_double(1ll << (k + 1074));
   if (k > 1023) k = 1023;
   return __longlong_as_double(static_cast<long long>(k + 1023) << 52);
 }
@@ -649,8 +651,9 @@ __global__ void ozaki_split_kernel(const double* __restrict__ src, long long ld,
     unsigned long long m = max_bits(abs_bits(x[0]), abs_bits(x[1]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, off));
-    // max |x| < 2^e; a line whose max is 2^1023 or more is scaled by 2^-1023 (digits up to
-    // 256, still exact, but such entries lie outside any usable factorization anyway)
+    // max |x| < 2^e (the scale 2^-e is exact, subnormal for e = 1023); a line whose max
+    // is 2^1023 or more is scaled by 2^-1023 only, its leading digits reach 256 and the
+    // exactness bounds no longer hold: such entries are outside this mode's range
     int e = m == 0ull ? 0 : static_cast<int>((m >> 52) & 0x7FFu) - 1022;
     e = min(max(e, -1021), 1023);
     if (lane == 0 && r < rows) exps[r] = e;
