@@ -6,9 +6,10 @@ Only tests/, __graft_entry__.smoke() and bench.py's CPU legs (``cpu_baseline`` a
 """
 from .algorithm import (LUResult, NonFiniteError, PanelResult, SingularError, SwapLimitError,
                       eta, householder_qr, lu_prrp, lu_solve, qrcp, refine, selection_multipliers, strong_rrqr, unpack)
+from .calu import CALUResult, calu_growth_bound_log10, calu_prrp
 from . import metrics
 
 __all__ = ["LUResult", "NonFiniteError", "PanelResult", "SingularError", "SwapLimitError", "eta",
            "householder_qr", "lu_prrp", "lu_solve", "qrcp", "refine", "selection_multipliers",
-           "strong_rrqr", "unpack",
+           "strong_rrqr", "unpack", "CALUResult", "calu_prrp", "calu_growth_bound_log10",
            "metrics"]
