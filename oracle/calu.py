@@ -46,7 +46,7 @@ class CALUResult:
     height: int               # largest reduction-tree height over the panels
     first_growth: float       # max |A^(1)| / max |A| after the first panel
     panel_l21: list = field(default_factory=list)   # max |L21| per panel
-    nodes: list = field(default_factory=list)   # per node: (B = node matrix, selected local indices)
+    nodes: list = field(default_factory=list)   # per node: (panel, level, B = node matrix, selected)
 
 
 def calu_prrp(A: np.ndarray, b: int = 64, tau: float = 2.0, leaf_rows: int = 256,
@@ -72,7 +72,7 @@ def calu_prrp(A: np.ndarray, b: int = 64, tau: float = 2.0, leaf_rows: int = 256
         w = min(b, n - k0)
         m = n - k0
 
-        def node(cpos):
+        def node(cpos, level_no):
             """Strong RRQR of the node matrix (the rows at panel positions cpos); its
             transpositions move whole rows, so the selected rows take cpos[:w]."""
             nonlocal swaps
@@ -81,7 +81,7 @@ def calu_prrp(A: np.ndarray, b: int = 64, tau: float = 2.0, leaf_rows: int = 256
             margins.extend(pr.qrcp_margins + pr.test_margins + pr.choice_margins)
             swaps += pr.swaps
             if keep_nodes:
-                nodes_out.append((B, np.array(pr.order[:w])))
+                nodes_out.append((k0 // b, level_no, B, np.array(pr.order[:w])))
             for (a, c) in pr.transpositions:
                 if a != c:
                     ra, rc = k0 + cpos[a], k0 + cpos[c]
@@ -95,12 +95,12 @@ def calu_prrp(A: np.ndarray, b: int = 64, tau: float = 2.0, leaf_rows: int = 256
         for i in range(nleaf):
             r0 = i * leaf_rows
             r1 = m if i == nleaf - 1 else (i + 1) * leaf_rows
-            level.append(node(list(range(r0, r1))))
+            level.append(node(list(range(r0, r1)), 0))
         # 2. binary reduction tree
         h = 0
         while len(level) > 1:
             h += 1
-            nxt = [node(level[i] + level[i + 1]) for i in range(0, len(level) - 1, 2)]
+            nxt = [node(level[i] + level[i + 1], h) for i in range(0, len(level) - 1, 2)]
             if len(level) % 2:
                 nxt.append(level[-1])
             level = nxt

@@ -72,7 +72,7 @@ def test_every_node_is_locally_maximal(n, b, leaf, tau, seed):
     A = pi.randn(n, 70 + seed)
     r = oracle.calu_prrp(A, b=b, tau=tau, leaf_rows=leaf, keep_nodes=True)
     assert r.nodes
-    for B, sel in r.nodes:
+    for _, _, B, sel in r.nodes:
         assert _det_ratio_ok(B, list(sel), tau)
 
 
@@ -81,3 +81,21 @@ def test_singular_panel_raises():
     A[:, 3] = A[:, 2]
     with pytest.raises(oracle.SingularError):
         oracle.calu_prrp(A, b=8, leaf_rows=8)
+
+
+@pytest.mark.parametrize("n,b,leaf", [(100, 8, 24), (75, 5, 10), (64, 8, 8)])
+def test_tree_structure(n, b, leaf):
+    """The tournament's shape, from its definition: per panel the leaves partition the panel's
+    rows, a binary tree over P leaves has P - 1 merge nodes, and every merge node sees the
+    2b candidates of its two children."""
+    A = pi.randn(n, 31)
+    r = oracle.calu_prrp(A, b=b, leaf_rows=leaf, keep_nodes=True)
+    for j, k0 in enumerate(range(0, n, b)):
+        w, m = min(b, n - k0), n - k0
+        mine = [(lv, B) for (pj, lv, B, _) in r.nodes if pj == j]
+        leaves = [B for lv, B in mine if lv == 0]
+        merges = [B for lv, B in mine if lv > 0]
+        assert len(leaves) == max(1, m // leaf)
+        assert sum(B.shape[1] for B in leaves) == m
+        assert len(merges) == len(leaves) - 1
+        assert all(B.shape == (w, 2 * w) for B in merges)
