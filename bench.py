@@ -541,6 +541,7 @@ def run_ours(args) -> None:
         forms["batched"] = form_batched(prrp, ctx, torch, dev)
         forms["served"] = form_served(prrp, ctx)
         forms["fp64_emu"] = form_mixed(prrp, ctx, torch, dev, n=n, kappas=(0.0,), prec=4)
+        forms["mixed_tf32"] = form_mixed(prrp, ctx, torch, dev, kappas=(1e2, 1e4), prec=1, plain=False)
     if rank == 0:
         csum = clocks.summary()
         up = kstats["update"]
@@ -608,7 +609,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the mixed-precision, batched and served measurements")
-    ap.add_argument("--form", choices=["mixed", "batched", "served", "update", "fp64_emu"],
+    ap.add_argument("--form", choices=["mixed", "batched", "served", "update", "fp64_emu", "mixed_tf32"],
                     help="run only one of the other forms and print its JSON")
     ap.add_argument("--count", type=int, default=4096,
                     help="--form batched: number of systems (smaller batches for profiling)")
@@ -641,7 +642,9 @@ def main():
               "served": lambda: form_served(prrp, ctx),
               "update": lambda: form_update(prrp, ctx, torch, dev,
                                             n=args.n if args.n != N_DEFAULT else 16384),
-              "fp64_emu": lambda: form_mixed(prrp, ctx, torch, dev, n=args.n, kappas=(0.0,), prec=4)}[args.form]
+              "fp64_emu": lambda: form_mixed(prrp, ctx, torch, dev, n=args.n, kappas=(0.0,), prec=4),
+              "mixed_tf32": lambda: form_mixed(prrp, ctx, torch, dev, kappas=(1e2, 1e4), prec=1,
+                                               plain=False)}[args.form]
         out = fn()
         if dist is None or dist.get_rank() == 0:
             print(json.dumps({"form": args.form, **out}), flush=True)
