@@ -550,10 +550,10 @@ def run_ours(args) -> None:
         total_kernel_ms = sum(v["ms"] for v in kstats.values())
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            dt, fl = oracle_sample(n, b, args.ref_panels)
+            dt, fl = oracle_sample(n, b, args.cpu_panels)
             cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
                    "kind": "oracle",
-                   "sample": f"first {args.ref_panels} of {(n + b - 1) // b} panels of the same "
+                   "sample": f"first {args.cpu_panels} of {(n + b - 1) // b} panels of the same "
                              f"n={n} factorization, {dt:.1f} s"}
         lat = sorted(step_ms)
         out = {
@@ -605,7 +605,10 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--b", type=int, default=B_DEFAULT)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--ref-panels", type=int, default=8)
+    ap.add_argument("--ref-panels", type=int, default=8,
+                    help="--impl reference: panels of the oracle per step")
+    ap.add_argument("--cpu-panels", type=int, default=32,
+                    help="cpu_baseline: panels of the oracle timed beside the GPU run (about 10 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the mixed-precision, batched and served measurements")
