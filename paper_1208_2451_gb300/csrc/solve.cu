@@ -1,9 +1,11 @@
 // Triangular solves and FP64 residuals with the in-place L\U of LU_PRRP (the solver tests
 // of Section 2.3; the refinement of Section 3.3).
 //
-// Forward and back substitution are blocked by 64 rows with inverted diagonal blocks (see
-// the substitution section below).  The refinement residual is always FP64; factors from a
-// low-precision Schur update are applied in FP32 for the correction solves.
+// Forward and back substitution are blocked by 64 rows with inverted diagonal blocks: one
+// launch per triangle for up to 16 right-hand sides (CTAs following an in-order front of
+// final blocks), else one launch per block.  The refinement residual is always FP64;
+// factors from a low-precision Schur update are applied in FP32 for the correction solves,
+// and the block products and column operations below serve the GMRES-based refinement.
 #include <algorithm>
 
 #include "common.cuh"

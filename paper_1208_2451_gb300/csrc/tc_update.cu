@@ -2,7 +2,9 @@
 // mixed-precision forms: TF32 (one product) or a 3-term BF16 split (x = hi + mid + lo,
 // six products hi*hi + hi*mid + mid*hi + hi*lo + lo*hi + mid*mid, about FP32 accuracy).
 // Accumulation is FP32 in tensor memory; the FP64 trailing matrix is updated in the
-// epilogue (C_ij -= acc_ij in FP64).
+// epilogue (C_ij -= acc_ij in FP64).  The same C -= L U form carries U12 and the final
+// multipliers in those modes.  A second kernel further down computes the update to FP64
+// accuracy from an exact fixed-point split into BF16 digits (the "FP64-accurate update").
 //
 // One persistent CTA per SM, warp-specialized, over 128 x 128 output tiles:
 //   * warp 0 (one lane) streams every operand slice of a tile with TMA (K-major, 128-byte
