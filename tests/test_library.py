@@ -59,3 +59,27 @@ def test_product_package_does_not_use_the_oracle():
             if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def _prototype_arity():
+    """Parameter count of every prototype in the header (comments stripped)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for name in declared_functions():
+        m = re.search(r"\b" + name + r"\s*\(", text)
+        i, depth, j = m.end(), 1, m.end()
+        while depth:
+            depth += {"(": 1, ")": -1}.get(text[j], 0)
+            j += 1
+        params = " ".join(text[i:j - 1].split())
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_header():
+    """Every ctypes signature in the binding takes as many arguments as the header's
+    prototype, so a changed entry point cannot be called with a stale argument list."""
+    import paper_1208_2451_gb300.binding as B
+    arity = _prototype_arity()
+    wrong = {n: (len(B._SIGS[n][1]), arity[n]) for n in arity if len(B._SIGS[n][1]) != arity[n]}
+    assert not wrong, wrong
