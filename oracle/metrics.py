@@ -10,6 +10,9 @@ legs, never by the product package.
 * ``eta``, ``componentwise``   normwise (1-norm) and componentwise backward errors
                        (eq. "eta" and eq. "comp").
 * ``factor_residual``  ||PA - LU||_F / ||A||_F.
+
+Pins (tests/test_oracle_metrics.py): hand-computed exact values, the Rigal-Gaches and
+Oettli-Prager perturbations that attain eta and w, and planted-mistake mutants.
 """
 from __future__ import annotations
 
