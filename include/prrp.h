@@ -363,18 +363,19 @@ prrp_status prrp_ctx_kernel_stats(prrp_ctx* ctx, double* ms, long long* launches
  *
  * Scratch: the kernel's device state word and cross-CTA exchange records live in one
  * library-wide static device array of 338,176 bytes, which every GPU that loads libprrp.so
- * holds until the process exits.  The first call on a device (the current device at the
- * time of the call) looks up that array's device address; make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's contents (the
- * state word is cleared at the start of each call): calls that overlap on the GPU, from
- * any stream or thread, race and must not be issued.
+ * holds until the process exits.  The call runs on the caller's current device: dP,
+ * dOrder and dL21 must be device memory of that device (INVALID_ARG otherwise).  All calls
+ * share the array and it keeps the last call's contents (the state word and the exchange
+ * flags are cleared at the start of each call): calls that overlap on the GPU, from any
+ * stream or thread, race and must not be issued.
  *
  * Limits: the exchange records hold at most 160 CTAs (the grid is min(#SMs, 160,
  * ceil(m/32)) CTAs); a panel whose rows then exceed one CTA's shared memory returns
  * PRRP_ERR_UNSUPPORTED.  Arguments as prrp_panel_select, except dOrder (m ints, DEVICE,
  * caller-owned) receives the order; hSwaps (host, may be NULL) the interchange count.
- * The call synchronizes `stream` and returns the kernel's status (SINGULAR, SWAP_LIMIT,
- * TIMEOUT) or INVALID_ARG / UNSUPPORTED / CUDA.
+ * The call synchronizes `stream` and reads the kernel's status on the host, so it cannot
+ * be used inside stream capture.  It returns that status (SINGULAR, SWAP_LIMIT, TIMEOUT)
+ * or INVALID_ARG / UNSUPPORTED / CUDA.
  */
 prrp_status prrp_panel_select_noalloc(int m, int w, const double* dP, int ldp, double tau,
                                       int max_swaps, int* dOrder, double* dL21, int* hSwaps,

@@ -360,10 +360,13 @@ def prrp_panel_select_noalloc(P, tau=2.0, max_swaps=64, stream=None):
     order = torch.empty(m, dtype=torch.int32, device=P.device)
     L21 = torch.empty((max(m - w, 0), w), dtype=torch.float64, device=P.device)
     sw = C.c_int(0)
-    st = _lib.prrp_panel_select_noalloc(m, w, C.c_void_p(P.data_ptr()), ldp, float(tau),
-                                        int(max_swaps), C.c_void_p(order.data_ptr()),
-                                        C.c_void_p(L21.data_ptr() if L21.numel() else 0),
-                                        C.byref(sw), _stream_ptr(stream))
+    with torch.cuda.device(P.device):     # the C side runs on the current device
+        if stream is None:
+            stream = torch.cuda.current_stream(P.device)
+        st = _lib.prrp_panel_select_noalloc(m, w, C.c_void_p(P.data_ptr()), ldp, float(tau),
+                                            int(max_swaps), C.c_void_p(order.data_ptr()),
+                                            C.c_void_p(L21.data_ptr() if L21.numel() else 0),
+                                            C.byref(sw), _stream_ptr(stream))
     _check(st, "prrp_panel_select_noalloc")
     return order, L21, sw.value
 

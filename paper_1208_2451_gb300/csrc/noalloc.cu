@@ -11,11 +11,10 @@
 // the library holds until the process exits.
 //
 // Host code must not pass the array's name to a kernel: on the host that name is only a
-// stand-in, not a device address.  The device address is looked up once per device with
-// cudaGetSymbolAddress, with that device current, on the first call made on it.
+// stand-in, not a device address.  Every call looks the device address up with
+// cudaGetSymbolAddress, with the caller's current device current (cheap next to the
+// launch and the synchronization), so a module reloaded after cudaDeviceReset is followed.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -36,20 +35,27 @@ static_assert(kScratchBytes % 256 == 0, "scratch slots keep 256-byte alignment")
 static __device__ __align__(256) unsigned char g_panel_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {};
 
-// Once per device, with that device current: the device address of the static scratch.
-cudaError_t scratch_address(int dev, unsigned char** out) {
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_panel_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+// With the device current: the device address of the static scratch.
+cudaError_t scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_panel_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
+}
+
+// A caller pointer must be device memory of the current device (or managed memory):
+// a kernel launched here would otherwise read another GPU's address.
+bool on_device(const void* ptr, int dev) {
+  if (!ptr) return true;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -73,8 +79,9 @@ extern "C" prrp_status prrp_panel_select_noalloc(int m, int w, const double* dP,
   const int G = std::max(1, std::min(std::min(sms, kStaticMaxCtas), (m + 31) / 32));
   const int rpc = (m + G - 1) / G;
   if (panel_smem_for(w, rpc) > (size_t)smem) return PRRP_ERR_UNSUPPORTED;
+  if (!on_device(dP, dev) || !on_device(dOrder, dev) || !on_device(dL21, dev)) return PRRP_ERR_INVALID_ARG;
   unsigned char* base = nullptr;
-  if (scratch_address(dev, &base) != cudaSuccess) return PRRP_ERR_CUDA;
+  if (scratch_address(&base) != cudaSuccess) return PRRP_ERR_CUDA;
   DevState* st = reinterpret_cast<DevState*>(base);
   // The array keeps the previous call's contents: clear the state word (error status,
   // barrier arrivals, counters) and the exchange keys (ready flags).  The other exchange
