@@ -53,6 +53,8 @@ struct prrp_ctx {
   double* xval = nullptr;       // panel exchange records
   int2* xkey = nullptr;
   double* xvec = nullptr;
+  unsigned long long* qkey = nullptr;   // QRCP step keys [3][xcap][kQKeyStride]
+  double* qrow = nullptr;               // QRCP records [3][xcap][kQStride]
   int xcap = 0;                 // CTAs the exchange can hold
   int* pairs = nullptr;
   int pairs_cap = 0;
@@ -237,9 +239,10 @@ prrp_status check_opts(const prrp_opts* o) {
   return PRRP_OK;
 }
 
-// Cooperative grid size for an m-row panel: <= one CTA per SM, >= 32 rows per CTA.
+// Cooperative grid size for an m-row panel: <= one CTA per SM (and <= kPanelMaxCtas),
+// >= 32 rows per CTA.
 prrp_status panel_grid(prrp_ctx* ctx, int m, int w, int* G, int* rpc) {
-  int g = std::max(1, std::min(ctx->num_sms, (m + 31) / 32));
+  int g = std::max(1, std::min(std::min(ctx->num_sms, kPanelMaxCtas), (m + 31) / 32));
   int r = (m + g - 1) / g;
   if (panel_smem_for(w, r) > ctx->smem_optin) return PRRP_ERR_UNSUPPORTED;
   *G = g;
@@ -249,14 +252,17 @@ prrp_status panel_grid(prrp_ctx* ctx, int m, int w, int* G, int* rpc) {
 
 prrp_status ensure_panel_ws(prrp_ctx* ctx, int n, int w, int max_swaps) {
   prrp_status s;
-  if (ctx->xcap < 2 * ctx->num_sms) {
-    const int G = 2 * ctx->num_sms;
-    size_t c1 = 0, c2 = 0, c3 = 0;
+  if (ctx->xcap < kPanelMaxCtas) {
+    const int G = kPanelMaxCtas;
+    size_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
     if (ctx->xval) { cudaFree(ctx->xval); cudaFree(ctx->xkey); cudaFree(ctx->xvec); }
-    ctx->xval = nullptr; ctx->xkey = nullptr; ctx->xvec = nullptr;
+    if (ctx->qkey) { cudaFree(ctx->qkey); cudaFree(ctx->qrow); }
+    ctx->xval = nullptr; ctx->xkey = nullptr; ctx->xvec = nullptr; ctx->qkey = nullptr; ctx->qrow = nullptr;
     if ((s = grow(ctx, &ctx->xval, &c1, 2 * (size_t)G * kXVal)) != PRRP_OK) return s;
     if ((s = grow(ctx, &ctx->xkey, &c2, 2 * (size_t)G)) != PRRP_OK) return s;
     if ((s = grow(ctx, &ctx->xvec, &c3, 2 * (size_t)G * kMaxW)) != PRRP_OK) return s;
+    if ((s = grow(ctx, &ctx->qkey, &c4, 3 * (size_t)G * kQKeyStride)) != PRRP_OK) return s;
+    if ((s = grow(ctx, &ctx->qrow, &c5, 3 * (size_t)G * kQStride)) != PRRP_OK) return s;
     ctx->xcap = G;
   }
   if ((s = grow_i(ctx, &ctx->pairs, &ctx->pairs_cap, 4 * (w + max_swaps) + 8)) != PRRP_OK) return s;
@@ -274,12 +280,13 @@ prrp_status enqueue_panel(prrp_ctx* ctx, const double* P, long long ldp, int m, 
   prrp_status ps = panel_grid(ctx, m, w, &G, &rpc);
   if (ps != PRRP_OK) return ps;
   CK(cudaMemsetAsync(&ctx->st->barrier, 0, 2 * sizeof(unsigned), s));
-  // the exchange keys double as the reflector-ready flags of the QRCP steps
-  CK(cudaMemsetAsync(ctx->xkey, 0, 2 * sizeof(int2) * G, s));
+  // a QRCP key slot is empty while it holds 0
+  CK(cudaMemsetAsync(ctx->qkey, 0, 3 * sizeof(unsigned long long) * G * kQKeyStride, s));
   PanelParams p{};
   p.P = P; p.ldp = ldp; p.m = m; p.w = w; p.tau = tau; p.max_swaps = max_swaps;
   p.col_offset = col_offset; p.L21 = L21; p.ldl = ldl; p.order = order; p.pairs = pairs;
   p.st = ctx->st; p.xval = ctx->xval; p.xkey = ctx->xkey; p.xvec = ctx->xvec; p.rows_per_cta = rpc;
+  p.qkey = ctx->qkey; p.qrow = ctx->qrow;
   p.cluster_rows = ctx->panel_cluster_rows;
   cudaError_t e = launch_panel(p, G, s);
   if (e == cudaErrorCooperativeLaunchTooLarge) return PRRP_ERR_UNSUPPORTED;
@@ -381,7 +388,7 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
   if (ctx->bmeta) cudaFree(ctx->bmeta);
   if (ctx->bws) cudaFree(ctx->bws);
   if (ctx->bout) cudaFree(ctx->bout);
-  void* ptrs[] = {ctx->st, ctx->xval, ctx->xkey, ctx->xvec, ctx->pairs, ctx->ipiv, ctx->order,
+  void* ptrs[] = {ctx->st, ctx->xval, ctx->xkey, ctx->xvec, ctx->qkey, ctx->qrow, ctx->pairs, ctx->ipiv, ctx->order,
                   ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB, ctx->tcws,
                   ctx->l21b, ctx->a12, ctx->tcws2, ctx->dinv64, ctx->dinv32, ctx->lu32, ctx->y32,
                   ctx->tcount, ctx->zbuf, ctx->gemm_ctr, ctx->krylov, ctx->gm_coef, ctx->tcws3, ctx->tri};

@@ -10,7 +10,8 @@
 namespace prrp {
 
 constexpr int kMaxW = 128;              // largest panel width b supported
-constexpr int kPanelThreads = 256;      // threads per panel CTA
+constexpr int kPanelThreads = 320;      // threads per panel CTA (communication, helper, 8 row warps)
+constexpr int kPanelMaxCtas = 160;      // CTAs a panel grid may have (exchange slots per step)
 constexpr int kTeam = 4;                // threads cooperating on one panel row
 // A bounded wait gives up after this many polls (each poll sleeps ~100 ns): about 1-2 s.
 constexpr unsigned kSpinLimit = 1u << 24;

@@ -8,7 +8,9 @@
 
 namespace prrp {
 
-constexpr int kXVal = 3;   // doubles per panel exchange record: value, reflector alpha, beta
+constexpr int kXVal = 3;   // doubles per interchange exchange record (the value; 2 spare)
+constexpr int kQStride = kMaxW + 2;   // doubles per QRCP record: the row, then alpha and beta
+constexpr int kQKeyStride = 16;       // u64 per QRCP key slot: one 128-byte line each
 
 struct PanelParams {
   const double* P;        // m x w panel, row-major
@@ -22,9 +24,11 @@ struct PanelParams {
   int* order;             // m ints (final position -> panel row) or nullptr
   int* pairs;             // (dst, src) row moves, 2 ints each, or nullptr
   DevState* st;
-  double* xval;           // exchange records: [2][G][kXVal] (value, alpha, beta)
-  int2* xkey;             // [2][G]
-  double* xvec;           // [2][G][kMaxW]
+  double* xval;           // interchange exchange records: [2][G][kXVal] (value)
+  int2* xkey;             // [2][G] (tie-breaks)
+  double* xvec;           // [2][G][kMaxW] (row)
+  unsigned long long* qkey;   // QRCP step keys [3][G][kQKeyStride], zero at launch
+  double* qrow;               // QRCP records [3][G][kQStride]
   int rows_per_cta;
   int cluster_rows;       // panels of at most this many rows run as one cluster (0: default)
 };

@@ -23,12 +23,16 @@
 namespace prrp {
 namespace {
 
-constexpr int kStaticMaxCtas = 160;   // panel CTAs the static exchange records can hold
+constexpr int kStaticMaxCtas = kPanelMaxCtas;   // panel CTAs the static records can hold (160)
 constexpr size_t kStateBytes = 256;   // DevState, padded
 constexpr size_t kValBytes = 2 * kStaticMaxCtas * kXVal * sizeof(double);
 constexpr size_t kKeyBytes = 2 * kStaticMaxCtas * sizeof(int2);
 constexpr size_t kVecBytes = 2 * (size_t)kStaticMaxCtas * kMaxW * sizeof(double);
-constexpr size_t kScratchBytes = kStateBytes + kValBytes + kKeyBytes + kVecBytes;   // 338,176 B
+constexpr size_t kQKeyBytes = 3 * kStaticMaxCtas * kQKeyStride * sizeof(unsigned long long);
+constexpr size_t kQRowBytes = 3 * (size_t)kStaticMaxCtas * kQStride * sizeof(double);
+constexpr size_t kScratchBytes =
+    kStateBytes + kValBytes + kKeyBytes + kVecBytes + kQKeyBytes + kQRowBytes;   // 898,816 B
+static_assert(kScratchBytes == 898816, "the documented size of the static scratch");
 static_assert(sizeof(DevState) <= kStateBytes, "state word does not fit its slot");
 static_assert(kScratchBytes % 256 == 0, "scratch slots keep 256-byte alignment");
 
@@ -84,11 +88,11 @@ extern "C" prrp_status prrp_panel_select_noalloc(int m, int w, const double* dP,
   if (scratch_address(&base) != cudaSuccess) return PRRP_ERR_CUDA;
   DevState* st = reinterpret_cast<DevState*>(base);
   // The array keeps the previous call's contents: clear the state word (error status,
-  // barrier arrivals, counters) and the exchange keys (ready flags).  The other exchange
-  // records need no clearing: each is written before it is read within a call.
+  // barrier arrivals, counters) and the QRCP step keys (a slot is empty while it holds 0).
+  // The other records need no clearing: each is written before it is read within a call.
   if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return PRRP_ERR_CUDA;
-  // the exchange keys double as the panel's reflector-ready flags: they start at zero
-  if (cudaMemsetAsync(base + kStateBytes + kValBytes, 0, kKeyBytes, s) != cudaSuccess) return PRRP_ERR_CUDA;
+  unsigned char* qbase = base + kStateBytes + kValBytes + kKeyBytes + kVecBytes;
+  if (cudaMemsetAsync(qbase, 0, kQKeyBytes, s) != cudaSuccess) return PRRP_ERR_CUDA;
   PanelParams p{};
   p.P = dP; p.ldp = ldp; p.m = m; p.w = w; p.tau = tau; p.max_swaps = max_swaps;
   p.col_offset = 0; p.L21 = dL21; p.ldl = w; p.order = dOrder; p.pairs = nullptr;
@@ -96,6 +100,8 @@ extern "C" prrp_status prrp_panel_select_noalloc(int m, int w, const double* dP,
   p.xval = reinterpret_cast<double*>(base + kStateBytes);
   p.xkey = reinterpret_cast<int2*>(base + kStateBytes + kValBytes);
   p.xvec = reinterpret_cast<double*>(base + kStateBytes + kValBytes + kKeyBytes);
+  p.qkey = reinterpret_cast<unsigned long long*>(qbase);
+  p.qrow = reinterpret_cast<double*>(qbase + kQKeyBytes);
   p.rows_per_cta = rpc;
   cudaError_t e = launch_panel(p, G, s);
   if (e == cudaErrorCooperativeLaunchTooLarge) return PRRP_ERR_UNSUPPORTED;
