@@ -328,6 +328,19 @@ prrp_status prrp_ctx_set_timing(prrp_ctx* ctx, int enable);
  * cluster_max_rows in [0, 4096], 0 = the default (512); INVALID_ARG otherwise. */
 prrp_status prrp_ctx_set_panel_mode(prrp_ctx* ctx, int cluster_max_rows);
 
+/* SM split of the tensor-core modes (PRRP_TF32, PRRP_BF16X3, PRRP_FP64_EMU) for this
+ * context (a tuning knob; results do not change).  Their trailing-update kernels hold one
+ * SM's shared memory per CTA, so a panel (Algorithm 2) cannot run on the SMs they hold.
+ * prrp_factor in these modes therefore runs the panels, and the narrow update of the next
+ * panel's columns between them, on at most panel_ctas CTAs (more when a panel's rows would
+ * not fit them), the diagonal-block work (GEPP, U12, the final multipliers) on at most
+ * block_ctas, and the rest of each trailing update on the remaining SMs, so that the
+ * panel of step j + 1 runs beside the update of step j.  0 selects the library default
+ * (64 and 8); panel_ctas equal to the SM count turns the split off.  INVALID_ARG when a
+ * value is negative or above the SM count, or when the two leave fewer than 8 SMs for the
+ * rest update.  The plain FP64 mode is not affected. */
+prrp_status prrp_ctx_set_sm_split(prrp_ctx* ctx, int panel_ctas, int block_ctas);
+
 /* Substitution form of prrp_solve for this context (a tuning knob).  mode 0 (the default):
  * a triangle with at most 16 right-hand sides is solved by one launch whose CTAs wait for
  * one another's row blocks, the lowest latency for one solve on an otherwise idle GPU;

@@ -71,6 +71,7 @@ _SIGS = {
     "prrp_ctx_kernel_stats": (_I, [_P, _P, _P, _P, _I]),
     "prrp_ctx_timeline": (_I, [_P, _I, _P, _P, _P, C.POINTER(_I)]),
     "prrp_ctx_set_panel_mode": (_I, [_P, _I]),
+    "prrp_ctx_set_sm_split": (_I, [_P, _I, _I]),
     "prrp_server_create": (_I, [_P, C.c_size_t, C.POINTER(prrp_opts), _I, C.POINTER(_P)]),
     "prrp_server_submit": (_I, [_P, _P, C.POINTER(C.c_uint64)]),
     "prrp_server_wait": (_I, [_P, C.c_uint64, C.c_int64, _P]),
@@ -318,6 +319,11 @@ def prrp_ctx_set_timing(ctx: Context, enable=True) -> None:
 def prrp_ctx_set_panel_mode(ctx: Context, cluster_max_rows: int = 0) -> None:
     """Panels of at most cluster_max_rows rows run as one thread-block cluster (0: default)."""
     _check(_lib.prrp_ctx_set_panel_mode(ctx.handle, int(cluster_max_rows)), "prrp_ctx_set_panel_mode")
+
+
+def prrp_ctx_set_sm_split(ctx: Context, panel_ctas: int = 0, block_ctas: int = 0) -> None:
+    """SMs for the panels and the diagonal-block work in the tensor-core modes (0: default)."""
+    _check(_lib.prrp_ctx_set_sm_split(ctx.handle, int(panel_ctas), int(block_ctas)), "prrp_ctx_set_sm_split")
 
 
 def prrp_ctx_set_solve_mode(ctx: Context, mode: int) -> None:

@@ -107,6 +107,8 @@ struct prrp_ctx {
   double* zbuf = nullptr;           // second n x nrhs buffer of the one-launch substitution
   size_t zbuf_cap = 0;
   int panel_cluster_rows = 0;       // prrp_ctx_set_panel_mode (0: the library default)
+  int split_panel = 0;              // prrp_ctx_set_sm_split (0: the library defaults)
+  int split_blk = 0;
   int solve_mode = 0;               // prrp_ctx_set_solve_mode
   double* krylov = nullptr;         // GMRES-based refinement: Krylov basis, coefficients
   size_t krylov_cap = 0;
@@ -240,11 +242,20 @@ prrp_status check_opts(const prrp_opts* o) {
 }
 
 // Cooperative grid size for an m-row panel: <= one CTA per SM (and <= kPanelMaxCtas),
-// >= 32 rows per CTA.
-prrp_status panel_grid(prrp_ctx* ctx, int m, int w, int* G, int* rpc) {
-  int g = std::max(1, std::min(std::min(ctx->num_sms, kPanelMaxCtas), (m + 31) / 32));
+// >= 32 rows per CTA, and <= max_ctas when that is given, unless the rows per CTA would
+// then not fit a CTA's shared memory.
+prrp_status panel_grid(prrp_ctx* ctx, int m, int w, int* G, int* rpc, int max_ctas = 0) {
+  const int gmax = std::min(ctx->num_sms, kPanelMaxCtas);
+  int g = std::max(1, std::min(gmax, (m + 31) / 32));
+  if (max_ctas > 0) g = std::min(g, max_ctas);
   int r = (m + g - 1) / g;
-  if (panel_smem_for(w, r) > ctx->smem_optin) return PRRP_ERR_UNSUPPORTED;
+  // the kernel's static shared memory (under 8 KB) comes out of the same opt-in limit
+  const size_t limit = ctx->smem_optin - 8192;
+  while (panel_smem_for(w, r) > limit && g < gmax) {
+    ++g;
+    r = (m + g - 1) / g;
+  }
+  if (panel_smem_for(w, r) > limit) return PRRP_ERR_UNSUPPORTED;
   *G = g;
   *rpc = r;
   return PRRP_OK;
@@ -275,9 +286,9 @@ prrp_status ensure_panel_ws(prrp_ctx* ctx, int n, int w, int max_swaps) {
 // and the pair counter first.
 prrp_status enqueue_panel(prrp_ctx* ctx, const double* P, long long ldp, int m, int w, double tau,
                           int max_swaps, int col_offset, double* L21, int ldl, int* order,
-                          int* pairs, cudaStream_t s) {
+                          int* pairs, cudaStream_t s, int max_ctas = 0) {
   int G = 0, rpc = 0;
-  prrp_status ps = panel_grid(ctx, m, w, &G, &rpc);
+  prrp_status ps = panel_grid(ctx, m, w, &G, &rpc, max_ctas);
   if (ps != PRRP_OK) return ps;
   CK(cudaMemsetAsync(&ctx->st->barrier, 0, 2 * sizeof(unsigned), s));
   // a QRCP key slot is empty while it holds 0
@@ -478,13 +489,29 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
   cudaEvent_t ev_rest = nullptr, ev_blk = nullptr;        // of the previous panel
   // C (mm x nn) -= L (mm x kk, ld kk) * U (kk x nn, ld ldu)
   if ((ps = grow(ctx, &ctx->gemm_ctr, &ctx->gemm_ctr_cap, 2)) != PRRP_OK) return fail(ps);
+  // SM split of the tensor-core modes.  Their update kernels hold a whole SM's shared memory
+  // per CTA, so a panel cannot share an SM with them: the panels (and the narrow update
+  // between them, on the same stream) get split_panel SMs, the block stream's kernels
+  // split_blk, and the rest update the others.  The FP64 update shares SMs with the panels
+  // and keeps the whole GPU.
+  int cap_panel = 0, cap_blk = 0, cap_rest = 0;
+  if (o.prec != PRRP_FP64) {
+    cap_panel = ctx->split_panel > 0 ? ctx->split_panel : kSplitPanelDefault;
+    cap_blk = ctx->split_blk > 0 ? ctx->split_blk : kSplitBlkDefault;
+    if (cap_panel >= ctx->num_sms) {
+      cap_panel = cap_blk = 0;                 // no split: every kernel may take every SM
+    } else {
+      cap_rest = std::max(8, ctx->num_sms - cap_panel - cap_blk);
+    }
+  }
   auto update = [&](int mm, int nn, int kk, const double* L, const double* U, long long ldu, double* C,
                     unsigned char* ws, cudaStream_t st) -> cudaError_t {
     if (o.prec == PRRP_FP64)   // one tile counter per stream: the narrow and rest updates overlap
       return launch_gemm_fp64(mm, nn, kk, L, kk, U, ldu, C, lda, ctx->st, 1, ctx->num_sms, st, 1,
                               ctx->gemm_ctr + (st == sr ? 1 : 0));
     ctx->kind_launches[PRRP_KIND_UPDATE] += 2;   // the two operand splits before the MMA kernel
-    return launch_tc_update(o.prec, mm, nn, kk, L, kk, U, ldu, C, lda, ctx->st, 1, ws, st);
+    return launch_tc_update(o.prec, mm, nn, kk, L, kk, U, ldu, C, lda, ctx->st, 1, ws, st,
+                            st == sr ? cap_rest : cap_panel);
   };
   for (int jp = 0, k0 = 0; k0 < n; k0 += b, ++jp) {
     const int w = std::min(b, n - k0), m = n - k0;
@@ -494,7 +521,7 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
     double* A12 = ctx->a12 + (size_t)(jp & 1) * n * b;     // snapshot: w x nc, ld nc
     {
       Timed t(ctx, s, PRRP_KIND_PANEL, 3LL * m * w * w);
-      ps = enqueue_panel(ctx, Akk, lda, m, w, o.tau, o.max_swaps, k0, L21, w, nullptr, ctx->pairs, s);
+      ps = enqueue_panel(ctx, Akk, lda, m, w, o.tau, o.max_swaps, k0, L21, w, nullptr, ctx->pairs, s, cap_panel);
     }
     if (ps != PRRP_OK) return fail(ps);
     if (ev_rest) CK(cudaStreamWaitEvent(s, ev_rest, 0));
@@ -545,7 +572,7 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
         if (e == cudaSuccess) e = launch_tri_blocks(dA, lda, k0, w, ctx->tri, ctx->st, sb);
         if (e == cudaSuccess && nc > 0)
           e = launch_tc_update(o.prec, w, nc, w, ctx->tri, w, Akk + w, lda, Akk + w, lda, ctx->st, 2,
-                               ctx->tcws3, sb);
+                               ctx->tcws3, sb, cap_blk);
       }
       if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "u12"));
       if (m > w) {
@@ -555,7 +582,7 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
         e = launch_lfix_copy(dA, lda, n, k0, w, L21, w, ctx->ipiv, ctx->st, sb);
         if (e == cudaSuccess)
           e = launch_tc_update(o.prec, m - w, w, w, Y, lda, ctx->tri + (size_t)w * w, w, Y, lda, ctx->st, 0,
-                               ctx->tcws3, sb);
+                               ctx->tcws3, sb, cap_blk);
       }
       if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "lfix"));
     } else {
@@ -1392,6 +1419,15 @@ prrp_status prrp_ctx_set_timing(prrp_ctx* ctx, int enable) {
 prrp_status prrp_ctx_set_panel_mode(prrp_ctx* ctx, int cluster_max_rows) {
   if (!ctx || cluster_max_rows < 0 || cluster_max_rows > 4096) return PRRP_ERR_INVALID_ARG;
   ctx->panel_cluster_rows = cluster_max_rows;
+  return PRRP_OK;
+}
+
+prrp_status prrp_ctx_set_sm_split(prrp_ctx* ctx, int panel_ctas, int block_ctas) {
+  if (!ctx || panel_ctas < 0 || block_ctas < 0 || panel_ctas > ctx->num_sms || block_ctas > ctx->num_sms)
+    return PRRP_ERR_INVALID_ARG;
+  if (panel_ctas < ctx->num_sms && panel_ctas + block_ctas > ctx->num_sms - 8) return PRRP_ERR_INVALID_ARG;
+  ctx->split_panel = panel_ctas;
+  ctx->split_blk = block_ctas;
   return PRRP_OK;
 }
 

@@ -11,6 +11,9 @@ namespace prrp {
 constexpr int kXVal = 3;   // doubles per interchange exchange record (the value; 2 spare)
 constexpr int kQStride = kMaxW + 2;   // doubles per QRCP record: the row, then alpha and beta
 constexpr int kQKeyStride = 16;       // u64 per QRCP key slot: one 128-byte line each
+// SM split of the tensor-core modes (prrp_ctx_set_sm_split): panel CTAs, block-stream CTAs
+constexpr int kSplitPanelDefault = 64;
+constexpr int kSplitBlkDefault = 8;
 
 struct PanelParams {
   const double* P;        // m x w panel, row-major
@@ -54,13 +57,15 @@ cudaError_t launch_gemm_fp64(int m, int n, int k, const double* L, long long ldl
                              unsigned* tile_ctr = nullptr);
 
 // Same update on tcgen05 tensor cores, prec = PRRP_TF32 or PRRP_BF16X3 (FP32 accumulation,
-// FP64 C); ws holds the split operands (tc_workspace_bytes).  Both operands are split into
-// ws before C is touched, so C may alias L or U.  track: 0 none, 1 max |C| into
-// st->gmax_bits, 2 into st->umax_bits.
+// FP64 C) or PRRP_FP64_EMU (exact digit split); ws holds the split operands
+// (tc_workspace_bytes).  Both operands are split into ws before C is touched, so C may
+// alias L or U.  track: 0 none, 1 max |C| into st->gmax_bits, 2 into st->umax_bits.
+// max_ctas > 0 caps the persistent grid (one CTA per SM), leaving the other SMs free for
+// kernels that run beside it.
 size_t tc_workspace_bytes(int prec, int m, int n, int k);
 cudaError_t launch_tc_update(int prec, int m, int n, int k, const double* L, long long ldl,
                              const double* U, long long ldu, double* C, long long ldc, DevState* st,
-                             int track, void* ws, cudaStream_t s);
+                             int track, void* ws, cudaStream_t s, int max_ctas = 0);
 
 // GEPP on the w x w diagonal block at A[k0][k0]; in-block pivots to ipiv, perm updated,
 // max |U11| tracked.

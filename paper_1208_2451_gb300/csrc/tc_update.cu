@@ -547,7 +547,7 @@ bool make_c_map(CUtensorMap* m, double* C, int M, int N, long long ldc) {
 template <int MODE, int CT>
 cudaError_t launch_tc_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mc, int M, int N,
                              int kblocks, int Mpad, int Npad, double* C, long long ldc, DevState* st, int track,
-                             cudaStream_t s) {
+                             int max_ctas, cudaStream_t s) {
   using Cfg = TcCfg<MODE, CT>;
   cudaError_t e = smem_optin(tc_update_kernel<MODE, CT>);
   if (e != cudaSuccess) return e;
@@ -555,6 +555,7 @@ cudaError_t launch_tc_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int tiles = (Npad / kBN) * (Mpad / kBM);
+  if (max_ctas > 0) sms = std::min(sms, max_ctas);
   tc_update_kernel<MODE, CT><<<std::min(tiles, sms), kThreads, Cfg::SMEM, s>>>(ma, mb, mc, M, N, kblocks, Mpad,
                                                                                Npad, C, ldc, st, track);
   return cudaGetLastError();
@@ -563,7 +564,7 @@ cudaError_t launch_tc_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const
 template <int MODE>
 cudaError_t launch_tc_mode(int M, int N, int K, const double* L, long long ldl, const double* U, long long ldu,
                            double* C, long long ldc, DevState* st, int track, void* wsA, void* wsB,
-                           cudaStream_t s) {
+                           int max_ctas, cudaStream_t s) {
   using Cfg = TcCfg<MODE, 0>;
   const int kblocks = (K + 63) / 64, kpad = kblocks * 64;
   const int Mpad = (M + kBM - 1) / kBM * kBM, Npad = (N + kBN - 1) / kBN * kBN;
@@ -578,8 +579,8 @@ cudaError_t launch_tc_mode(int M, int N, int K, const double* L, long long ldl, 
   if (!make_map(&ma, wsA, MODE, Cfg::NS * Mpad, kpad) || !make_map(&mb, wsB, MODE, Cfg::NS * Npad, kpad))
     return cudaErrorInvalidValue;
   if (make_c_map(&mc, C, M, N, ldc))
-    return launch_tc_kernel<MODE, 1>(ma, mb, mc, M, N, kblocks, Mpad, Npad, C, ldc, st, track, s);
-  return launch_tc_kernel<MODE, 0>(ma, mb, ma, M, N, kblocks, Mpad, Npad, C, ldc, st, track, s);
+    return launch_tc_kernel<MODE, 1>(ma, mb, mc, M, N, kblocks, Mpad, Npad, C, ldc, st, track, max_ctas, s);
+  return launch_tc_kernel<MODE, 0>(ma, mb, ma, M, N, kblocks, Mpad, Npad, C, ldc, st, track, max_ctas, s);
 }
 
 
@@ -835,7 +836,8 @@ size_t ozaki_ws_bytes(int M, int N) {
 }
 
 cudaError_t launch_ozaki(int M, int N, int K, const double* L, long long ldl, const double* U, long long ldu,
-                         double* C, long long ldc, DevState* st, int track, void* ws, cudaStream_t s) {
+                         double* C, long long ldc, DevState* st, int track, void* ws, int max_ctas,
+                         cudaStream_t s) {
   if (K > 64) return cudaErrorInvalidValue;
   const int Mpad = (M + kBM - 1) / kBM * kBM, Npad = (N + kOzBN - 1) / kOzBN * kOzBN;
   uint8_t* w = static_cast<uint8_t*>(ws);
@@ -855,6 +857,7 @@ cudaError_t launch_ozaki(int M, int N, int K, const double* L, long long ldl, co
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int tiles = (Mpad / kBM) * (Npad / kOzBN);
+  if (max_ctas > 0) sms = std::min(sms, max_ctas);
   ozaki_update_kernel<<<std::min(tiles, sms), kOzThreads, kOzSmem, s>>>(ma, mb, M, N, Mpad, Npad, rexp, cexp, C,
                                                                          ldc, st, track);
   return cudaGetLastError();
@@ -873,17 +876,17 @@ size_t tc_workspace_bytes(int prec, int M, int N, int K) {
 
 cudaError_t launch_tc_update(int prec, int M, int N, int K, const double* L, long long ldl, const double* U,
                              long long ldu, double* C, long long ldc, DevState* st, int track, void* ws,
-                             cudaStream_t s) {
+                             cudaStream_t s, int max_ctas) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-  if (prec == PRRP_FP64_EMU) return launch_ozaki(M, N, K, L, ldl, U, ldu, C, ldc, st, track, ws, s);
+  if (prec == PRRP_FP64_EMU) return launch_ozaki(M, N, K, L, ldl, U, ldu, C, ldc, st, track, ws, max_ctas, s);
   const int mode = prec == PRRP_TF32 ? 0 : 1;
   const int ns = mode == 0 ? 1 : 3, eb = mode == 0 ? 4 : 2;
   const size_t kpad = static_cast<size_t>((K + 63) / 64) * 64;
   const size_t Mpad = static_cast<size_t>((M + kBM - 1) / kBM) * kBM;
   uint8_t* a = static_cast<uint8_t*>(ws);
   uint8_t* b = a + ((ns * eb * kpad * Mpad + 1023) & ~size_t(1023));
-  if (mode == 0) return launch_tc_mode<0>(M, N, K, L, ldl, U, ldu, C, ldc, st, track, a, b, s);
-  return launch_tc_mode<1>(M, N, K, L, ldl, U, ldu, C, ldc, st, track, a, b, s);
+  if (mode == 0) return launch_tc_mode<0>(M, N, K, L, ldl, U, ldu, C, ldc, st, track, a, b, max_ctas, s);
+  return launch_tc_mode<1>(M, N, K, L, ldl, U, ldu, C, ldc, st, track, a, b, max_ctas, s);
 }
 
 }  // namespace prrp

@@ -77,14 +77,21 @@ def test_emulated_update_large(prrp, ctx, m, n, k):
     assert np.all(np.abs(got - want) <= bound)
 
 
-@pytest.mark.parametrize("n,b,seed", [(1000, 64, 3), (2048, 64, 5), (700, 32, 7), (513, 16, 11)])
-def test_emulated_factor_matches_oracle(prrp, ctx, n, b, seed):
+@pytest.mark.parametrize("n,b,seed,split", [(1000, 64, 3, None), (2048, 64, 5, None), (700, 32, 7, None),
+                                            (513, 16, 11, None), (2048, 64, 13, (16, 8)), (2048, 64, 17, (8, 4))])
+def test_emulated_factor_matches_oracle(prrp, ctx, n, b, seed, split):
     """The whole factorization with the emulated update: the oracle's pivots wherever its
     decisions are untied, the FP64 backward-error bound, the same statistics, and a solve
-    without refinement as accurate as the plain FP64 path's on the same matrix."""
+    without refinement as accurate as the plain FP64 path's on the same matrix.  The
+    narrow SM splits put 128 to 256 rows on each panel CTA of the first panels (256: the
+    one-lane-per-row form)."""
     A = pi.randn(n, seed)
     dA = torch.from_numpy(A).cuda()
-    F = prrp.prrp_factor(ctx, dA, b=b, prec=EMU)
+    prrp.prrp_ctx_set_sm_split(ctx, *(split or (0, 0)))
+    try:
+        F = prrp.prrp_factor(ctx, dA, b=b, prec=EMU)
+    finally:
+        prrp.prrp_ctx_set_sm_split(ctx, 0, 0)
     st = F.stats()
     perm = F.perm().astype(np.int64)
     B = pi.rhs(n, 2, seed)

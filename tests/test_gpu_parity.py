@@ -133,6 +133,40 @@ def test_panel_select(prrp, ctx, m, w, tau):
     assert np.max(np.abs(Lx), initial=0) <= tau * (1 + 1e-9)
 
 
+@pytest.mark.parametrize("m,w,tau,cluster_rows", [(30000, 64, 2.0, 0), (30000, 32, 1.05, 0), (4096, 64, 2.0, 4096),
+                                                  (3200, 16, 1.05, 4096), (30400, 16, 2.0, 0)])
+def test_panel_select_many_rows(prrp, m, w, tau, cluster_rows):
+    """Rows a1-a3 with 198 to 256 rows per CTA, the one-lane-per-row form of the panel
+    kernel (grid form, and the cluster form with panels up to 4096 rows)."""
+    c = prrp.prrp_create(0)
+    try:
+        prrp.prrp_ctx_set_panel_mode(c, cluster_rows)
+        P = pi.randn(w, 11 + m + w, m=m)
+        ref = oracle.strong_rrqr(P.T, tau=tau, max_swaps=64)
+        order, L21, swaps = prrp.prrp_panel_select(c, torch.from_numpy(P).cuda(), tau=tau)
+    finally:
+        c.close()
+    margins = ref.qrcp_margins + ref.test_margins + ref.choice_margins
+    if min(margins, default=np.inf) > 1e-8:
+        assert list(order) == list(ref.order)
+        assert swaps == ref.swaps
+        np.testing.assert_allclose(L21.cpu().numpy(), ref.M.T, atol=1e-10, rtol=1e-9)
+    Lx = np.linalg.solve(P[order[:w]].T, P[order[w:]].T).T
+    np.testing.assert_allclose(L21.cpu().numpy(), Lx, atol=1e-9, rtol=1e-8)
+    assert np.max(np.abs(Lx)) <= tau * (1 + 1e-9)
+
+
+def test_factor_cluster_panels_many_rows(prrp):
+    """A whole factorization whose first panels run as 16-CTA clusters of up to 256 rows
+    per CTA (cluster panels up to 4096 rows, as the serve loop can set)."""
+    c = prrp.prrp_create(0)
+    try:
+        prrp.prrp_ctx_set_panel_mode(c, 4096)
+        check_parity(prrp, c, pi.randn(4096, 77), 64)
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("m,n,k", [(8128, 8128, 64), (1000, 777, 64), (129, 65, 1), (300, 2000, 128),
                                    (64, 64, 100), (1, 1, 16), (5000, 31, 16)])
 def test_schur_update(prrp, ctx, m, n, k):
