@@ -219,20 +219,25 @@ def plain_fp64(prrp, ctx, torch, dev, As, Bs, b):
 
 def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=1, plain=True):
     """Mixed-precision form: A = Q1 diag(sigma) Q2^T (cond kappa, Q from QR of seeded
-    Gaussians), BF16X3 tensor-core Schur update with FP64 pivoting, FP64 refinement of 4
-    right-hand sides.  The matrix is generated on the GPU in FP64 (torch QR).  A kappa of
-    0 stands for an iid N(0,1) matrix instead (no QR).  The first matrix is also solved by
-    the plain FP64 path for the solves/s comparison."""
+    Gaussians, sigma_i = kappa^(-(i-1)/(n-1))), tensor-core Schur update with FP64 pivoting,
+    FP64 refinement of 4 right-hand sides.  The matrix is generated on the GPU in FP64
+    (torch QR; Q1 and Q2 once per call, shared by the kappas).  A kappa of 0 stands for an
+    iid N(0,1) matrix instead (no QR).  The first matrix is also solved by the plain FP64
+    path for the solves/s comparison."""
     out = {}
+    Qs = None
     for kappa in kappas:
         g = torch.Generator(device=dev)
         g.manual_seed(int(kappa) % 1000003)
         if kappa > 0:
-            Q1, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=g))
-            Q2, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=g))
+            if Qs is None:
+                gq = torch.Generator(device=dev)
+                gq.manual_seed(12345)
+                Q1, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=gq))
+                Q2, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=gq))
+                Qs = (Q1, Q2)
             sig = kappa ** (-torch.arange(n, dtype=torch.float64, device=dev) / (n - 1))
-            A0 = (Q1 * sig) @ Q2.T
-            del Q1, Q2
+            A0 = (Qs[0] * sig) @ Qs[1].T
         else:
             A0 = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
         B0 = torch.randn(n, 4, dtype=torch.float64, device=dev, generator=g)
@@ -254,7 +259,7 @@ def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=
         dt = min(times)
         key = f"kappa={kappa:g}" if kappa > 0 else "randn"
         out[key] = {"s": dt, "tflops": 2 * n ** 3 / 3 / dt / 1e12, "solves_per_s": 1.0 / dt,
-                    "eta": eta, "iterations": info["iterations"],
+                    "eta": eta, "iterations": info["iterations"], "fp64_level": bool(eta <= 1e-15),
                     "roofline_fracs": fracs(2 * n ** 3 / 3 / dt / 1e12, prec)}
         if plain and kappa == kappas[0]:
             del A, B
@@ -267,6 +272,8 @@ def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=
         else:
             del A0, A, B0, B
         torch.cuda.empty_cache()
+    del Qs
+    torch.cuda.empty_cache()
     upd = {1: "TF32", 2: "BF16X3", 4: "FP64-accurate (8-digit BF16 split)"}[prec]
     mat = "cond-controlled A" if any(k > 0 for k in kappas) else "A iid N(0,1)"
     return {"workload": f"n={n}, b=64, tau=2, {mat}, 4 RHS, {upd} Schur update + FP64 refinement", "runs": out}
@@ -396,15 +403,25 @@ def form_batched(prrp, ctx, torch, dev, count=4096, reps=3, plain_sample=256, di
     return {"workload": f"{count} systems, n uniform in [32, 512], b=16, 1 RHS", "runs": res}
 
 
-def form_served(prrp, ctx, rates=(300.0, 3000.0), count=400, budget=64 << 30, plain_sample=120):
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+def form_served(prrp, ctx, rates=(25.0, 50.0, 100.0, 150.0, 300.0, 1000.0), budget=64 << 30, plain_sample=120):
     """Served form: Poisson arrivals, n log-uniform in [64, 4096], RHS count uniform in
     1..16, iid N(0,1); a pool of 48 pre-generated matrices is cycled so request generation
-    does not bound the arrival rate."""
+    does not bound the arrival rate.  The arrival rate sweeps through the server's capacity:
+    each rate runs about 4 s of arrivals (100 to 400 requests).  Per rate: solves/s,
+    latency (submit to completion) p50/p99, queueing (submit to admission) p50/p99 and the
+    service time (admission to completion) p50/p99 for small (n <= 512, batched) and large
+    requests, the queue's growth (mean queueing of the last quarter of the requests over
+    the first quarter), and the peak HBM admitted."""
     import prrp_inputs as pi
     pool_sizes = np.unique(np.geomspace(64, 4096, 48).astype(int))
     pool = {int(k): pi.randn(int(k), 7000 + int(k)) for k in pool_sizes}
     out = {}
     for rate in rates:
+        count = int(min(400, max(100, 4 * rate)))
         t, ns, nr = pi.serve_requests(count, rate, 64, 4096, 16, int(rate))
         keys = np.array(sorted(pool))
         reqs = []
@@ -423,8 +440,19 @@ def form_served(prrp, ctx, rates=(300.0, 3000.0), count=400, budget=64 << 30, pl
         st = srv.stats()
         srv.close()
         worst = max(r["eta"] for r in results)
-        out[f"rate={rate:g}/s"] = {"solves_per_s": st["solves_per_s"], "p50_ms": st["p50_us"] / 1e3,
-                                   "p99_ms": st["p99_us"] / 1e3, "max_eta": worst,
+        qms = [r["queue_us"] / 1e3 for r in results]
+        svc = [(r["latency_us"] - r["queue_us"]) / 1e3 for r in results]
+        small = [s_ for s_, (A, _, _) in zip(svc, reqs) if A.shape[0] <= 512]
+        large = [s_ for s_, (A, _, _) in zip(svc, reqs) if A.shape[0] > 512]
+        qq = max(1, len(qms) // 4)
+        out[f"rate={rate:g}/s"] = {"requests": count, "solves_per_s": st["solves_per_s"],
+                                   "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+                                   "queue_p50_ms": _pct(qms, 50), "queue_p99_ms": _pct(qms, 99),
+                                   "service_p50_ms": _pct(svc, 50), "service_p99_ms": _pct(svc, 99),
+                                   "service_small_p50_ms": _pct(small, 50), "service_large_p50_ms": _pct(large, 50),
+                                   "service_large_p99_ms": _pct(large, 99),
+                                   "queue_growth": float(np.mean(qms[-qq:]) / max(np.mean(qms[:qq]), 1e-3)),
+                                   "max_eta": worst,
                                    "failed": sum(1 for r in results if r["status"] != 0),
                                    "peak_busy_lanes": st["peak_busy_lanes"],
                                    "peak_GB_in_use": st["peak_bytes_in_use"] / 2**30}
@@ -444,8 +472,8 @@ def form_served(prrp, ctx, rates=(300.0, 3000.0), count=400, budget=64 << 30, pl
                          "sample": f"first {len(sample)} requests of the last stream, back to back"}
     best = max(v["solves_per_s"] for k, v in out.items() if k.startswith("rate="))
     out["speedup_vs_plain_fp64"] = best / out["plain_fp64"]["solves_per_s"]
-    return {"workload": f"{count} requests per rate, n log-uniform [64, 4096], nrhs 1..16, "
-                        f"64 GB admission budget, 4 lanes", "runs": out}
+    return {"workload": "Poisson arrivals at each rate for about 4 s (100-400 requests), n log-uniform "
+                        "[64, 4096], nrhs 1..16, 64 GB admission budget, 4 lanes", "runs": out}
 
 
 def run_ours(args) -> None:
@@ -612,7 +640,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the mixed-precision, batched and served measurements")
-    ap.add_argument("--form", choices=["mixed", "batched", "served", "update", "fp64_emu", "mixed_tf32"],
+    ap.add_argument("--form", choices=["mixed", "batched", "served", "update", "fp64_emu", "mixed_tf32",
+                                       "kappa_sweep"],
                     help="run only one of the other forms and print its JSON")
     ap.add_argument("--count", type=int, default=4096,
                     help="--form batched: number of systems (smaller batches for profiling)")
@@ -647,7 +676,13 @@ def main():
                                             n=args.n if args.n != N_DEFAULT else 16384),
               "fp64_emu": lambda: form_mixed(prrp, ctx, torch, dev, n=args.n, kappas=(0.0,), prec=4),
               "mixed_tf32": lambda: form_mixed(prrp, ctx, torch, dev, kappas=(1e2, 1e4), prec=1,
-                                               plain=False)}[args.form]
+                                               plain=False),
+              "kappa_sweep": lambda: {
+                  "workload": "n=16384 cond-controlled A, kappa 1e2..1e6, 4 RHS: 3xBF16 and TF32 updates",
+                  "bf16x3": form_mixed(prrp, ctx, torch, dev, kappas=(1e2, 1e3, 1e4, 1e5, 1e6), prec=2,
+                                       plain=False),
+                  "tf32": form_mixed(prrp, ctx, torch, dev, kappas=(1e2, 1e3, 1e4, 1e5, 1e6), prec=1,
+                                     plain=False)}}[args.form]
         out = fn()
         if dist is None or dist.get_rank() == 0:
             print(json.dumps({"form": args.form, **out}), flush=True)
