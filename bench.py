@@ -279,6 +279,49 @@ def form_mixed(prrp, ctx, torch, dev, n=16384, kappas=(1e2, 1e6), prec=2, steps=
     return {"workload": f"n={n}, b=64, tau=2, {mat}, 4 RHS, {upd} Schur update + FP64 refinement", "runs": out}
 
 
+def form_calu(prrp, ctx, torch, dev, n=8192, b=64, leaves=(64, 128), reps=2):
+    """CALU_PRRP (Section 3, tournament pivoting over leaves of leaf_rows rows) beside
+    LU_PRRP on the same iid N(0,1) matrix: factor + one-RHS solve refined to eta <= 2^-53,
+    in FP64 and with the 3xBF16 tensor-core update; the growth factor against Section 3.2's
+    bound.  Best of `reps` after a warm-up."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(8192)
+    A0 = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+    B0 = torch.randn(n, 1, dtype=torch.float64, device=dev, generator=g)
+    A = torch.empty_like(A0)
+    B = torch.empty_like(B0)
+    out = {}
+    for prec, pname in ((0, "fp64"), (2, "bf16x3")):
+        for leaf in (0,) + tuple(leaves):
+            times, st, info = [], None, None
+            for it in range(reps + 1):
+                A.copy_(A0)
+                B.copy_(B0)
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                if leaf:
+                    F = prrp.prrp_factor_calu(ctx, A, leaf, b=b, prec=prec)
+                else:
+                    F = prrp.prrp_factor(ctx, A, b=b, prec=prec)
+                info = prrp.prrp_solve(ctx, F, B, A_orig=A0, refine_max_iter=30)
+                torch.cuda.synchronize(dev)
+                if it:
+                    times.append(time.perf_counter() - t0)
+                st = F.stats()
+                F.close()
+            dt = min(times)
+            nleaf = max(1, n // leaf) if leaf else 1
+            height = int(math.ceil(math.log2(nleaf))) if nleaf > 1 else 0
+            key = f"{pname}, " + (f"CALU_PRRP leaf={leaf}" if leaf else "LU_PRRP")
+            out[key] = {"s": dt, "tflops": 2 * n ** 3 / 3 / dt / 1e12, "eta": info["eta"],
+                        "iterations": info["iterations"], "growth": st["growth"], "max_l21": st["max_l21"],
+                        "swaps": st["swaps"], "tree_height_first_panel": height,
+                        "log10_growth_bound": ((n / b) * (height + 1) - 1) * math.log10(1 + 2.0 * b)}
+    del A0, A, B0, B
+    torch.cuda.empty_cache()
+    return {"workload": f"n={n}, b={b}, tau=2, A iid N(0,1), 1 RHS refined to FP64 level", "runs": out}
+
+
 def wilkinson_check(prrp, ctx, torch, dev, n=2048, taus=2.0):
     """The n = 2048 Wilkinson matrix (1 on the diagonal, -1 strictly below, 1 in the last
     column), on which GEPP grows as 2^(n-1): LU_PRRP's growth factor against the bound
@@ -570,6 +613,7 @@ def run_ours(args) -> None:
         forms["served"] = form_served(prrp, ctx)
         forms["fp64_emu"] = form_mixed(prrp, ctx, torch, dev, n=n, kappas=(0.0,), prec=4)
         forms["mixed_tf32"] = form_mixed(prrp, ctx, torch, dev, kappas=(1e2, 1e4), prec=1, plain=False)
+        forms["calu"] = form_calu(prrp, ctx, torch, dev)
     if rank == 0:
         csum = clocks.summary()
         up = kstats["update"]
@@ -641,7 +685,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the mixed-precision, batched and served measurements")
     ap.add_argument("--form", choices=["mixed", "batched", "served", "update", "fp64_emu", "mixed_tf32",
-                                       "kappa_sweep"],
+                                       "kappa_sweep", "calu"],
                     help="run only one of the other forms and print its JSON")
     ap.add_argument("--count", type=int, default=4096,
                     help="--form batched: number of systems (smaller batches for profiling)")
@@ -677,6 +721,7 @@ def main():
               "fp64_emu": lambda: form_mixed(prrp, ctx, torch, dev, n=args.n, kappas=(0.0,), prec=4),
               "mixed_tf32": lambda: form_mixed(prrp, ctx, torch, dev, kappas=(1e2, 1e4), prec=1,
                                                plain=False),
+              "calu": lambda: form_calu(prrp, ctx, torch, dev),
               "kappa_sweep": lambda: {
                   "workload": "n=16384 cond-controlled A, kappa 1e2..1e6, 4 RHS: 3xBF16 and TF32 updates",
                   "bf16x3": form_mixed(prrp, ctx, torch, dev, kappas=(1e2, 1e3, 1e4, 1e5, 1e6), prec=2,

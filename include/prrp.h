@@ -130,6 +130,26 @@ prrp_status prrp_destroy(prrp_ctx* ctx);
 prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts,
                         void* stream, prrp_factors** F);
 
+/*
+ * prrp_factor_calu - CALU_PRRP (Section 3): prrp_factor with the panel pivots of step 1
+ * chosen by tournament pivoting (Section 3.1) instead of one strong RRQR of the whole
+ * panel.  The panel's rows are cut into leaves of leaf_rows rows (the last leaf takes the
+ * remainder; a panel of fewer than 2 leaf_rows rows is one leaf); the strong RRQR of each
+ * leaf's transpose selects w candidates, which lead their leaf; a binary tree then merges
+ * consecutive nodes, left then right, by the strong RRQR of the 2w candidates, the
+ * selected rows taking the left node's positions (an unpaired node goes up unchanged).
+ * Each node's interchanges move whole rows.  L21 = (R11^-1 R12)^T then comes from the
+ * unpivoted QR of the permuted panel, so |L21| is no longer bounded by tau; Section 3.2
+ * bounds the growth by (1 + tau b)^((n/b)(H+1) - 1), H the height of the tree.  Steps 3
+ * to 6 are those of prrp_factor, in every precision mode.  With one leaf per panel
+ * (leaf_rows >= n) the pivots are those of prrp_factor.
+ * Requires b <= 64 and b <= leaf_rows <= 128 (UNSUPPORTED for b > 64 or leaf_rows > 128,
+ * INVALID_ARG for leaf_rows < max(b, 1)); the context keeps an n x n workspace for the row
+ * moves.  Other arguments, outputs and errors as prrp_factor.
+ */
+prrp_status prrp_factor_calu(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts, int leaf_rows,
+                             void* stream, prrp_factors** F);
+
 /* Copy the permutation (n ints, may be NULL) and statistics (may be NULL) to the host. */
 prrp_status prrp_factors_get(const prrp_factors* F, int* hperm, prrp_factor_stats* stats);
 

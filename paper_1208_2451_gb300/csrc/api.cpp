@@ -114,6 +114,10 @@ struct prrp_ctx {
   size_t krylov_cap = 0;
   double* gm_coef = nullptr;
   size_t gm_coef_cap = 0;
+  int* calu_pmap = nullptr;         // CALU_PRRP: tournament position -> panel row
+  int* calu_ptmp = nullptr;         //   row moves through tmp
+  double* calu_tmp = nullptr;
+  size_t calu_cap = 0;              //   rows of n doubles the tmp holds (n of the factorization)
   unsigned* gemm_ctr = nullptr;     // tile counters of the FP64 updates (critical, rest stream)
   size_t gemm_ctr_cap = 0;
   unsigned long long factor_gen = 0;
@@ -286,7 +290,7 @@ prrp_status ensure_panel_ws(prrp_ctx* ctx, int n, int w, int max_swaps) {
 // and the pair counter first.
 prrp_status enqueue_panel(prrp_ctx* ctx, const double* P, long long ldp, int m, int w, double tau,
                           int max_swaps, int col_offset, double* L21, int ldl, int* order,
-                          int* pairs, cudaStream_t s, int max_ctas = 0) {
+                          int* pairs, cudaStream_t s, int max_ctas = 0, int nopivot = 0) {
   int G = 0, rpc = 0;
   prrp_status ps = panel_grid(ctx, m, w, &G, &rpc, max_ctas);
   if (ps != PRRP_OK) return ps;
@@ -298,6 +302,7 @@ prrp_status enqueue_panel(prrp_ctx* ctx, const double* P, long long ldp, int m, 
   p.col_offset = col_offset; p.L21 = L21; p.ldl = ldl; p.order = order; p.pairs = pairs;
   p.st = ctx->st; p.xval = ctx->xval; p.xkey = ctx->xkey; p.xvec = ctx->xvec; p.rows_per_cta = rpc;
   p.qkey = ctx->qkey; p.qrow = ctx->qrow;
+  p.nopivot = nopivot;
   p.cluster_rows = ctx->panel_cluster_rows;
   cudaError_t e = launch_panel(p, G, s);
   if (e == cudaErrorCooperativeLaunchTooLarge) return PRRP_ERR_UNSUPPORTED;
@@ -402,7 +407,8 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
   void* ptrs[] = {ctx->st, ctx->xval, ctx->xkey, ctx->xvec, ctx->qkey, ctx->qrow, ctx->pairs, ctx->ipiv, ctx->order,
                   ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB, ctx->tcws,
                   ctx->l21b, ctx->a12, ctx->tcws2, ctx->dinv64, ctx->dinv32, ctx->lu32, ctx->y32,
-                  ctx->tcount, ctx->zbuf, ctx->gemm_ctr, ctx->krylov, ctx->gm_coef, ctx->tcws3, ctx->tri};
+                  ctx->tcount, ctx->zbuf, ctx->gemm_ctr, ctx->krylov, ctx->gm_coef, ctx->tcws3, ctx->tri,
+                  ctx->calu_pmap, ctx->calu_ptmp, ctx->calu_tmp};
   for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
   if (ctx->s_rest) cudaStreamDestroy(ctx->s_rest);
   if (ctx->s_blk) cudaStreamDestroy(ctx->s_blk);
@@ -412,8 +418,14 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
   return PRRP_OK;
 }
 
-prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts_in,
-                        void* stream, prrp_factors** F) {
+}  // extern "C"
+
+namespace {
+
+// Algorithm 1 (leaf_rows == 0: LU_PRRP) or CALU_PRRP (Section 3.1: panel pivots from a
+// tournament over leaves of leaf_rows rows, then L21 from an unpivoted QR of the panel).
+prrp_status factor_impl(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts_in,
+                        int leaf_rows, void* stream, prrp_factors** F) {
   if (!ctx || !F) return PRRP_ERR_INVALID_ARG;
   *F = nullptr;
   prrp_opts o;
@@ -423,6 +435,8 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
   prrp_status ps = check_opts(&o);
   if (ps != PRRP_OK) return ps;
   if (o.prec == PRRP_FP32 || (o.prec == PRRP_FP64_EMU && o.b > 64)) return PRRP_ERR_UNSUPPORTED;
+  if (leaf_rows < 0 || (leaf_rows > 0 && leaf_rows < o.b)) return PRRP_ERR_INVALID_ARG;
+  if (leaf_rows > 0 && (o.b > 64 || leaf_rows > 128)) return PRRP_ERR_UNSUPPORTED;
   if (n > 65536) return PRRP_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaSetDevice(ctx->device));
@@ -469,6 +483,17 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
       return fail(cuda_fail(ctx, e, "stream create"));
   }
   if ((ps = grow(ctx, &ctx->l21b, &ctx->l21b_cap, (size_t)n * b)) != PRRP_OK) return fail(ps);
+  if (leaf_rows > 0 && ctx->calu_cap < (size_t)n) {
+    // the tournament's row moves go through an n x n buffer (the first panel moves rows of
+    // all n columns)
+    size_t c1 = 0, c2 = 0, c3 = 0;
+    if (ctx->calu_tmp) { cudaFree(ctx->calu_tmp); cudaFree(ctx->calu_pmap); cudaFree(ctx->calu_ptmp); }
+    ctx->calu_tmp = nullptr; ctx->calu_pmap = nullptr; ctx->calu_ptmp = nullptr; ctx->calu_cap = 0;
+    if ((ps = grow(ctx, &ctx->calu_tmp, &c1, (size_t)n * n)) != PRRP_OK) return fail(ps);
+    if ((ps = grow(ctx, &ctx->calu_pmap, &c2, (size_t)n)) != PRRP_OK) return fail(ps);
+    if ((ps = grow(ctx, &ctx->calu_ptmp, &c3, (size_t)n)) != PRRP_OK) return fail(ps);
+    ctx->calu_cap = n;
+  }
   if ((ps = grow(ctx, &ctx->a12, &ctx->a12_cap, 2 * (size_t)n * b)) != PRRP_OK) return fail(ps);
   if (o.prec != PRRP_FP64 &&
       (ps = grow(ctx, &ctx->tcws2, &ctx->tcws2_cap, tc_workspace_bytes(o.prec, n, b, b))) != PRRP_OK)
@@ -519,13 +544,47 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
     double* Akk = dA + (long long)k0 * lda + k0;
     double* L21 = (jp & 1) ? ctx->l21b : ctx->l21;
     double* A12 = ctx->a12 + (size_t)(jp & 1) * n * b;     // snapshot: w x nc, ld nc
-    {
-      Timed t(ctx, s, PRRP_KIND_PANEL, 3LL * m * w * w);
-      ps = enqueue_panel(ctx, Akk, lda, m, w, o.tau, o.max_swaps, k0, L21, w, nullptr, ctx->pairs, s, cap_panel);
+    if (leaf_rows == 0) {
+      {
+        Timed t(ctx, s, PRRP_KIND_PANEL, 3LL * m * w * w);
+        ps = enqueue_panel(ctx, Akk, lda, m, w, o.tau, o.max_swaps, k0, L21, w, nullptr, ctx->pairs, s, cap_panel);
+      }
+      if (ps != PRRP_OK) return fail(ps);
+      if (ev_rest) CK(cudaStreamWaitEvent(s, ev_rest, 0));
+      if (ev_blk) CK(cudaStreamWaitEvent(s, ev_blk, 0));
+    } else {
+      // CALU_PRRP: the tournament reads only the panel's columns; its row moves (whole
+      // rows) wait for the rest update and the block work of the previous panel; then
+      // L21 from the unpivoted QR of the permuted panel (no row moves of its own).
+      TournParams tp{};
+      tp.P = Akk; tp.ldp = lda; tp.m = m; tp.w = w; tp.leaf = leaf_rows;
+      tp.nleaf = std::max(1, m / leaf_rows);
+      int h = 0;
+      while ((1 << h) < tp.nleaf) ++h;
+      tp.height = h;
+      tp.tau = o.tau; tp.max_swaps = o.max_swaps; tp.col_offset = k0; tp.pmap = ctx->calu_pmap; tp.st = ctx->st;
+      {
+        Timed t(ctx, s, PRRP_KIND_PANEL, 3LL * m * w * w);
+        e = launch_iota(ctx->calu_pmap, m, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&ctx->st->barrier, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = launch_tournament(tp, std::min(ctx->num_sms, kPanelMaxCtas), s);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "tournament"));
+      if (ev_rest) CK(cudaStreamWaitEvent(s, ev_rest, 0));
+      if (ev_blk) CK(cudaStreamWaitEvent(s, ev_blk, 0));
+      {
+        Timed t(ctx, s, PRRP_KIND_PERMUTE);
+        e = launch_gather_permute(dA, lda, n, k0, m, ctx->calu_pmap, f->perm, ctx->calu_tmp, ctx->calu_ptmp,
+                                  ctx->st, s);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "tournament row moves"));
+      {
+        Timed t(ctx, s, PRRP_KIND_PANEL, 3LL * m * w * w);
+        ps = enqueue_panel(ctx, Akk, lda, m, w, o.tau, o.max_swaps, k0, L21, w, nullptr, ctx->pairs, s, cap_panel,
+                           1);
+      }
+      if (ps != PRRP_OK) return fail(ps);
     }
-    if (ps != PRRP_OK) return fail(ps);
-    if (ev_rest) CK(cudaStreamWaitEvent(s, ev_rest, 0));
-    if (ev_blk) CK(cudaStreamWaitEvent(s, ev_blk, 0));
     {
       Timed t(ctx, s, PRRP_KIND_PERMUTE);
       e = launch_permute(dA, lda, n, k0, ctx->pairs, max_pairs, f->perm, ctx->st, s);
@@ -622,6 +681,24 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
     return (prrp_status)h.status;
   }
   return PRRP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts_in,
+                        void* stream, prrp_factors** F) {
+  return factor_impl(ctx, n, dA, lda, opts_in, 0, stream, F);
+}
+
+prrp_status prrp_factor_calu(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts, int leaf_rows,
+                             void* stream, prrp_factors** F) {
+  if (leaf_rows < 1) {
+    if (F) *F = nullptr;
+    return PRRP_ERR_INVALID_ARG;
+  }
+  return factor_impl(ctx, n, dA, lda, opts, leaf_rows, stream, F);
 }
 
 prrp_status prrp_factors_get(const prrp_factors* F, int* hperm, prrp_factor_stats* stats) {

@@ -34,11 +34,37 @@ struct PanelParams {
   double* qrow;               // QRCP records [3][G][kQStride]
   int rows_per_cta;
   int cluster_rows;       // panels of at most this many rows run as one cluster (0: default)
+  int nopivot;            // 1: unpivoted QR of the panel (CALU_PRRP's L21), no interchanges
 };
 
 int panel_width_class(int w);
 size_t panel_smem_for(int w, int rows_per_cta);
 cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t stream);
+// A cooperative launch that waits, through a per-device event chain, for the previous
+// cooperative launch of the library on any stream (two partially resident cooperative
+// grids could otherwise wait on each other).
+cudaError_t launch_cooperative_chained(const void* func, int grid, int threads, void** args, size_t smem,
+                                       cudaStream_t stream);
+
+// CALU_PRRP tournament (Section 3.1) on the m x w panel P (row-major, ldp): leaves of
+// `leaf` rows (the last takes the remainder), a binary tree of strong RRQRs, one CTA per
+// node.  pmap (m ints, identity on entry) receives position -> panel row.  w <= 64,
+// w <= leaf <= 128.  Interchanges are added to st->swaps_total.
+struct TournParams {
+  const double* P;
+  long long ldp;
+  int m, w, leaf, nleaf, height;
+  double tau;
+  int max_swaps;
+  int col_offset;
+  int* pmap;
+  DevState* st;
+};
+cudaError_t launch_tournament(const TournParams& p, int num_sms, cudaStream_t s);
+// Rows k0 + i (all n columns) and perm[k0 + i] take those at k0 + pmap[i], i < m, through
+// tmp (m x n doubles) and ptmp (m ints); rows with pmap[i] == i are not touched.
+cudaError_t launch_gather_permute(double* A, long long lda, int n, int k0, int m, const int* pmap, int* perm,
+                                  double* tmp, int* ptmp, DevState* st, cudaStream_t s);
 
 // max |a_ij| and non-finite detection over an n x n row-major matrix.
 cudaError_t launch_scan(const double* A, long long lda, int n, DevState* st, cudaStream_t s);

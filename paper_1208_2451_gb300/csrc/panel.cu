@@ -62,8 +62,11 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "select.cuh"
 
 namespace prrp {
+
+using namespace sel;
 
 namespace {
 
@@ -86,79 +89,6 @@ constexpr unsigned long long kSentinel = 0x7FF8DEADBEEF0001ull;
 std::mutex g_coop_mu;
 cudaEvent_t g_coop_done[64] = {};
 
-// A proposal in an argmax.  The value is a non-negative double (a squared norm or |M_ij|)
-// kept as its IEEE bit pattern: for x, y >= 0, x < y exactly when bits(x) < bits(y), so
-// the reduction trees compare on the integer pipe instead of the (1/64-rate) FP64 pipe.
-struct Cand {
-  unsigned long long v;   // bits of the value to maximize (0 with k1 = INT_MAX: none)
-  int k1;                 // first tie-break, ascending (position, or remaining slot j)
-  int k2;                 // second tie-break, ascending (selected slot i)
-  int aux;                // payload: local row index, or proposing CTA
-};
-
-__device__ __forceinline__ unsigned long long vbits(double x) {
-  return static_cast<unsigned long long>(__double_as_longlong(x));
-}
-__device__ __forceinline__ double vval(unsigned long long b) {
-  return __longlong_as_double(static_cast<long long>(b));
-}
-
-__device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
-  if (a.v != b.v) return a.v > b.v;
-  if (a.k1 != b.k1) return a.k1 < b.k1;
-  return a.k2 < b.k2;
-}
-
-// The best candidate of a full warp (largest value, then smallest k1, then smallest k2),
-// returned in every lane: warp-wide max/min reductions on the value's two halves and on
-// the tie-breaks, then the payload from the winning lane.
-__device__ __forceinline__ Cand warp_argmax(const Cand& c) {
-  const unsigned full = 0xffffffffu;
-  const unsigned hi = static_cast<unsigned>(c.v >> 32), lo = static_cast<unsigned>(c.v);
-  const unsigned mhi = __reduce_max_sync(full, hi);
-  const unsigned mlo = __reduce_max_sync(full, hi == mhi ? lo : 0u);
-  const bool eq = hi == mhi && lo == mlo;
-  const int mk1 = __reduce_min_sync(full, eq ? c.k1 : 0x7fffffff);
-  const bool eq1 = eq && c.k1 == mk1;
-  const int mk2 = __reduce_min_sync(full, eq1 ? c.k2 : 0x7fffffff);
-  const unsigned who = __ballot_sync(full, eq1 && c.k2 == mk2);
-  Cand r;
-  r.v = (static_cast<unsigned long long>(mhi) << 32) | mlo;
-  r.k1 = mk1;
-  r.k2 = mk2;
-  r.aux = __shfl_sync(full, c.aux, __ffs(who) - 1);
-  return r;
-}
-
-// QRCP proposals carry one 64-bit key: the squared norm's IEEE bits with the low kPosBits
-// bits replaced by (kPosMask - position).  The largest key is the largest norm, ties (and
-// norms equal to 2^-32 relative, far inside the 1e-8 decision margin) to the smallest
-// position.  A key without norm bits (zero norm) is at least kPosMask - (m - 1) > 1, so it
-// still beats kNoCand, the key of a CTA without remaining rows; 0 marks an empty slot.
-constexpr int kPosBits = 20;
-constexpr unsigned long long kPosMask = (1ull << kPosBits) - 1;
-constexpr unsigned long long kNoCand = 1ull;
-__device__ __forceinline__ unsigned long long qrcp_key(double nrm, int pos) {
-  const long long b = __double_as_longlong(nrm);
-  return (static_cast<unsigned long long>(b < 0 ? 0 : b) & ~kPosMask) | (kPosMask - static_cast<unsigned>(pos));
-}
-__device__ __forceinline__ int key_pos(unsigned long long k) { return static_cast<int>(kPosMask - (k & kPosMask)); }
-
-// The largest key of a full warp with the payload of its lane (keys are unique or equal to
-// kNoCand / 0, where any lane's payload will do).
-__device__ __forceinline__ Cand warp_max_key(const Cand& c) {
-  const unsigned full = 0xffffffffu;
-  const unsigned hi = static_cast<unsigned>(c.v >> 32), lo = static_cast<unsigned>(c.v);
-  const unsigned mhi = __reduce_max_sync(full, hi);
-  const unsigned mlo = __reduce_max_sync(full, hi == mhi ? lo : 0u);
-  Cand r;
-  r.v = (static_cast<unsigned long long>(mhi) << 32) | mlo;
-  r.k1 = 0;
-  r.k2 = 0;
-  r.aux = __shfl_sync(full, c.aux, __ffs(__ballot_sync(full, c.v == r.v)) - 1);
-  return r;
-}
-
 // Lanes per row team for panels of width class W.  With up to ~190 rows per CTA, teams of
 // 4 lanes (8 at W = 128) fill whole warp passes on several sub-partitions, two warps each;
 // with more rows, one lane per row (2 at W = 128) needs about 40% fewer FP64 instructions
@@ -168,14 +98,6 @@ __host__ __device__ constexpr int panel_team(int W, bool many_rows) {
   return many_rows ? (W >= 128 ? 2 : 1) : (W >= 128 ? 8 : 4);
 }
 constexpr int kManyRows = 192;     // rows per CTA from which the one-lane-per-row form runs
-
-// The reflector of x = B(t:w, row) from its first entry x0 and ||x||^2:
-// H = I - beta v v^T, H x = alpha e_1, v = x - alpha e_1, v^T v = 2 ||x|| (||x|| + |x0|).
-__device__ __forceinline__ void reflector(double x0, double nrm2, double* alpha, double* beta) {
-  const double normx = sqrt(nrm2);
-  *alpha = (x0 >= 0.0) ? -normx : normx;
-  *beta = 1.0 / (normx * (normx + abs_int(x0)));
-}
 
 // ---- global-memory signalling (grid form) ----
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
@@ -197,21 +119,6 @@ __device__ __forceinline__ void named_sync(int id, int count) {
 }
 __device__ __forceinline__ void named_arrive(int id, int count) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
-// Sum over the TEAM lanes of a row team.  Every lane receives the same bits: the xor
-// butterfly adds the same pairs in each lane, only commuted.
-template <int TEAM>
-__device__ __forceinline__ double team_sum(double s, unsigned tmask) {
-#pragma unroll
-  for (int off = 1; off < TEAM; off <<= 1) s += __shfl_xor_sync(tmask, s, off);
-  return s;
-}
-
-// (a > b) for non-negative b: signed compare of the IEEE bit patterns (a negative a, or a
-// -0, compares below every positive b; nan above).
-__device__ __forceinline__ bool gt_nonneg(double a, double b) {
-  return __double_as_longlong(a) > __double_as_longlong(b);
 }
 
 // ---- distributed shared memory of a thread-block cluster (cluster form) ----
@@ -507,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1) panel_rrqr_kernel(PanelParams p) 
           }
         }
       }
-      if (ok && (g.v >> kPosBits) == 0ull) {    // the largest remaining norm is zero: rank < w
+      if (ok && key_norm_zero(g.v)) {           // the largest remaining norm is zero: rank < w
         if (cta == 0 && lane == 0) set_error(st, PRRP_ERR_SINGULAR, p.col_offset + t + 1);
         ok = 0;
       }
@@ -578,7 +485,9 @@ __global__ void __launch_bounds__(kThreads, 1) panel_rrqr_kernel(PanelParams p) 
         thr[r] = 1e-4 * s;
         pos[r] = r0 + r;
         pend[r] = 0;
-        const unsigned long long k = qrcp_key(s, r0 + r);
+        // unpivoted QR (CALU_PRRP's L21): the row at position 0 is the only proposal
+        const unsigned long long k =
+            p.nopivot ? (r0 + r == 0 ? qrcp_key(s, 0) | kTopBit : 0ull) : qrcp_key(s, r0 + r);
         if (k > kbest) { kbest = k; rbest = r; }
       }
     }
@@ -656,7 +565,8 @@ __global__ void __launch_bounds__(kThreads, 1) panel_rrqr_kernel(PanelParams p) 
           pos[r] = np;
           fpend[r] = f;
           pend[r] = defer;
-          const unsigned long long k = qrcp_key(n2, np);
+          const unsigned long long k =
+              p.nopivot ? (np == t + 1 ? qrcp_key(n2, np) | kTopBit : 0ull) : qrcp_key(n2, np);
           if (k > kbest) { kbest = k; rbest = r; }
         }
       }
@@ -710,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, 1) panel_rrqr_kernel(PanelParams p) 
   // ---------------- tau-bounded interchanges ----------------
   {
   int swaps = 0;
-  for (int it = 0;; ++it) {
+  for (int it = 0; !p.nopivot; ++it) {
     const int par = it & 1;
     if (warp >= kRowWarp0) {
       Cand c{0ull, 0x7fffffff, 0x7fffffff, -1};
@@ -987,6 +897,24 @@ cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t stream) {
     case 64: e = launch_panel_w<64>(p, G, stream); break;
     default: e = launch_panel_w<128>(p, G, stream); break;
   }
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(g_coop_done[dev], stream);
+}
+
+cudaError_t launch_cooperative_chained(const void* func, int grid, int threads, void** args, size_t smem,
+                                       cudaStream_t stream) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_coop_mu);
+  if (!g_coop_done[dev]) {
+    e = cudaEventCreateWithFlags(&g_coop_done[dev], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaStreamWaitEvent(stream, g_coop_done[dev], 0);
+  if (e != cudaSuccess) return e;
+  e = cudaLaunchCooperativeKernel(func, dim3(grid), dim3(threads), args, smem, stream);
   if (e != cudaSuccess) return e;
   return cudaEventRecord(g_coop_done[dev], stream);
 }
