@@ -6,10 +6,12 @@ Only tests/, __graft_entry__.smoke() and bench.py's CPU legs (``cpu_baseline`` a
 """
 from .algorithm import (LUResult, NonFiniteError, PanelResult, SingularError, SwapLimitError,
                       eta, householder_qr, lu_prrp, lu_solve, qrcp, refine, selection_multipliers, strong_rrqr, unpack)
+from .block_lu import BlockLUResult, block_lu_prrp, block_solve
 from .calu import CALUResult, calu_growth_bound_log10, calu_prrp
 from . import metrics
 
 __all__ = ["LUResult", "NonFiniteError", "PanelResult", "SingularError", "SwapLimitError", "eta",
            "householder_qr", "lu_prrp", "lu_solve", "qrcp", "refine", "selection_multipliers",
            "strong_rrqr", "unpack", "CALUResult", "calu_prrp", "calu_growth_bound_log10",
+           "BlockLUResult", "block_lu_prrp", "block_solve",
            "metrics"]
