@@ -322,6 +322,49 @@ def form_calu(prrp, ctx, torch, dev, n=8192, b=64, leaves=(64, 128), reps=2):
     return {"workload": f"n={n}, b={b}, tau=2, A iid N(0,1), 1 RHS refined to FP64 level", "runs": out}
 
 
+def form_block_study(prrp, ctx, torch, dev, n=2048, seeds=(0, 1)):
+    """Block parallel / block pairwise LU_PRRP (Section 5) on the GPU, as a stability study:
+    growth factor g_W and max |D| per (b, P) on iid N(0,1) matrices, beside LU_PRRP's growth
+    on the same matrices, and the factorization time (mean over the seeds)."""
+    out = {}
+    mats = []
+    for sd in seeds:
+        g = torch.Generator(device=dev)
+        g.manual_seed(20480 + sd)
+        mats.append(torch.randn(n, n, dtype=torch.float64, device=dev, generator=g))
+    for b in (8, 16):
+        gl = []
+        for A0 in mats:
+            A = A0.clone()
+            F = prrp.prrp_factor(ctx, A, b=b)
+            gl.append(F.stats()["growth"])
+            F.close()
+        out[f"b={b}, LU_PRRP"] = {"growth": float(np.mean(gl))}
+        for tree in ("parallel", "pairwise"):
+            for P in (8, 16, 32):
+                gs, ds, ts = [], [], []
+                try:
+                    for A0 in mats:
+                        A = A0.clone()
+                        torch.cuda.synchronize(dev)
+                        t0 = time.perf_counter()
+                        F = prrp.prrp_factor_block(ctx, A, P, tree=tree, b=b)
+                        torch.cuda.synchronize(dev)
+                        ts.append(time.perf_counter() - t0)
+                        st = F.stats()
+                        gs.append(st["growth"])
+                        ds.append(st["max_l21"])
+                        F.close()
+                except prrp.PrrpError as e:
+                    out[f"b={b}, {tree}, P={P}"] = {"unsupported": e.name}
+                    continue
+                out[f"b={b}, {tree}, P={P}"] = {"growth": float(np.mean(gs)), "max_D": float(max(ds)),
+                                                "s": float(np.mean(ts))}
+    del mats
+    torch.cuda.empty_cache()
+    return {"workload": f"n={n}, iid N(0,1), {len(seeds)} seeds, tau=2", "runs": out}
+
+
 def wilkinson_check(prrp, ctx, torch, dev, n=2048, taus=2.0):
     """The n = 2048 Wilkinson matrix (1 on the diagonal, -1 strictly below, 1 in the last
     column), on which GEPP grows as 2^(n-1): LU_PRRP's growth factor against the bound
@@ -685,7 +728,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the mixed-precision, batched and served measurements")
     ap.add_argument("--form", choices=["mixed", "batched", "served", "update", "fp64_emu", "mixed_tf32",
-                                       "kappa_sweep", "calu"],
+                                       "kappa_sweep", "calu", "block_study"],
                     help="run only one of the other forms and print its JSON")
     ap.add_argument("--count", type=int, default=4096,
                     help="--form batched: number of systems (smaller batches for profiling)")
@@ -722,6 +765,7 @@ def main():
               "mixed_tf32": lambda: form_mixed(prrp, ctx, torch, dev, kappas=(1e2, 1e4), prec=1,
                                                plain=False),
               "calu": lambda: form_calu(prrp, ctx, torch, dev),
+              "block_study": lambda: form_block_study(prrp, ctx, torch, dev),
               "kappa_sweep": lambda: {
                   "workload": "n=16384 cond-controlled A, kappa 1e2..1e6, 4 RHS: 3xBF16 and TF32 updates",
                   "bf16x3": form_mixed(prrp, ctx, torch, dev, kappas=(1e2, 1e3, 1e4, 1e5, 1e6), prec=2,

@@ -150,6 +150,28 @@ prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
 prrp_status prrp_factor_calu(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts, int leaf_rows,
                              void* stream, prrp_factors** F);
 
+/*
+ * prrp_factor_block - block parallel (tree = 0) or block pairwise (tree = 1) LU_PRRP
+ * (Section 5, algebra in Appendix E), for stability studies: the paper reports these
+ * variants as less stable than LU_PRRP and CALU_PRRP.  Per panel the active rows are cut
+ * into P' = max(1, min(blocks, m / (w + 1))) blocks of m / P' rows (the last takes the
+ * remainder).  A tree of strong RRQRs runs over them: block parallel, a binary tree (a
+ * merge node holds its children's selections, left then right); block pairwise, a flat
+ * tree (node i holds the running selection and all rows of block i).  Each node's
+ * permutation acts on its rows, so its selection leads; each row it does not select is
+ * eliminated at once, A_e(k0+w:n) -= D_e A_sel(k0+w:n) with D = (R11^-1 R12)^T (|D| <= tau),
+ * using rows not yet updated in this panel, and D_e is stored in the row's panel columns.
+ * The root's w rows lead the active rows; GEPP on their diagonal block and
+ * U12 = L11^-1 Pi_jj^T A12 follow.  On return dA holds those pivot rows' L11\U11 and U12,
+ * every eliminated row's D in the panel's columns, and F the permutation and statistics
+ * (growth = g_W over every updated row, max_l21 = max |D|).  The factorization is a
+ * product of lower triangular factors, not P A = L U: prrp_solve returns UNSUPPORTED for
+ * it.  FP64 only; b <= 64; every tree node must hold at most 255 rows (UNSUPPORTED
+ * otherwise: use more blocks).  Other arguments and errors as prrp_factor.
+ */
+prrp_status prrp_factor_block(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts, int blocks,
+                              int tree, void* stream, prrp_factors** F);
+
 /* Copy the permutation (n ints, may be NULL) and statistics (may be NULL) to the host. */
 prrp_status prrp_factors_get(const prrp_factors* F, int* hperm, prrp_factor_stats* stats);
 

@@ -55,6 +55,7 @@ _SIGS = {
     "prrp_destroy": (_I, [_P]),
     "prrp_factor": (_I, [_P, _I, _P, _I, C.POINTER(prrp_opts), _P, C.POINTER(_P)]),
     "prrp_factor_calu": (_I, [_P, _I, _P, _I, C.POINTER(prrp_opts), _I, _P, C.POINTER(_P)]),
+    "prrp_factor_block": (_I, [_P, _I, _P, _I, C.POINTER(prrp_opts), _I, _I, _P, C.POINTER(_P)]),
     "prrp_factors_get": (_I, [_P, _P, C.POINTER(prrp_factor_stats)]),
     "prrp_factors_perm_device": (_P, [_P]),
     "prrp_factors_destroy": (None, [_P]),
@@ -253,6 +254,27 @@ def prrp_factor_calu(ctx: Context, A, leaf_rows: int, b=64, tau=2.0, prec=PRRP_F
         _check(st, "prrp_factor_calu", ctx.handle)
     if F is not None:
         F.status = st
+    return F
+
+
+def prrp_factor_block(ctx: Context, A, blocks: int, tree: str = "parallel", b=16, tau=2.0, max_swaps=64,
+                      stream=None) -> Factors:
+    """Block parallel (tree="parallel") or block pairwise (tree="pairwise") LU_PRRP of the
+    square float64 CUDA tensor A in place, for stability studies (product form: no solve)."""
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("square matrix expected")
+    t = {"parallel": 0, "pairwise": 1}[tree]
+    lda = _dev_matrix(A, "A") if n else 1
+    o = default_opts(b, tau, PRRP_FP64, max_swaps)
+    h = C.c_void_p()
+    st = _lib.prrp_factor_block(ctx.handle, n, C.c_void_p(A.data_ptr() if n else 0), lda, C.byref(o),
+                                int(blocks), t, _stream_ptr(stream), C.byref(h))
+    F = Factors(h, n, A) if h.value else None
+    if st != PRRP_OK:
+        if F is not None:
+            F.close()
+        _check(st, "prrp_factor_block", ctx.handle)
     return F
 
 

@@ -156,6 +156,7 @@ struct prrp_factors {
   prrp_factor_stats stats{};
   prrp_opts opts{};
   unsigned long long gen = 0;   // identifies this factorization to the context's solve caches
+  int kind = 0;                 // 0: P A = L U; 1: block LU_PRRP's product form (no prrp_solve)
 };
 
 namespace {
@@ -562,6 +563,7 @@ prrp_status factor_impl(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
       int h = 0;
       while ((1 << h) < tp.nleaf) ++h;
       tp.height = h;
+      tp.mode = 0; tp.level0 = 0; tp.level1 = h + 1;      // the whole tree in one launch
       tp.tau = o.tau; tp.max_swaps = o.max_swaps; tp.col_offset = k0; tp.pmap = ctx->calu_pmap; tp.st = ctx->st;
       {
         Timed t(ctx, s, PRRP_KIND_PANEL, 3LL * m * w * w);
@@ -690,6 +692,105 @@ extern "C" {
 prrp_status prrp_factor(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts_in,
                         void* stream, prrp_factors** F) {
   return factor_impl(ctx, n, dA, lda, opts_in, 0, stream, F);
+}
+
+prrp_status prrp_factor_block(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts_in, int blocks,
+                              int tree, void* stream, prrp_factors** F) {
+  if (!ctx || !F) return PRRP_ERR_INVALID_ARG;
+  *F = nullptr;
+  prrp_opts o;
+  prrp_opts_default(&o);
+  if (opts_in) o = *opts_in;
+  if (n < 0 || lda < std::max(n, 1) || (n > 0 && !dA) || blocks < 1 || (tree != 0 && tree != 1))
+    return PRRP_ERR_INVALID_ARG;
+  prrp_status ps = check_opts(&o);
+  if (ps != PRRP_OK) return ps;
+  if (o.prec != PRRP_FP64 || o.b > 64 || n > 65536) return PRRP_ERR_UNSUPPORTED;
+  const int b = std::min(o.b, std::max(n, 1));
+  // every tree node must fit one CTA: the largest block (the last one) plus, for the flat
+  // tree, the running selection
+  for (int k0 = 0; k0 < n; k0 += b) {
+    const int w = std::min(b, n - k0), m = n - k0;
+    const int parts = std::max(1, std::min(blocks, m / (w + 1)));
+    const int q = m / parts, last = m - (parts - 1) * q;
+    const int rows = std::max(tree == 1 && parts > 1 ? w + last : last, parts > 1 ? 2 * w : 0);
+    if (rows > kTreeNodeMaxRows) return PRRP_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaSetDevice(ctx->device));
+  prrp_factors* f = new (std::nothrow) prrp_factors();
+  if (!f) return PRRP_ERR_OOM;
+  f->ctx = ctx; f->n = n; f->dA = dA; f->lda = lda; f->opts = o; f->gen = ++ctx->factor_gen; f->kind = 1;
+  auto fail = [&](prrp_status st) { prrp_factors_destroy(f); return st; };
+  cudaError_t e = cudaMalloc(&f->perm, sizeof(int) * std::max(n, 1));
+  if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "cudaMalloc perm"));
+  if (n == 0) { f->stats.growth = f->stats.growth_u = 1.0; *F = f; return PRRP_OK; }
+  if ((ps = ensure_panel_ws(ctx, n, b, o.max_swaps)) != PRRP_OK) return fail(ps);
+  if (ctx->calu_cap < (size_t)n) {
+    size_t c1 = 0, c2 = 0, c3 = 0;
+    if (ctx->calu_tmp) { cudaFree(ctx->calu_tmp); cudaFree(ctx->calu_pmap); cudaFree(ctx->calu_ptmp); }
+    ctx->calu_tmp = nullptr; ctx->calu_pmap = nullptr; ctx->calu_ptmp = nullptr; ctx->calu_cap = 0;
+    if ((ps = grow(ctx, &ctx->calu_tmp, &c1, (size_t)n * n)) != PRRP_OK) return fail(ps);
+    if ((ps = grow(ctx, &ctx->calu_pmap, &c2, (size_t)n)) != PRRP_OK) return fail(ps);
+    if ((ps = grow(ctx, &ctx->calu_ptmp, &c3, (size_t)n)) != PRRP_OK) return fail(ps);
+    ctx->calu_cap = n;
+  }
+  if ((e = cudaMemsetAsync(ctx->st, 0, sizeof(DevState), s)) != cudaSuccess) return fail(cuda_fail(ctx, e, "memset"));
+  if ((e = launch_iota(f->perm, n, s)) != cudaSuccess) return fail(cuda_fail(ctx, e, "iota"));
+  if ((e = launch_scan(dA, lda, n, ctx->st, s)) != cudaSuccess) return fail(cuda_fail(ctx, e, "scan"));
+  const int sms = std::min(ctx->num_sms, kPanelMaxCtas);
+  for (int k0 = 0; k0 < n; k0 += b) {
+    const int w = std::min(b, n - k0), m = n - k0;
+    const int parts = std::max(1, std::min(blocks, m / (w + 1)));
+    int height = 0;
+    if (tree == 0) while ((1 << height) < parts) ++height;
+    else height = parts - 1;
+    double* Akk = dA + (long long)k0 * lda + k0;
+    TournParams tp{};
+    tp.P = Akk; tp.Pw = Akk; tp.ldp = lda; tp.m = m; tp.w = w; tp.leaf = m / parts; tp.nleaf = parts;
+    tp.height = height; tp.mode = tree == 0 ? 1 : 2; tp.tau = o.tau; tp.max_swaps = o.max_swaps;
+    tp.col_offset = k0; tp.pmap = ctx->calu_pmap; tp.st = ctx->st;
+    {
+      Timed t(ctx, s, PRRP_KIND_PANEL, 3LL * m * w * w);
+      e = launch_iota(ctx->calu_pmap, m, s);
+      // each level: the nodes' selections (panel columns only), then their eliminations
+      for (int h = 0; h <= height && e == cudaSuccess; ++h) {
+        tp.level0 = h;
+        tp.level1 = h + 1;
+        e = launch_tournament(tp, sms, s);
+        if (e == cudaSuccess) e = launch_tree_eliminate(tp, dA, lda, n, k0, sms, s);
+      }
+    }
+    if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "block tree"));
+    {
+      Timed t(ctx, s, PRRP_KIND_PERMUTE);
+      e = launch_gather_permute(dA, lda, n, k0, m, ctx->calu_pmap, f->perm, ctx->calu_tmp, ctx->calu_ptmp,
+                                ctx->st, s);
+    }
+    if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "block row moves"));
+    {
+      Timed t(ctx, s, PRRP_KIND_DIAG, 2LL * w * w * w / 3);
+      e = launch_diag_gepp(dA, lda, k0, w, ctx->ipiv, f->perm, ctx->st, s);
+    }
+    if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "diag gepp"));
+    if (n > w) {
+      Timed t(ctx, s, PRRP_KIND_U12, 1LL * (n - k0 - w) * w * w);
+      e = launch_u12(dA, lda, n, k0, w, ctx->ipiv, ctx->st, s);
+    }
+    if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "u12"));
+  }
+  DevState h{};
+  if ((ps = read_state(ctx, &h, s)) != PRRP_OK) return fail(ps);
+  collect_timing(ctx);
+  f->stats.amax = bits_to_double(h.amax_bits);
+  f->stats.growth = f->stats.amax > 0 ? bits_to_double(h.gmax_bits) / f->stats.amax : 1.0;
+  f->stats.growth_u = f->stats.amax > 0 ? bits_to_double(h.umax_bits) / f->stats.amax : 1.0;
+  f->stats.max_l21 = bits_to_double(h.l21_bits);
+  f->stats.swaps = h.swaps_total;
+  f->stats.info = h.info;
+  f->stats.panels = (n + b - 1) / b;
+  *F = f;
+  return h.status != 0 ? (prrp_status)h.status : PRRP_OK;
 }
 
 prrp_status prrp_factor_calu(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_opts* opts, int leaf_rows,
@@ -842,6 +943,7 @@ prrp_status prrp_solve(prrp_ctx* ctx, const prrp_factors* F, const double* dA_or
     o.refine_target = opts_in->refine_target;
   }
   if (info) { info->iterations = 0; info->eta0 = -1.0; info->eta = -1.0; }
+  if (F->kind != 0) return PRRP_ERR_UNSUPPORTED;
   const int n = F->n;
   if (n == 0 || nrhs == 0) return PRRP_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -17,6 +17,12 @@
 // downdating with its recompute guard, back substitution and basis-exchange interchanges,
 // selection decided on FP64 values), so the tournament's pivots agree with the oracle's
 // wherever its decisions are untied.
+//
+// The same kernel runs the trees of block parallel and block pairwise LU_PRRP (Section 5,
+// Appendix E), one level per launch: there each node also eliminates the rows it does not
+// select, with D = (R11^-1 R12)^T written into their panel columns, and
+// tree_eliminate_kernel then applies A_e -= D_e A_sel to their trailing columns before the
+// next level's selection (which reads only panel columns of rows not yet updated).
 #include <algorithm>
 
 #include "common.cuh"
@@ -31,13 +37,41 @@ namespace {
 
 constexpr int kTThreads = 256;
 constexpr int kTWarps = kTThreads / 32;
-constexpr int kNodeMax = 255;     // a leaf holds < 2 leaf <= 256 rows; a merge node 2 w <= 128
+constexpr int kNodeMax = kTreeNodeMaxRows;   // CALU: a leaf < 2 leaf <= 256 rows, a merge 2 w
 constexpr int kTTeam = 4;
 
 template <int W>
 constexpr size_t tourn_smem_bytes() {
   return (size_t)kNodeMax * (W + kTTeam) * sizeof(double) + (size_t)W * W * sizeof(double) +
          2 * (size_t)kNodeMax * sizeof(double) + (size_t)W * sizeof(double) + 3 * (size_t)kNodeMax * sizeof(int) + 16;
+}
+
+// Nodes at level h of the tree, and the panel positions of node `node` (0 rows: the node
+// is unpaired and goes up unchanged).  Writes gpos[0..rows) with stride `stride` from
+// `first` (so that a CTA's threads can share the work).
+__host__ __device__ inline int tree_nodes(const TournParams& p, int h) {
+  return p.mode == 2 ? 1 : (p.nleaf + (1 << h) - 1) >> h;
+}
+__device__ inline int tree_node_rows(const TournParams& p, int h, int node, int* gpos, int first, int stride) {
+  const int w = p.w;
+  if (p.mode == 2) {                                  // flat tree: block h after positions 0..w-1
+    const int r0 = h == 0 ? 0 : h * p.leaf;
+    const int r1 = h == p.nleaf - 1 ? p.m : (h + 1) * p.leaf;
+    const int lead = h == 0 ? 0 : w;
+    const int nr = lead + (r1 - r0);
+    for (int k = first; k < nr; k += stride) gpos[k] = k < lead ? k : r0 + (k - lead);
+    return nr;
+  }
+  if (h == 0) {
+    const int r0 = node * p.leaf;
+    const int r1 = node == p.nleaf - 1 ? p.m : r0 + p.leaf;
+    for (int k = first; k < r1 - r0; k += stride) gpos[k] = r0 + k;
+    return r1 - r0;
+  }
+  const int a = node << h, b = a + (1 << (h - 1));
+  if (b >= p.nleaf) return 0;
+  for (int k = first; k < 2 * w; k += stride) gpos[k] = k < w ? a * p.leaf + k : b * p.leaf + (k - w);
+  return 2 * w;
 }
 
 template <int W>
@@ -70,21 +104,12 @@ __global__ void __launch_bounds__(kTThreads, 1) tournament_kernel(TournParams p)
   if (s_abort) return;
   int swaps_total = 0;
 
-  for (int h = 0; h <= p.height; ++h) {
-    const int cnt = (p.nleaf + (1 << h) - 1) >> h;        // nodes at this level
+  unsigned long long dmax = 0ull;
+  for (int h = p.level0; h < p.level1; ++h) {
+    const int cnt = tree_nodes(p, h);
     for (int node = blockIdx.x; node < cnt; node += gridDim.x) {
-      int nr;
-      if (h == 0) {
-        const int r0 = node * p.leaf;
-        const int r1 = node == p.nleaf - 1 ? p.m : r0 + p.leaf;
-        nr = r1 - r0;
-        for (int k = tid; k < nr; k += kTThreads) gpos[k] = r0 + k;
-      } else {
-        const int a = node << h, b = a + (1 << (h - 1));
-        if (b >= p.nleaf) continue;                       // unpaired: goes up unchanged
-        nr = 2 * w;
-        for (int k = tid; k < nr; k += kTThreads) gpos[k] = k < w ? a * p.leaf + k : b * p.leaf + (k - w);
-      }
+      const int nr = tree_node_rows(p, h, node, gpos, tid, kTThreads);
+      if (nr == 0) continue;                              // unpaired: goes up unchanged
       __syncthreads();
       for (int r = tid; r < nr; r += kTThreads) rid[r] = __ldcg(&p.pmap[gpos[r]]);
       __syncthreads();
@@ -257,14 +282,73 @@ __global__ void __launch_bounds__(kTThreads, 1) tournament_kernel(TournParams p)
         swaps_total += swaps;
       }
       __syncthreads();
-      if (good)      // the node's rows in their new order: position pos[r] holds local row r
+      if (good) {    // the node's rows in their new order: position pos[r] holds local row r
         for (int r = tid; r < nr; r += kTThreads) p.pmap[gpos[pos[r]]] = rid[r];
+        if (p.mode != 0)   // block LU_PRRP: D of each eliminated row into its panel columns
+          for (int e = tid; e < nr * w; e += kTThreads) {
+            const int r = e / w, c = e - r * w;
+            if (pos[r] >= w) {
+              const double d = Ps[r * SP + c];
+              p.Pw[(long long)rid[r] * p.ldp + c] = d;
+              dmax = max_bits(dmax, abs_bits(d));
+            }
+          }
+      }
       __syncthreads();
     }
     // the next level reads the positions this one wrote (or learns of an error)
-    if (h < p.height && !grid_barrier(st, (h + 1) * gridDim.x, 21)) return;
+    if (h + 1 < p.level1 && !grid_barrier(st, (h - p.level0 + 1) * gridDim.x, 21)) return;
   }
+  for (int off = 16; off > 0; off >>= 1) dmax = max_bits(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+  if (lane == 0 && dmax) atomicMax(&st->l21_bits, dmax);
   if (tid == 0 && swaps_total) atomicAdd(&st->swaps_total, swaps_total);
+}
+
+// Block LU_PRRP eliminations of one level: blockIdx.y = node, blockIdx.x = a tile of 32
+// trailing columns; the node's w selected rows' tile is staged in shared memory, the D
+// rows of its eliminated rows 32 at a time (33.5 KB of static shared memory at w = 64).
+constexpr int kElimCols = 32;
+constexpr int kElimRows = 32;
+template <int W>
+__global__ void __launch_bounds__(256) tree_eliminate_kernel(TournParams p, double* __restrict__ A, long long lda,
+                                                             int n, int k0) {
+  __shared__ int gpos[kNodeMax];
+  __shared__ double S[W][kElimCols + 1];
+  __shared__ double Dm[kElimRows][W + 1];
+  const DevState* st = p.st;
+  if (dev_status(st) != 0) return;
+  const int h = p.level0, w = p.w, tid = threadIdx.x;
+  const int nr = tree_node_rows(p, h, blockIdx.y, gpos, tid, 256);
+  if (nr <= w) return;
+  __syncthreads();
+  const int c0 = k0 + w + blockIdx.x * kElimCols;
+  const int cw = min(kElimCols, n - c0);
+  if (cw <= 0) return;
+  for (int e = tid; e < w * kElimCols; e += 256) {
+    const int k = e / kElimCols, c = e - k * kElimCols;
+    S[k][c] = c < cw ? A[(long long)(k0 + __ldcg(&p.pmap[gpos[k]])) * lda + c0 + c] : 0.0;
+  }
+  unsigned long long cmax = 0ull;
+  const int col = tid & (kElimCols - 1), rq = tid / kElimCols;       // 8 row phases
+  for (int e0 = w; e0 < nr; e0 += kElimRows) {
+    const int ne = min(kElimRows, nr - e0);
+    __syncthreads();
+    for (int e = tid; e < ne * w; e += 256) {
+      const int r = e / w, k = e - r * w;
+      Dm[r][k] = A[(long long)(k0 + __ldcg(&p.pmap[gpos[e0 + r]])) * lda + k0 + k];
+    }
+    __syncthreads();
+    if (col < cw)
+      for (int r = rq; r < ne; r += 256 / kElimCols) {
+        double* a = A + (long long)(k0 + __ldcg(&p.pmap[gpos[e0 + r]])) * lda + c0 + col;
+        double acc = *a;
+        for (int k = 0; k < w; ++k) acc = fma(-Dm[r][k], S[k][col], acc);
+        *a = acc;
+        cmax = max_bits(cmax, abs_bits(acc));
+      }
+  }
+  for (int off = 16; off > 0; off >>= 1) cmax = max_bits(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
+  if ((tid & 31) == 0 && cmax) atomicMax(&const_cast<DevState*>(st)->gmax_bits, cmax);
 }
 
 template <int W>
@@ -272,7 +356,9 @@ cudaError_t launch_tournament_w(const TournParams& p, int num_sms, cudaStream_t 
   const size_t smem = tourn_smem_bytes<W>();
   cudaError_t e = smem_optin(tournament_kernel<W>);
   if (e != cudaSuccess) return e;
-  const int grid = std::max(1, std::min(p.nleaf, num_sms));
+  int nodes = 0;
+  for (int h = p.level0; h < p.level1; ++h) nodes = std::max(nodes, tree_nodes(p, h));
+  const int grid = std::max(1, std::min(nodes, num_sms));
   TournParams q = p;
   void* args[] = {&q};
   return launch_cooperative_chained((const void*)tournament_kernel<W>, grid, kTThreads, args, smem, s);
@@ -315,10 +401,25 @@ __global__ void __launch_bounds__(256) scatter_rows_kernel(double* __restrict__ 
 }  // namespace
 
 cudaError_t launch_tournament(const TournParams& p, int num_sms, cudaStream_t s) {
-  if (p.w < 1 || p.w > 64 || p.leaf < p.w || p.leaf > 128 || p.m < p.w || p.nleaf < 1) return cudaErrorInvalidValue;
+  if (p.w < 1 || p.w > 64 || p.m < p.w || p.nleaf < 1 || p.level0 < 0 || p.level1 <= p.level0)
+    return cudaErrorInvalidValue;
+  if (p.mode == 0 && (p.leaf < p.w || p.leaf > 128)) return cudaErrorInvalidValue;
+  if (p.mode != 0 && p.level1 != p.level0 + 1) return cudaErrorInvalidValue;
   if (p.w <= 16) return launch_tournament_w<16>(p, num_sms, s);
   if (p.w <= 32) return launch_tournament_w<32>(p, num_sms, s);
   return launch_tournament_w<64>(p, num_sms, s);
+}
+
+cudaError_t launch_tree_eliminate(const TournParams& p, double* A, long long lda, int n, int k0, int num_sms,
+                                  cudaStream_t s) {
+  (void)num_sms;
+  const int nc = n - k0 - p.w;
+  if (nc <= 0) return cudaSuccess;
+  const dim3 grid((nc + kElimCols - 1) / kElimCols, tree_nodes(p, p.level0));
+  if (p.w <= 16) tree_eliminate_kernel<16><<<grid, 256, 0, s>>>(p, A, lda, n, k0);
+  else if (p.w <= 32) tree_eliminate_kernel<32><<<grid, 256, 0, s>>>(p, A, lda, n, k0);
+  else tree_eliminate_kernel<64><<<grid, 256, 0, s>>>(p, A, lda, n, k0);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gather_permute(double* A, long long lda, int n, int k0, int m, const int* pmap, int* perm,

@@ -46,21 +46,37 @@ cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t stream);
 cudaError_t launch_cooperative_chained(const void* func, int grid, int threads, void** args, size_t smem,
                                        cudaStream_t stream);
 
-// CALU_PRRP tournament (Section 3.1) on the m x w panel P (row-major, ldp): leaves of
-// `leaf` rows (the last takes the remainder), a binary tree of strong RRQRs, one CTA per
-// node.  pmap (m ints, identity on entry) receives position -> panel row.  w <= 64,
-// w <= leaf <= 128.  Interchanges are added to st->swaps_total.
+// Trees of strong RRQRs over a panel's rows, one CTA per node (calu.cu), on the m x w
+// panel P (row-major, ldp) whose first row is row k0 of A:
+//   mode 0 (CALU_PRRP, Section 3.1): leaves of `leaf` rows (the last takes the remainder),
+//     a binary tree; levels [level0, level1) in one launch with grid barriers between them;
+//   mode 1 (block parallel LU_PRRP, Section 5): nleaf blocks of `leaf` rows (the last takes
+//     the remainder), the same binary tree; mode 2 (block pairwise): a flat tree, level i
+//     merges positions 0..w-1 with block i.  In modes 1 and 2 one launch runs one level
+//     (level0 + 1 == level1), and each node also writes D = (R11^-1 R12)^T of the rows it
+//     eliminates into their panel columns (Pw) and tracks max |D| in st->l21_bits.
+// pmap (m ints, identity before level 0) maps position -> panel row; a node's selected
+// rows take its first w positions.  w <= 64; every node holds at most 255 rows.
+// Interchanges are added to st->swaps_total.
 struct TournParams {
   const double* P;
+  double* Pw;
   long long ldp;
   int m, w, leaf, nleaf, height;
+  int mode, level0, level1;
   double tau;
   int max_swaps;
   int col_offset;
   int* pmap;
   DevState* st;
 };
+constexpr int kTreeNodeMaxRows = 255;
 cudaError_t launch_tournament(const TournParams& p, int num_sms, cudaStream_t s);
+// Modes 1 and 2, after the level's node launch: every row the level's nodes eliminated
+// gets A_e(k0+w:n) -= D_e A_sel(k0+w:n) (the node's selected rows, not yet updated in this
+// panel); max |A_e| into st->gmax_bits.  A is the whole matrix, row-major.
+cudaError_t launch_tree_eliminate(const TournParams& p, double* A, long long lda, int n, int k0,
+                                  int num_sms, cudaStream_t s);
 // Rows k0 + i (all n columns) and perm[k0 + i] take those at k0 + pmap[i], i < m, through
 // tmp (m x n doubles) and ptmp (m ints); rows with pmap[i] == i are not touched.
 cudaError_t launch_gather_permute(double* A, long long lda, int n, int k0, int m, const int* pmap, int* perm,
