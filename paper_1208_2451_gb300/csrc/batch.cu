@@ -6,12 +6,12 @@
 // stored in T (float, or double for the plain-FP64 batched form); the panel's strong RRQR
 // (QR with column pivoting, the tau test and interchanges, Algorithm 2), the diagonal-block
 // GEPP and the refinement residual r = b - A x are computed in FP64.  The Schur update,
-// U12 and the final multipliers are computed in T.  Substitutions use FP64 arithmetic on
-// the T factors.
+// U12 and the final multipliers are computed in T.  Substitutions use T's arithmetic on
+// the T factors (the refinement residual and solution stay FP64).
 //
-// Inside a CTA: the panel (m x w, w <= 32) lives in shared memory in FP64; a team of 4
-// threads works on one panel row; argmax keys compare non-negative doubles by their IEEE
-// bit patterns.  The trailing matrix stays in the CTA's global scratch (L2-resident for
+// Inside a CTA: the panel (m x w, w <= 32) lives in shared memory in FP64; one thread
+// works on one panel row; argmax keys compare non-negative doubles by their IEEE bit
+// patterns.  The trailing matrix stays in the CTA's global scratch (L2-resident for
 // these sizes).  No grid-wide synchronization is used: CTAs never wait on one another.
 #include <cuda_runtime.h>
 
@@ -26,7 +26,6 @@ namespace {
 
 constexpr int kBT = 256;          // threads per batch CTA
 constexpr int kBW = 32;           // largest panel width in the batched kernel
-constexpr int kBTeams = kBT / kTeam;
 constexpr int kUnroll = 4;        // global loads a thread keeps in flight in the copy and update loops
 
 struct BKey {
@@ -69,13 +68,6 @@ __device__ BKey block_best_key(BKey c, BKey* s_w) {
   return r;
 }
 
-__device__ __forceinline__ double bteam_sum(double s) {
-  const unsigned mask = 0xfu << ((threadIdx.x & 31) & ~3);
-  s += __shfl_xor_sync(mask, s, 1);
-  s += __shfl_xor_sync(mask, s, 2);
-  return s;
-}
-
 __device__ __forceinline__ double block_sum(double v, double* s_red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -101,18 +93,22 @@ __device__ __forceinline__ double block_max(double v, double* s_red) {
 // Strong RRQR of the transposed m x w panel held in Ps (FP64, stride sp), Algorithm 2.
 // On return pos[r] is the final position of panel row r and rows with pos >= w hold their
 // multipliers M(:, pos - w) = (R11^-1 R12)(:, .).  Returns 0, or a prrp_status.
+// One thread per panel row: an FP64 instruction holds its sub-partition's FP64 unit for
+// 64 cycles whatever its active lanes, so whole rows per lane (no team reductions, no
+// per-row fixed cost spread over several lanes) issue the fewest FP64 instructions.
 __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, int max_swaps,
                                   double* nrm, double* nref, int* pos, double* Rs, double* rdiag,
                                   BKey* s_w, int* swaps_out) {
   __shared__ double s_refl[3];                   // alpha, beta, v0 of the current reflector
   const int tid = threadIdx.x, lane = tid & 31;
-  const int tl = tid & (kTeam - 1), team = tid / kTeam;
-  const unsigned tmask = 0xfu << (lane & ~3);
-  for (int r = team; r < m; r += kBTeams) {
-    double s = 0.0;
-    for (int i = tl; i < w; i += kTeam) { const double x = Ps[r * sp + i]; s = fma(x, x, s); }
-    s = bteam_sum(s);
-    if (tl == 0) { nrm[r] = s; nref[r] = s; pos[r] = r; }
+  for (int r = tid; r < m; r += kBT) {
+    const double* x = Ps + r * sp;
+    double s0 = 0.0, s1 = 0.0;
+    int i = 0;
+    for (; i + 1 < w; i += 2) { s0 = fma(x[i], x[i], s0); s1 = fma(x[i + 1], x[i + 1], s1); }
+    if (i < w) s0 = fma(x[i], x[i], s0);
+    const double s = s0 + s1;
+    nrm[r] = s; nref[r] = s; pos[r] = r;
   }
   __syncthreads();
   for (int t = 0; t < w; ++t) {
@@ -138,82 +134,72 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
     if (g.v == 0ull) return PRRP_ERR_SINGULAR;
     const int rw = g.k2, pw = g.k1;
     const double* xw = Ps + rw * sp;
-    if (tid < 32) {
+    if (tid == 0) {
       const double x0 = xw[t];
       const double normx = sqrt(__longlong_as_double(static_cast<long long>(g.v)));
       const double alpha = (x0 >= 0.0) ? -normx : normx;
-      if (tid == 0) {
-        s_refl[0] = alpha;
-        s_refl[1] = 1.0 / (normx * (normx + abs_int(x0)));
-        s_refl[2] = x0 - alpha;
-        Rs[t * kBW + t] = alpha;
-      }
+      s_refl[0] = alpha;
+      s_refl[1] = 1.0 / (normx * (normx + abs_int(x0)));
+      s_refl[2] = x0 - alpha;
+      Rs[t * kBW + t] = alpha;
     }
     for (int i = tid; i < t; i += kBT) Rs[i * kBW + t] = xw[i];
     __syncthreads();
     const double beta = s_refl[1], v0 = s_refl[2];
-    // the winner row's values are read by every team below; it is itself not updated
-    for (int r = team; r < m; r += kBTeams) {
+    // the winner row's values are read by every thread below; it is itself not updated
+    for (int r = tid; r < m; r += kBT) {
       const int pr = pos[r];
       if (r == rw) {                                 // the winner takes position t
-        if (tl == 0) pos[r] = t;
+        pos[r] = t;
         continue;
       }
       if (pr < t) continue;
       double* x = Ps + r * sp;
-      double sd = 0.0;
-      for (int i = t + tl; i < w; i += kTeam) sd = fma(i == t ? v0 : xw[i], x[i], sd);
-      sd = bteam_sum(sd);
-      const double f = beta * sd;
-      double xt = 0.0;
-      for (int i = t + tl; i < w; i += kTeam) {
-        const double y = fma(-f, i == t ? v0 : xw[i], x[i]);
-        x[i] = y;
-        if (i == t) xt = y;
-      }
-      xt = __shfl_sync(tmask, xt, lane & ~3);
+      double s0 = v0 * x[t], s1 = 0.0, s2 = 0.0;     // three chains over the row
+      int i = t + 1;
+      for (; i + 1 < w; i += 2) { s1 = fma(xw[i], x[i], s1); s2 = fma(xw[i + 1], x[i + 1], s2); }
+      if (i < w) s1 = fma(xw[i], x[i], s1);
+      const double f = beta * (s0 + (s1 + s2));
+      const double xt = fma(-f, v0, x[t]);
+      x[t] = xt;
+      for (int k = t + 1; k < w; ++k) x[k] = fma(-f, xw[k], x[k]);
       double n2 = fma(-xt, xt, nrm[r]);
       if (!(n2 > 1e-4 * nref[r])) {
-        double e2 = 0.0;
-        for (int i = t + 1 + tl; i < w; i += kTeam) e2 = fma(x[i], x[i], e2);
-        n2 = bteam_sum(e2);
-        if (tl == 0) nref[r] = n2;
+        double e0 = 0.0, e1 = 0.0;
+        int k = t + 1;
+        for (; k + 1 < w; k += 2) { e0 = fma(x[k], x[k], e0); e1 = fma(x[k + 1], x[k + 1], e1); }
+        if (k < w) e0 = fma(x[k], x[k], e0);
+        n2 = e0 + e1;
+        nref[r] = n2;
       }
-      __syncwarp(tmask);
-      if (tl == 0) { nrm[r] = n2; pos[r] = (pr == t) ? pw : pr; }
+      nrm[r] = n2;
+      pos[r] = (pr == t) ? pw : pr;
     }
     __syncthreads();
   }
   for (int i = tid; i < w; i += kBT) rdiag[i] = 1.0 / Rs[i * kBW + i];
   __syncthreads();
-  for (int r = team; r < m; r += kBTeams) {
+  for (int r = tid; r < m; r += kBT) {
     if (pos[r] < w) continue;
     double* b = Ps + r * sp;
     for (int i = w - 1; i >= 0; --i) {
-      const int owner = i & (kTeam - 1);
-      double mi = 0.0;
-      if (tl == owner) mi = b[i] * rdiag[i];
-      mi = __shfl_sync(tmask, mi, (lane & ~3) | owner);
-      if (tl == owner) b[i] = mi;
-      for (int k = tl; k < i; k += kTeam) b[k] = fma(-Rs[k * kBW + i], mi, b[k]);
+      const double mi = b[i] * rdiag[i];
+      b[i] = mi;
+      for (int k = 0; k < i; ++k) b[k] = fma(-Rs[k * kBW + i], mi, b[k]);
     }
   }
   __syncthreads();
   int swaps = 0;
   for (;;) {
     BKey c{0ull, 0x7fffffff, 0x7fffffff};
-    for (int r = team; r < m; r += kBTeams) {
+    for (int r = tid; r < m; r += kBT) {
       const int pr = pos[r];
       if (pr < w) continue;
       BKey d{0ull, pr - w, 0x7fffffff};
-      for (int i = tl; i < w; i += kTeam) {
+      for (int i = 0; i < w; ++i) {
         const unsigned long long a = abs_bits(Ps[r * sp + i]);
         if (a > d.v || d.k2 == 0x7fffffff) { d.v = a; d.k2 = i; }
       }
-      BKey o = bshfl(d, 1, tmask);
-      if (bbetter(o, d)) d = o;
-      o = bshfl(d, 2, tmask);
-      if (bbetter(o, d)) d = o;
       if (bbetter(d, c)) c = d;
     }
     const BKey g = block_best_key(c, s_w);
@@ -230,21 +216,17 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
       for (int i = 0; i < w; ++i) colv[i] = Ps[rin * sp + i];
     __syncthreads();
     const double mu = colv[is];
-    for (int r = team; r < m; r += kBTeams) {
+    for (int r = tid; r < m; r += kBT) {
       const int pr = pos[r];
       double* x = Ps + r * sp;
       if (pr == w + js) {
-        if (tl == 0) pos[r] = is;
+        pos[r] = is;
       } else if (pr == is) {
-        for (int k = tl; k < w; k += kTeam) x[k] = (k == is) ? 1.0 / mu : -colv[k] / mu;
-        __syncwarp(tmask);
-        if (tl == 0) pos[r] = w + js;
+        for (int k = 0; k < w; ++k) x[k] = (k == is) ? 1.0 / mu : -colv[k] / mu;
+        pos[r] = w + js;
       } else if (pr >= w) {
-        const int owner = is & (kTeam - 1);
-        double f = 0.0;
-        if (tl == owner) f = x[is] / mu;
-        f = __shfl_sync(tmask, f, (lane & ~3) | owner);
-        for (int k = tl; k < w; k += kTeam) x[k] = (k == is) ? f : fma(-f, colv[k], x[k]);
+        const double f = x[is] / mu;
+        for (int k = 0; k < w; ++k) x[k] = (k == is) ? f : fma(-f, colv[k], x[k]);
       }
     }
     ++swaps;
@@ -304,8 +286,11 @@ __device__ __forceinline__ void stage_block(const T* W, int n, int k0, int kb, d
   __syncthreads();
 }
 
-// x (FP64, length n) <- U^-1 L^-1 P y for the T factors in W (ld n); y = b or r in v, x out.
-// Db: kBW x (kBW + 1) doubles of shared scratch.
+// x (length n, stored in FP64) <- U^-1 L^-1 P y for the T factors in W (ld n); y = b or r
+// in v, x out.  The arithmetic is T's: FP32 factors give FP32-accurate solutions whatever
+// the arithmetic, so the FP32-factor form solves in FP32 (its refinement keeps the
+// residual and the accumulated solution in FP64, Section 3.3); dependent FP64 chains would
+// cost 64 cycles per step on this GPU.  Db: kBW x (kBW + 1) doubles of shared scratch.
 template <typename T>
 __device__ void batch_lu_solve(const T* W, int n, const int* perm, const double* rhs, double* x,
                                double* s_red, double* Db) {
@@ -317,19 +302,19 @@ __device__ void batch_lu_solve(const T* W, int n, const int* perm, const double*
     const int kb = min(32, n - k0);
     stage_block(W, n, k0, kb, Db);
     if (warp == 0) {
-      double y = lane < kb ? x[k0 + lane] : 0.0;
+      T y = lane < kb ? static_cast<T>(x[k0 + lane]) : T(0);
       for (int k = 0; k < kb; ++k) {
-        const double xk = __shfl_sync(0xffffffffu, y, k);
-        if (lane > k && lane < kb) y = fma(-Db[lane * (kBW + 1) + k], xk, y);
+        const T xk = __shfl_sync(0xffffffffu, y, k);
+        if (lane > k && lane < kb) y = fma(-static_cast<T>(Db[lane * (kBW + 1) + k]), xk, y);
       }
-      if (lane < kb) x[k0 + lane] = y;
+      if (lane < kb) x[k0 + lane] = static_cast<double>(y);
     }
     __syncthreads();
     for (int i = k0 + kb + tid; i < n; i += kBT) {
       const T* row = W + (long long)i * n + k0;
-      double acc = 0.0;
-      for (int k = 0; k < kb; ++k) acc = fma(static_cast<double>(row[k]), x[k0 + k], acc);
-      x[i] -= acc;
+      T acc = 0;
+      for (int k = 0; k < kb; ++k) acc = fma(row[k], static_cast<T>(x[k0 + k]), acc);
+      x[i] = static_cast<double>(static_cast<T>(x[i]) - acc);
     }
     __syncthreads();
   }
@@ -337,20 +322,20 @@ __device__ void batch_lu_solve(const T* W, int n, const int* perm, const double*
     const int k0 = max(0, kend - 32), kb = kend - k0;
     stage_block(W, n, k0, kb, Db);
     if (warp == 0) {
-      double y = lane < kb ? x[k0 + lane] : 0.0;
+      T y = lane < kb ? static_cast<T>(x[k0 + lane]) : T(0);
       for (int k = kb - 1; k >= 0; --k) {
-        if (lane == k) y = y / Db[k * (kBW + 1) + k];
-        const double xk = __shfl_sync(0xffffffffu, y, k);
-        if (lane < k) y = fma(-Db[lane * (kBW + 1) + k], xk, y);
+        if (lane == k) y = y / static_cast<T>(Db[k * (kBW + 1) + k]);
+        const T xk = __shfl_sync(0xffffffffu, y, k);
+        if (lane < k) y = fma(-static_cast<T>(Db[lane * (kBW + 1) + k]), xk, y);
       }
-      if (lane < kb) x[k0 + lane] = y;
+      if (lane < kb) x[k0 + lane] = static_cast<double>(y);
     }
     __syncthreads();
     for (int i = tid; i < k0; i += kBT) {
       const T* row = W + (long long)i * n + k0;
-      double acc = 0.0;
-      for (int k = 0; k < kb; ++k) acc = fma(static_cast<double>(row[k]), x[k0 + k], acc);
-      x[i] -= acc;
+      T acc = 0;
+      for (int k = 0; k < kb; ++k) acc = fma(row[k], static_cast<T>(x[k0 + k]), acc);
+      x[i] = static_cast<double>(static_cast<T>(x[i]) - acc);
     }
     __syncthreads();
   }
@@ -682,13 +667,20 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
     int itmax = 0;
     double anorm = 0.0;
     if (fstat == 0) {
-      double cm = 0.0;
+      // ||A||_1 only scales eta: FP32 sums (relative error ~n 2^-24) on the FP32 pipe
+      // instead of n^2 FP64 additions
+      float cm = 0.0f;
       for (int j = tid; j < n; j += kBT) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += abs_int(A[(long long)i * lda + j]);
-        cm = fmax(cm, s);
+        float s0 = 0.0f, s1 = 0.0f;
+        int i = 0;
+        for (; i + 1 < n; i += 2) {
+          s0 += fabsf(static_cast<float>(A[(long long)i * lda + j]));
+          s1 += fabsf(static_cast<float>(A[(long long)(i + 1) * lda + j]));
+        }
+        if (i < n) s0 += fabsf(static_cast<float>(A[(long long)i * lda + j]));
+        cm = fmaxf(cm, s0 + s1);
       }
-      anorm = block_max(cm, s_red);
+      anorm = block_max(static_cast<double>(cm), s_red);
     }
     for (int c = 0; c < nr && fstat == 0; ++c) {
       double* bcol = dv;                                   // the right-hand side, packed

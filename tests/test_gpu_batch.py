@@ -49,9 +49,12 @@ def _run(prrp, ctx, As, Bs, prec, b=16, tau=2.0, refine=10):
     return st, info, [x.cpu().numpy() for x in dB], [p.cpu().numpy().astype(np.int64) for p in dP]
 
 
-def test_fp64_batch_pivots_match_oracle(prrp, ctx):
-    sizes = [32, 47, 64, 100, 129, 200, 256, 300]
-    As, Bs = _systems(sizes, 500)
+@pytest.mark.parametrize("sizes,seed", [([32, 47, 64, 100, 129, 200, 256, 300], 500),
+                                        ([512, 1024, 511, 777], 510)])
+def test_fp64_batch_pivots_match_oracle(prrp, ctx, sizes, seed):
+    """FP64 batched factors: the oracle's pivots where its decisions are untied (sizes up to
+    the kernel's limit, n = 1024), else a valid selection; refined to eta <= 1e-15."""
+    As, Bs = _systems(sizes, seed)
     st, info, X, P = _run(prrp, ctx, As, Bs, prec=0)
     assert all(s == 0 for s in st)
     for A, B, x, p in zip(As, Bs, X, P):
