@@ -383,6 +383,21 @@ prrp_status prrp_ctx_set_panel_mode(prrp_ctx* ctx, int cluster_max_rows);
  * rest update.  The plain FP64 mode is not affected. */
 prrp_status prrp_ctx_set_sm_split(prrp_ctx* ctx, int panel_ctas, int block_ctas);
 
+/* Aggregated trailing update of prrp_factor in the modes PRRP_TF32 and PRRP_BF16X3
+ * (Algorithm 1, line 7; a tuning knob, off by default).  The panels are grouped in blocks
+ * of q = floor(nb / b) panels.  Inside a block, each panel's row interchanges, Schur update
+ * and U12 reach only the block's own columns and the multipliers on its left; the columns
+ * right of the block are brought up to date once at the block's end: the block's composed
+ * row interchanges, U = L_blk^-1 X for the block's rows (L_blk the block's unit lower
+ * triangle of final multipliers; solved panel by panel with the 3 x BF16 product) and one
+ * rank-(q b) update A22 -= L2 U.  This equals the per-panel order up to rounding, since
+ * each panel's update L21 A12 is its final multipliers times its U12 rows.  The pivots are
+ * those of the updated matrix as before; the growth factor is then taken over the block's
+ * own columns at every panel and over the rest at block ends.  nb in [0, 256]; 0 (the
+ * default) and nb < 2 b keep the per-panel update.  INVALID_ARG otherwise.  Other modes
+ * are not affected. */
+prrp_status prrp_ctx_set_update_block(prrp_ctx* ctx, int nb);
+
 /* Substitution form of prrp_solve for this context (a tuning knob).  mode 0 (the default):
  * a triangle with at most 16 right-hand sides is solved by one launch whose CTAs wait for
  * one another's row blocks, the lowest latency for one solve on an otherwise idle GPU;

@@ -74,6 +74,7 @@ _SIGS = {
     "prrp_ctx_timeline": (_I, [_P, _I, _P, _P, _P, C.POINTER(_I)]),
     "prrp_ctx_set_panel_mode": (_I, [_P, _I]),
     "prrp_ctx_set_sm_split": (_I, [_P, _I, _I]),
+    "prrp_ctx_set_update_block": (_I, [_P, _I]),
     "prrp_server_create": (_I, [_P, C.c_size_t, C.POINTER(prrp_opts), _I, C.POINTER(_P)]),
     "prrp_server_submit": (_I, [_P, _P, C.POINTER(C.c_uint64)]),
     "prrp_server_wait": (_I, [_P, C.c_uint64, C.c_int64, _P]),
@@ -369,6 +370,12 @@ def prrp_ctx_set_panel_mode(ctx: Context, cluster_max_rows: int = 0) -> None:
 def prrp_ctx_set_sm_split(ctx: Context, panel_ctas: int = 0, block_ctas: int = 0) -> None:
     """SMs for the panels and the diagonal-block work in the tensor-core modes (0: default)."""
     _check(_lib.prrp_ctx_set_sm_split(ctx.handle, int(panel_ctas), int(block_ctas)), "prrp_ctx_set_sm_split")
+
+
+def prrp_ctx_set_update_block(ctx: Context, nb: int = 0) -> None:
+    """Aggregated trailing update in the TF32 / BF16X3 modes: blocks of floor(nb / b)
+    panels, nb <= 256 (0, the default, or nb < 2 b: the per-panel update)."""
+    _check(_lib.prrp_ctx_set_update_block(ctx.handle, int(nb)), "prrp_ctx_set_update_block")
 
 
 def prrp_ctx_set_solve_mode(ctx: Context, mode: int) -> None:

@@ -110,6 +110,18 @@ struct prrp_ctx {
   int split_panel = 0;              // prrp_ctx_set_sm_split (0: the library defaults)
   int split_blk = 0;
   int solve_mode = 0;               // prrp_ctx_set_solve_mode
+  int agg_nb = 0;                   // prrp_ctx_set_update_block (0: per-panel update)
+  // aggregated update of the mixed-precision forms: row order at the block's start, where
+  // each row sat then, the moved rows and their count, the moves' buffers for the next
+  // block's columns and for the rest
+  int* agg_perm0 = nullptr;
+  int* agg_pos0 = nullptr;
+  int* agg_pairs = nullptr;
+  size_t agg_perm0_cap = 0, agg_pos0_cap = 0, agg_pairs_cap = 0;
+  double* agg_tmp1 = nullptr;
+  double* agg_tmp2 = nullptr;
+  size_t agg_tmp1_cap = 0, agg_tmp2_cap = 0;
+  cudaEvent_t agg_ev[3] = {};       // the block's end on s; the far update's splits; its end
   double* krylov = nullptr;         // GMRES-based refinement: Krylov basis, coefficients
   size_t krylov_cap = 0;
   double* gm_coef = nullptr;
@@ -409,8 +421,11 @@ prrp_status prrp_destroy(prrp_ctx* ctx) {
                   ctx->l21, ctx->solve_ws, ctx->norms, ctx->hA, ctx->hA0, ctx->hB, ctx->tcws,
                   ctx->l21b, ctx->a12, ctx->tcws2, ctx->dinv64, ctx->dinv32, ctx->lu32, ctx->y32,
                   ctx->tcount, ctx->zbuf, ctx->gemm_ctr, ctx->krylov, ctx->gm_coef, ctx->tcws3, ctx->tri,
-                  ctx->calu_pmap, ctx->calu_ptmp, ctx->calu_tmp};
+                  ctx->calu_pmap, ctx->calu_ptmp, ctx->calu_tmp, ctx->agg_perm0, ctx->agg_pos0,
+                  ctx->agg_pairs, ctx->agg_tmp1, ctx->agg_tmp2};
   for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->agg_ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->s_rest) cudaStreamDestroy(ctx->s_rest);
   if (ctx->s_blk) cudaStreamDestroy(ctx->s_blk);
   for (void* p : ptrs)
@@ -507,6 +522,33 @@ prrp_status factor_impl(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
     if ((ps = grow(ctx, &ctx->tcws3, &ctx->tcws3_cap, ws3)) != PRRP_OK) return fail(ps);
     if ((ps = grow(ctx, &ctx->tri, &ctx->tri_cap, 2 * (size_t)b * b)) != PRRP_OK) return fail(ps);
   }
+  // Aggregated update (mixed-precision LU_PRRP, opt-in): blocks of q_agg panels whose row
+  // moves, updates and U12 stay inside the block's columns; the columns right of a block
+  // are moved, solved and updated once at its end, by one rank-NB product.
+  int q_agg = 1;
+  if (tc_a7 && leaf_rows == 0) q_agg = std::max(1, std::min(ctx->agg_nb, kAggMaxNB) / b);
+  const int NB = q_agg * b;
+  const bool agg = q_agg > 1 && n > NB;
+  int agg_cap = 0;            // rows a block can move: its permutes' pairs and GEPP's rows
+  if (agg) {
+    agg_cap = (int)std::min<long long>(n, (long long)q_agg * (max_pairs + b));
+    if ((ps = grow(ctx, &ctx->agg_perm0, &ctx->agg_perm0_cap, (size_t)n)) != PRRP_OK ||
+        (ps = grow(ctx, &ctx->agg_pos0, &ctx->agg_pos0_cap, (size_t)n)) != PRRP_OK ||
+        (ps = grow(ctx, &ctx->agg_pairs, &ctx->agg_pairs_cap, 2 * (size_t)agg_cap + 1)) != PRRP_OK ||
+        (ps = grow(ctx, &ctx->agg_tmp1, &ctx->agg_tmp1_cap, (size_t)agg_cap * NB)) != PRRP_OK ||
+        (ps = grow(ctx, &ctx->agg_tmp2, &ctx->agg_tmp2_cap, (size_t)agg_cap * n)) != PRRP_OK ||
+        (ps = grow(ctx, &ctx->tri, &ctx->tri_cap, 2 * (size_t)q_agg * 2 * b * b)) != PRRP_OK)
+      return fail(ps);
+    const size_t w2s = std::max({tc_workspace_bytes(o.prec, n, NB, b), tc_workspace_bytes(PRRP_BF16X3, b, NB, NB),
+                                 tc_workspace_bytes(o.prec, n, NB, NB)});
+    const size_t wrs = std::max(tc_workspace_bytes(PRRP_BF16X3, b, n, NB), tc_workspace_bytes(o.prec, n, n, NB));
+    if ((ps = grow(ctx, &ctx->tcws2, &ctx->tcws2_cap, w2s)) != PRRP_OK ||
+        (ps = grow(ctx, &ctx->tcws, &ctx->tcws_cap, wrs)) != PRRP_OK)
+      return fail(ps);
+    for (cudaEvent_t& ev : ctx->agg_ev)
+      if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(cuda_fail(ctx, e, "event create"));
+  }
   cudaStream_t sr = ctx->s_rest, sb = ctx->s_blk;
   cudaEvent_t ev_start = next_event(ctx);
   CK(cudaEventRecord(ev_start, s));
@@ -539,12 +581,26 @@ prrp_status factor_impl(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
     return launch_tc_update(o.prec, mm, nn, kk, L, kk, U, ldu, C, lda, ctx->st, 1, ws, st,
                             st == sr ? cap_rest : cap_panel);
   };
+  int K0 = 0, KB = n;                                      // the current block's columns
+  cudaEvent_t ev_split = nullptr, ev_far = nullptr;        // far update of the previous block
   for (int jp = 0, k0 = 0; k0 < n; k0 += b, ++jp) {
     const int w = std::min(b, n - k0), m = n - k0;
     const int w2 = std::min(b, n - k0 - w);                 // next panel's width (0: last)
     double* Akk = dA + (long long)k0 * lda + k0;
     double* L21 = (jp & 1) ? ctx->l21b : ctx->l21;
     double* A12 = ctx->a12 + (size_t)(jp & 1) * n * b;     // snapshot: w x nc, ld nc
+    const bool blk_first = agg && jp % q_agg == 0;
+    if (blk_first) {
+      K0 = k0;
+      KB = std::min(n, k0 + NB);
+      // the row order at the block's start (rows above K0 are no longer moved)
+      CK(cudaMemcpyAsync(ctx->agg_perm0, f->perm + k0, sizeof(int) * (n - k0), cudaMemcpyDeviceToDevice, s));
+    }
+    const bool blk_last = agg && k0 + w >= KB;
+    const int ncol = agg ? KB : n;                         // columns the panel's moves and U12 reach
+    // I - L11^-1 and I - L11 of this panel: kept for the block's end in the aggregated form
+    // (two sets of q_agg panels, alternating by block)
+    double* tri = agg ? ctx->tri + ((size_t)((jp / q_agg) & 1) * q_agg + jp % q_agg) * 2 * b * b : ctx->tri;
     if (leaf_rows == 0) {
       {
         Timed t(ctx, s, PRRP_KIND_PANEL, 3LL * m * w * w);
@@ -553,6 +609,8 @@ prrp_status factor_impl(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
       if (ps != PRRP_OK) return fail(ps);
       if (ev_rest) CK(cudaStreamWaitEvent(s, ev_rest, 0));
       if (ev_blk) CK(cudaStreamWaitEvent(s, ev_blk, 0));
+      // the previous block's far update has taken its multipliers (rows this block moves)
+      if (blk_first && ev_split) CK(cudaStreamWaitEvent(s, ev_split, 0));
     } else {
       // CALU_PRRP: the tournament reads only the panel's columns; its row moves (whole
       // rows) wait for the rest update and the block work of the previous panel; then
@@ -589,7 +647,7 @@ prrp_status factor_impl(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
     }
     {
       Timed t(ctx, s, PRRP_KIND_PERMUTE);
-      e = launch_permute(dA, lda, n, k0, ctx->pairs, max_pairs, f->perm, ctx->st, s);
+      e = launch_permute(dA, lda, ncol, k0, ctx->pairs, max_pairs, f->perm, ctx->st, s);
     }
     if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "permute"));
     cudaEvent_t ev_perm = next_event(ctx);
@@ -601,8 +659,21 @@ prrp_status factor_impl(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
       e = launch_diag_gepp(dA, lda, k0, w, ctx->ipiv, f->perm, ctx->st, sb);
     }
     if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "diag gepp"));
-    const int nc = n - k0 - w;                              // columns right of the panel
-    if (m > w) {
+    const int nc = ncol - k0 - w;                           // columns right of the panel updated now
+    if (m > w && agg) {
+      // every update of the block's own columns at once, on the critical stream
+      if (nc > 0)
+        CK(cudaMemcpy2DAsync(A12, sizeof(double) * nc, Akk + w, sizeof(double) * lda, sizeof(double) * nc, w,
+                             cudaMemcpyDeviceToDevice, s));
+      cudaEvent_t ev_snap = next_event(ctx);
+      CK(cudaEventRecord(ev_snap, s));
+      if (nc > 0) {
+        Timed t(ctx, s, PRRP_KIND_UPDATE, 2LL * (m - w) * nc * w);
+        e = update(m - w, nc, w, L21, A12, nc, Akk + (long long)w * lda + w, ctx->tcws2, s);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "schur update (block columns)"));
+      CK(cudaStreamWaitEvent(sb, ev_snap, 0));
+    } else if (m > w) {
       CK(cudaMemcpy2DAsync(A12, sizeof(double) * nc, Akk + w, sizeof(double) * lda, sizeof(double) * nc, w,
                            cudaMemcpyDeviceToDevice, s));
       cudaEvent_t ev_snap = next_event(ctx);
@@ -629,10 +700,10 @@ prrp_status factor_impl(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
       {
         Timed t(ctx, sb, PRRP_KIND_U12, 1LL * nc * w * w);
         ctx->kind_launches[PRRP_KIND_U12] += nc > 0 ? 4 : 1;   // swaps, E, 2 splits, MMA
-        e = launch_u12(dA, lda, n, k0, w, ctx->ipiv, ctx->st, sb, 0);
-        if (e == cudaSuccess) e = launch_tri_blocks(dA, lda, k0, w, ctx->tri, ctx->st, sb);
+        e = launch_u12(dA, lda, ncol, k0, w, ctx->ipiv, ctx->st, sb, 0);
+        if (e == cudaSuccess) e = launch_tri_blocks(dA, lda, k0, w, tri, ctx->st, sb);
         if (e == cudaSuccess && nc > 0)
-          e = launch_tc_update(o.prec, w, nc, w, ctx->tri, w, Akk + w, lda, Akk + w, lda, ctx->st, 2,
+          e = launch_tc_update(o.prec, w, nc, w, tri, w, Akk + w, lda, Akk + w, lda, ctx->st, 2,
                                ctx->tcws3, sb, cap_blk);
       }
       if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "u12"));
@@ -642,7 +713,7 @@ prrp_status factor_impl(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
         ctx->kind_launches[PRRP_KIND_LFIX] += 3;               // copy, 2 splits, MMA
         e = launch_lfix_copy(dA, lda, n, k0, w, L21, w, ctx->ipiv, ctx->st, sb);
         if (e == cudaSuccess)
-          e = launch_tc_update(o.prec, m - w, w, w, Y, lda, ctx->tri + (size_t)w * w, w, Y, lda, ctx->st, 0,
+          e = launch_tc_update(o.prec, m - w, w, w, Y, lda, tri + (size_t)w * w, w, Y, lda, ctx->st, 0,
                                ctx->tcws3, sb, cap_blk);
       }
       if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "lfix"));
@@ -660,9 +731,94 @@ prrp_status factor_impl(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
     }
     ev_blk = next_event(ctx);
     CK(cudaEventRecord(ev_blk, sb));
+    if (blk_last && KB < n) {
+      // the block's end: the columns right of it (next block's first, on the critical
+      // stream; the rest on s_rest, beside the next block's panels)
+      const int nF = n - KB, nF1 = std::min(NB, nF), nF2 = nF - nF1;
+      double* L2 = dA + (long long)KB * lda + K0;           // final multipliers below the block
+      int* cnt = ctx->agg_pairs + 2 * (size_t)agg_cap;
+      const double* tri_set = ctx->tri + (size_t)((jp / q_agg) & 1) * q_agg * 2 * b * b;
+      // U(K0:KB, c0:c0+nc) = L_blk^-1 A(K0:KB, c0:c0+nc), panel by panel: the rows of panel t
+      // lose the earlier panels' part (final multipliers times their U rows), then take
+      // L11^-1 as X - (I - L11^-1) X, as the per-panel U12 does.  These U rows are operands
+      // of the rank-NB update (the per-panel form updates with the unreduced A12 instead),
+      // so they are formed with the FP32-accurate 3 x BF16 product in both modes.
+      const int uprec = PRRP_BF16X3;
+      auto block_u = [&](int c0, int nc, unsigned char* ws, cudaStream_t st, int cap) -> cudaError_t {
+        cudaError_t r = cudaSuccess;
+        for (int t = 0; t < q_agg && r == cudaSuccess; ++t) {
+          double* Xt = dA + (long long)(K0 + t * b) * lda + c0;
+          if (t > 0) {
+            ctx->kind_launches[PRRP_KIND_U12] += 3;
+            r = launch_tc_update(uprec, b, nc, t * b, dA + (long long)(K0 + t * b) * lda + K0, lda,
+                                 dA + (long long)K0 * lda + c0, lda, Xt, lda, ctx->st, 1, ws, st, cap);
+          }
+          if (r == cudaSuccess) {
+            ctx->kind_launches[PRRP_KIND_U12] += 3;
+            r = launch_tc_update(uprec, b, nc, b, tri_set + (size_t)t * 2 * b * b, b, Xt, lda, Xt, lda, ctx->st, 2,
+                                 ws, st, cap);
+          }
+        }
+        return r;
+      };
+      CK(cudaStreamWaitEvent(s, ev_blk, 0));
+      if (ev_far) CK(cudaStreamWaitEvent(s, ev_far, 0));    // the previous far update wrote these
+      {
+        Timed t(ctx, s, PRRP_KIND_PERMUTE);
+        ctx->kind_launches[PRRP_KIND_PERMUTE] += 3;          // positions, pairs, gather, scatter
+        e = launch_block_pairs(ctx->agg_perm0, f->perm, K0, n - K0, ctx->agg_pos0, ctx->agg_pairs, cnt, agg_cap,
+                               ctx->st, s);
+        if (e == cudaSuccess)
+          e = launch_block_moves(dA, lda, K0, KB, nF1, ctx->agg_pairs, cnt, agg_cap, ctx->agg_tmp1, ctx->st, s);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "block row moves"));
+      {
+        Timed t(ctx, s, PRRP_KIND_U12, 1LL * NB * nF1 * NB);
+        ctx->kind_launches[PRRP_KIND_U12] -= 1;
+        e = block_u(KB, nF1, ctx->tcws2, s, cap_panel);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "block U12"));
+      {
+        Timed t(ctx, s, PRRP_KIND_UPDATE, 2LL * (n - KB) * nF1 * NB);
+        ctx->kind_launches[PRRP_KIND_UPDATE] += 2;
+        e = launch_tc_update(o.prec, n - KB, nF1, NB, L2, lda, dA + (long long)K0 * lda + KB, lda,
+                             dA + (long long)KB * lda + KB, lda, ctx->st, 1, ctx->tcws2, s, cap_panel);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "block update"));
+      ev_split = ev_far = nullptr;
+      if (nF2 > 0) {
+        const int c2 = KB + nF1;
+        CK(cudaEventRecord(ctx->agg_ev[0], s));
+        CK(cudaStreamWaitEvent(sr, ctx->agg_ev[0], 0));
+        {
+          Timed t(ctx, sr, PRRP_KIND_PERMUTE);
+          ctx->kind_launches[PRRP_KIND_PERMUTE] += 1;
+          e = launch_block_moves(dA, lda, K0, c2, nF2, ctx->agg_pairs, cnt, agg_cap, ctx->agg_tmp2, ctx->st, sr);
+        }
+        if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "block row moves (rest)"));
+        {
+          Timed t(ctx, sr, PRRP_KIND_U12, 1LL * NB * nF2 * NB);
+          ctx->kind_launches[PRRP_KIND_U12] -= 1;
+          e = block_u(c2, nF2, ctx->tcws, sr, cap_rest);
+        }
+        if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "block U12 (rest)"));
+        {
+          Timed t(ctx, sr, PRRP_KIND_UPDATE, 2LL * (n - KB) * nF2 * NB);
+          ctx->kind_launches[PRRP_KIND_UPDATE] += 2;
+          e = launch_tc_update(o.prec, n - KB, nF2, NB, L2, lda, dA + (long long)K0 * lda + c2, lda,
+                               dA + (long long)KB * lda + c2, lda, ctx->st, 1, ctx->tcws, sr, cap_rest,
+                               ctx->agg_ev[1]);
+        }
+        if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "block update (rest)"));
+        ev_split = ctx->agg_ev[1];
+        ev_far = ctx->agg_ev[2];
+        CK(cudaEventRecord(ev_far, sr));
+      }
+    }
   }
   if (ev_rest) CK(cudaStreamWaitEvent(s, ev_rest, 0));
   if (ev_blk) CK(cudaStreamWaitEvent(s, ev_blk, 0));
+  if (ev_far) CK(cudaStreamWaitEvent(s, ev_far, 0));
   DevState h{};
   if ((ps = read_state(ctx, &h, s)) != PRRP_OK) return fail(ps);
   collect_timing(ctx);
@@ -1607,6 +1763,12 @@ prrp_status prrp_ctx_set_sm_split(prrp_ctx* ctx, int panel_ctas, int block_ctas)
   if (panel_ctas < ctx->num_sms && panel_ctas + block_ctas > ctx->num_sms - 8) return PRRP_ERR_INVALID_ARG;
   ctx->split_panel = panel_ctas;
   ctx->split_blk = block_ctas;
+  return PRRP_OK;
+}
+
+prrp_status prrp_ctx_set_update_block(prrp_ctx* ctx, int nb) {
+  if (!ctx || nb < 0 || nb > kAggMaxNB) return PRRP_ERR_INVALID_ARG;
+  ctx->agg_nb = nb;
   return PRRP_OK;
 }
 

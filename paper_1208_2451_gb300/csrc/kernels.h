@@ -105,9 +105,26 @@ cudaError_t launch_gemm_fp64(int m, int n, int k, const double* L, long long ldl
 // max_ctas > 0 caps the persistent grid (one CTA per SM), leaving the other SMs free for
 // kernels that run beside it.
 size_t tc_workspace_bytes(int prec, int m, int n, int k);
+// after_split, when given, is recorded on s once both operands are in ws: from then on
+// L and U may change.
 cudaError_t launch_tc_update(int prec, int m, int n, int k, const double* L, long long ldl,
                              const double* U, long long ldu, double* C, long long ldc, DevState* st,
-                             int track, void* ws, cudaStream_t s, int max_ctas = 0);
+                             int track, void* ws, cudaStream_t s, int max_ctas = 0,
+                             cudaEvent_t after_split = nullptr);
+
+// Aggregated update of the mixed-precision forms (one rank-NB product per block of panels).
+// Block width limit: with TF32 operands, wider blocks no longer precondition FP64
+// refinement at kappa = 1e4 (the rank-NB product takes the block's U rows, not the
+// unreduced A12 of the per-panel form).
+constexpr int kAggMaxNB = 256;
+// Rows that moved between the block's start (perm0: row ids at positions K0..K0+rows-1)
+// and now (perm): (i, src) position pairs relative to K0 into pairs, their number into
+// *count (at most cap); pos0 is n ints of scratch.
+cudaError_t launch_block_pairs(const int* perm0, const int* perm, int K0, int rows, int* pos0, int* pairs,
+                               int* count, int cap, DevState* st, cudaStream_t s);
+// The moves of those pairs over columns c0..c0+nc-1, through tmp (cap x nc doubles).
+cudaError_t launch_block_moves(double* A, long long lda, int K0, int c0, int nc, const int* pairs,
+                               const int* count, int cap, double* tmp, DevState* st, cudaStream_t s);
 
 // GEPP on the w x w diagonal block at A[k0][k0]; in-block pivots to ipiv, perm updated,
 // max |U11| tracked.

@@ -564,7 +564,7 @@ cudaError_t launch_tc_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const
 template <int MODE>
 cudaError_t launch_tc_mode(int M, int N, int K, const double* L, long long ldl, const double* U, long long ldu,
                            double* C, long long ldc, DevState* st, int track, void* wsA, void* wsB,
-                           int max_ctas, cudaStream_t s) {
+                           int max_ctas, cudaStream_t s, cudaEvent_t after_split) {
   using Cfg = TcCfg<MODE, 0>;
   const int kblocks = (K + 63) / 64, kpad = kblocks * 64;
   const int Mpad = (M + kBM - 1) / kBM * kBM, Npad = (N + kBN - 1) / kBN * kBN;
@@ -574,6 +574,7 @@ cudaError_t launch_tc_mode(int M, int N, int K, const double* L, long long ldl, 
   split_kernel<MODE, true><<<static_cast<int>(std::min<long long>((tb + 255) / 256, 152 * 16)), 256, 0, s>>>(
       U, ldu, N, K, Npad, kpad, wsB);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && after_split) e = cudaEventRecord(after_split, s);
   if (e != cudaSuccess) return e;
   CUtensorMap ma, mb, mc;
   if (!make_map(&ma, wsA, MODE, Cfg::NS * Mpad, kpad) || !make_map(&mb, wsB, MODE, Cfg::NS * Npad, kpad))
@@ -876,17 +877,20 @@ size_t tc_workspace_bytes(int prec, int M, int N, int K) {
 
 cudaError_t launch_tc_update(int prec, int M, int N, int K, const double* L, long long ldl, const double* U,
                              long long ldu, double* C, long long ldc, DevState* st, int track, void* ws,
-                             cudaStream_t s, int max_ctas) {
-  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-  if (prec == PRRP_FP64_EMU) return launch_ozaki(M, N, K, L, ldl, U, ldu, C, ldc, st, track, ws, max_ctas, s);
+                             cudaStream_t s, int max_ctas, cudaEvent_t after_split) {
+  if (M <= 0 || N <= 0 || K <= 0) return after_split ? cudaEventRecord(after_split, s) : cudaSuccess;
+  if (prec == PRRP_FP64_EMU) {
+    cudaError_t e = launch_ozaki(M, N, K, L, ldl, U, ldu, C, ldc, st, track, ws, max_ctas, s);
+    return (e == cudaSuccess && after_split) ? cudaEventRecord(after_split, s) : e;
+  }
   const int mode = prec == PRRP_TF32 ? 0 : 1;
   const int ns = mode == 0 ? 1 : 3, eb = mode == 0 ? 4 : 2;
   const size_t kpad = static_cast<size_t>((K + 63) / 64) * 64;
   const size_t Mpad = static_cast<size_t>((M + kBM - 1) / kBM) * kBM;
   uint8_t* a = static_cast<uint8_t*>(ws);
   uint8_t* b = a + ((ns * eb * kpad * Mpad + 1023) & ~size_t(1023));
-  if (mode == 0) return launch_tc_mode<0>(M, N, K, L, ldl, U, ldu, C, ldc, st, track, a, b, max_ctas, s);
-  return launch_tc_mode<1>(M, N, K, L, ldl, U, ldu, C, ldc, st, track, a, b, max_ctas, s);
+  if (mode == 0) return launch_tc_mode<0>(M, N, K, L, ldl, U, ldu, C, ldc, st, track, a, b, max_ctas, s, after_split);
+  return launch_tc_mode<1>(M, N, K, L, ldl, U, ldu, C, ldc, st, track, a, b, max_ctas, s, after_split);
 }
 
 }  // namespace prrp

@@ -129,15 +129,21 @@ def _mixed_solve(prrp, ctx, A, B, prec, b):
     return LU, perm, st, dB.cpu().numpy(), info
 
 
+@pytest.mark.parametrize("nb", [0, 256, 128])
 @pytest.mark.parametrize("prec,n,kappa", [(1, 2048, None), (1, 1500, 1e4), (2, 1500, 1e6), (2, 400, 1e8)])
-def test_gmres_refinement_reaches_fp64(prrp, ctx, prec, n, kappa):
+def test_gmres_refinement_reaches_fp64(prrp, ctx, prec, n, kappa, nb):
     """Where the factors' precision times the conditioning leaves classic refinement slow or
     divergent (TF32 on larger random matrices and at kappa = 1e4, where kappa u_TF32 > 1;
     3xBF16 up to kappa = 1e8 at n = 400), refinement continues with GMRES preconditioned by
-    the factors and still reaches FP64-level backward error."""
+    the factors and still reaches FP64-level backward error -- with the per-panel update
+    (nb = 0) and with the rank-NB aggregated one (blocks of 4 and 2 panels)."""
     A = pi.randn(n, 31) if kappa is None else pi.conditioned(n, kappa, 31)
     B = pi.rhs(n, 3, 31)
-    LU, perm, st, X, info = _mixed_solve(prrp, ctx, A, B, prec, 64)
+    prrp.prrp_ctx_set_update_block(ctx, nb)
+    try:
+        LU, perm, st, X, info = _mixed_solve(prrp, ctx, A, B, prec, 64)
+    finally:
+        prrp.prrp_ctx_set_update_block(ctx, 0)
     assert info["eta"] <= 1e-15, info
     for c in range(3):
         assert M.eta(A, X[:, c], B[:, c]) <= 1e-15
@@ -173,3 +179,65 @@ def test_mixed_factor_and_refine(prrp, ctx, prec, n, b, kappa):
     assert info["eta"] <= 1e-15, info
     for c in range(B.shape[1]):
         assert M.eta(A, X[:, c], B[:, c]) <= 1e-15
+
+
+def _factor(prrp, ctx, A, prec, b, tau, nb):
+    prrp.prrp_ctx_set_update_block(ctx, nb)
+    try:
+        dA = torch.from_numpy(A).cuda()
+        F = prrp.prrp_factor(ctx, dA, b=b, tau=tau, prec=prec)
+        out = dA.cpu().numpy(), F.perm().astype(np.int64), F.stats()
+        F.close()
+    finally:
+        prrp.prrp_ctx_set_update_block(ctx, 0)
+    return out
+
+
+@pytest.mark.parametrize("prec,n,b,nb,tau", [(2, 1024, 64, 256, 2.0), (1, 1024, 64, 256, 2.0), (2, 1000, 64, 128, 2.0),
+                                             (2, 900, 16, 256, 1.05), (2, 777, 32, 96, 1.1), (1, 700, 64, 192, 2.0),
+                                             (2, 1500, 48, 200, 1.2)])
+def test_aggregated_update(prrp, ctx, prec, n, b, nb, tau):
+    """The rank-NB form of the update (blocks of floor(nb / b) panels; the columns right of a
+    block moved, solved and updated once at the block's end): P A = L U to the mode's
+    accuracy, every panel's pivots a valid LU_PRRP selection of the exact A, and, beside the
+    per-panel form of the same mode, the same factors to that accuracy wherever both chose
+    the same pivots."""
+    A = pi.randn(n, 31 + n + b)
+    LU, perm, st = _factor(prrp, ctx, A, prec, b, tau, nb)
+    assert sorted(perm) == list(range(n))
+    tol = 1e-2 if prec == 1 else 1e-5
+    res = M.factor_residual(A, LU, perm)
+    assert res <= tol * max(1.0, st["growth"]), res
+    mx = oracle.selection_multipliers(A, perm, b)
+    assert max(mx) <= tau * (1 + (0.5 if prec == 1 else 1e-3)), max(mx)
+    assert st["max_l21"] <= tau * (1 + 1e-12)
+    LU1, perm1, st1 = _factor(prrp, ctx, A, prec, b, tau, 0)
+    assert M.factor_residual(A, LU1, perm1) <= tol * max(1.0, st1["growth"])
+    if np.array_equal(perm, perm1):
+        scale = float(np.max(np.abs(LU1)))
+        assert np.max(np.abs(LU - LU1)) <= 50 * tol * scale, float(np.max(np.abs(LU - LU1)) / scale)
+        assert st["growth"] == pytest.approx(st1["growth"], rel=0.5)
+
+
+def test_aggregated_update_refines_to_fp64(prrp, ctx):
+    """A factorization of several blocks from the rank-NB form preconditions FP64
+    refinement to eta <= 1e-15, like the per-panel form."""
+    n, b = 1200, 64
+    A = pi.conditioned(n, 1e4, 33)
+    B = pi.rhs(n, 2, 33)
+    prrp.prrp_ctx_set_update_block(ctx, 256)
+    try:
+        LU, perm, st, X, info = _mixed_solve(prrp, ctx, A, B, 2, b)
+    finally:
+        prrp.prrp_ctx_set_update_block(ctx, 0)
+    assert info["eta"] <= 1e-15, info
+    for c in range(B.shape[1]):
+        assert M.eta(A, X[:, c], B[:, c]) <= 1e-15
+
+
+def test_update_block_limits(prrp, ctx):
+    for bad in (-1, 257):
+        with pytest.raises(prrp.PrrpError) as e:
+            prrp.prrp_ctx_set_update_block(ctx, bad)
+        assert e.value.name == "PRRP_ERR_INVALID_ARG"
+    prrp.prrp_ctx_set_update_block(ctx, 0)
