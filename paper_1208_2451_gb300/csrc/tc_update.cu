@@ -614,8 +614,17 @@ constexpr int kOzSmem = kOzStage + kOzEpi * 32 * kOzXP * 8 + 1024;
 static_assert(kOzSmem + 512 <= kSmemOptin, "one operand stage");
 constexpr uint32_t kOzIdesc = make_idesc(1u, kBM, kOzBN);
 
-// The integer held by a float of magnitude below 2^22, by integer operations.
-__device__ __forceinline__ int f2i_small(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
+// An accumulator's integer a (|a| < 2^22) as the bits of a + 1.5 2^23: a + kOzBias.
+constexpr unsigned kOzBias = 0x4B400000u;
+__device__ __forceinline__ uint32_t oz_bits(uint32_t acc) {
+  return __float_as_uint(__uint_as_float(acc) + 12582912.0f);
+}
+// The biases' total under the epilogue's weights, modulo 2^64 (unsigned arithmetic wraps).
+constexpr unsigned long long kOzBiasSum =
+    static_cast<unsigned long long>(kOzBias) * ((1ull << 41) + (1ull << 34) + (1ull << 27) + (1ull << 20) +
+                                                (1ull << 13) + (1ull << 6)) +
+    kOzBias / 2 + kOzBias / 256;
+static_assert(kOzBias % 256 == 0, "the floors pass through the bias");
 
 // 2^k as a double: subnormal down to 2^-1074, 0 below (an underflowing product is dropped),
 // 2^1023 above the range.
@@ -760,23 +769,32 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_update_kernel(
       if (!__all_sync(0xffffffffu, mbar_wait_bounded(&accf, tcount & 1))) { s_fail = 1; break; }
       tc_fence_after();
       const uint32_t tb = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(h * 32);
-      long long T[32];
+      // T = sum_{d <= 5} a_d 2^(41 - 7 d) + floor(a_6 / 2) + floor(a_7 / 256), a_d the integer
+      // in accumulator d.  Each a_d is read as the bits b_d = a_d + kOzBias of a_d + 1.5 2^23
+      // (one FP32 add); the b_d are summed with their weights modulo 2^64 by wide integer
+      // multiply-adds (kOzBias is a multiple of 256, so the floors pass through it), and the
+      // biases' weighted total comes off once.  |T| < 2^62, so the wrapped sum is T exactly.
+      unsigned long long T[32];
       uint32_t r[32];
-      tmem_ld32(tb, r);
+      tmem_ld32(tb, r);                                      // diagonal 0: 2^41
 #pragma unroll
-      for (int j = 0; j < 32; ++j) T[j] = f2i_small(__uint_as_float(r[j]));
+      for (int j = 0; j < 32; ++j) T[j] = static_cast<unsigned long long>(oz_bits(r[j]) << 9) << 32;
+      tmem_ld32(tb + static_cast<uint32_t>(kOzBN), r);       // diagonal 1: 2^34
+#pragma unroll
+      for (int j = 0; j < 32; ++j) T[j] += static_cast<unsigned long long>(oz_bits(r[j]) << 2) << 32;
 #pragma unroll 1
-      for (int d = 1; d < kOzS - 2; ++d) {                   // T = sum_{d <= 5} acc_d 128^(5 - d)
+      for (int d = 2; d < kOzS - 2; ++d) {                   // diagonals 2..5: 2^27 .. 2^6
         tmem_ld32(tb + static_cast<uint32_t>(d * kOzBN), r);
+        const uint32_t wgt = 1u << (41 - 7 * d);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) T[j] = (T[j] << 7) + f2i_small(__uint_as_float(r[j]));
+        for (int j = 0; j < 32; ++j) T[j] += static_cast<unsigned long long>(oz_bits(r[j])) * wgt;
       }
       tmem_ld32(tb + static_cast<uint32_t>((kOzS - 2) * kOzBN), r);   // diagonal 6: 2^-1
 #pragma unroll
-      for (int j = 0; j < 32; ++j) T[j] = (T[j] << 6) + (f2i_small(__uint_as_float(r[j])) >> 1);
+      for (int j = 0; j < 32; ++j) T[j] += oz_bits(r[j]) >> 1;
       tmem_ld32(tb + static_cast<uint32_t>((kOzS - 1) * kOzBN), r);   // diagonal 7: 2^-8
 #pragma unroll
-      for (int j = 0; j < 32; ++j) T[j] += f2i_small(__uint_as_float(r[j])) >> 8;
+      for (int j = 0; j < 32; ++j) T[j] = T[j] + (oz_bits(r[j]) >> 8) - kOzBiasSum;
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce);                     // accumulators free again
@@ -794,7 +812,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_update_kernel(
 #pragma unroll
         for (int j0 = 0; j0 < 32; j0 += 8) {
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) stg[lane * kOzXP + jj] = static_cast<double>(T[j0 + jj]);
+          for (int jj = 0; jj < 8; ++jj) stg[lane * kOzXP + jj] = static_cast<double>(static_cast<long long>(T[j0 + jj]));
           __syncwarp();
           const int col = c0 + j0 + cl;
           if (j0 + cl < ncols) {
