@@ -432,7 +432,7 @@ prrp_status prrp_ctx_kernel_stats(prrp_ctx* ctx, double* ms, long long* launches
  * and calls no cudaMalloc, cudaFree or other allocating routine.
  *
  * Scratch: the kernel's device state word and cross-CTA exchange records live in one
- * library-wide static device array of 898,816 bytes, which every GPU that loads libprrp.so
+ * library-wide static device array of 2,014,976 bytes, which every GPU that loads libprrp.so
  * holds until the process exits.  The call runs on the caller's current device: dP,
  * dOrder and dL21 must be device memory of that device (INVALID_ARG otherwise).  All calls
  * share the array and it keeps the last call's contents (the state word and the exchange

@@ -53,8 +53,8 @@ struct prrp_ctx {
   double* xval = nullptr;       // panel exchange records
   int2* xkey = nullptr;
   double* xvec = nullptr;
-  unsigned long long* qkey = nullptr;   // QRCP step keys [3][xcap][kQKeyStride]
-  double* qrow = nullptr;               // QRCP records [3][xcap][kQStride]
+  unsigned long long* qkey = nullptr;   // QRCP step keys [kQSlots][xcap][kQKeyStride]
+  double* qrow = nullptr;               // QRCP records [kQSlots][xcap][kQStride]
   int xcap = 0;                 // CTAs the exchange can hold
   int* pairs = nullptr;
   int pairs_cap = 0;
@@ -289,8 +289,8 @@ prrp_status ensure_panel_ws(prrp_ctx* ctx, int n, int w, int max_swaps) {
     if ((s = grow(ctx, &ctx->xval, &c1, 2 * (size_t)G * kXVal)) != PRRP_OK) return s;
     if ((s = grow(ctx, &ctx->xkey, &c2, 2 * (size_t)G)) != PRRP_OK) return s;
     if ((s = grow(ctx, &ctx->xvec, &c3, 2 * (size_t)G * kMaxW)) != PRRP_OK) return s;
-    if ((s = grow(ctx, &ctx->qkey, &c4, 3 * (size_t)G * kQKeyStride)) != PRRP_OK) return s;
-    if ((s = grow(ctx, &ctx->qrow, &c5, 3 * (size_t)G * kQStride)) != PRRP_OK) return s;
+    if ((s = grow(ctx, &ctx->qkey, &c4, kQSlots * (size_t)G * kQKeyStride)) != PRRP_OK) return s;
+    if ((s = grow(ctx, &ctx->qrow, &c5, kQSlots * (size_t)G * kQStride)) != PRRP_OK) return s;
     ctx->xcap = G;
   }
   if ((s = grow_i(ctx, &ctx->pairs, &ctx->pairs_cap, 4 * (w + max_swaps) + 8)) != PRRP_OK) return s;
@@ -308,8 +308,10 @@ prrp_status enqueue_panel(prrp_ctx* ctx, const double* P, long long ldp, int m, 
   prrp_status ps = panel_grid(ctx, m, w, &G, &rpc, max_ctas);
   if (ps != PRRP_OK) return ps;
   CK(cudaMemsetAsync(&ctx->st->barrier, 0, 2 * sizeof(unsigned), s));
-  // a QRCP key slot is empty while it holds 0
-  CK(cudaMemsetAsync(ctx->qkey, 0, 3 * sizeof(unsigned long long) * G * kQKeyStride, s));
+  // a QRCP key is absent while it holds 0 and a record word while it holds the sentinel;
+  // the kernel prepares a slot itself only for its second use within the launch
+  CK(cudaMemsetAsync(ctx->qkey, 0, kQSlots * sizeof(unsigned long long) * G * kQKeyStride, s));
+  CK(cudaMemsetAsync(ctx->qrow, kQSentinelByte, kQSlots * sizeof(double) * G * kQStride, s));
   PanelParams p{};
   p.P = P; p.ldp = ldp; p.m = m; p.w = w; p.tau = tau; p.max_swaps = max_swaps;
   p.col_offset = col_offset; p.L21 = L21; p.ldl = ldl; p.order = order; p.pairs = pairs;

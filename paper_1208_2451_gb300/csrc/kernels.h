@@ -10,7 +10,13 @@ namespace prrp {
 
 constexpr int kXVal = 3;   // doubles per interchange exchange record (the value; 2 spare)
 constexpr int kQStride = kMaxW + 2;   // doubles per QRCP record: the row, then alpha and beta
-constexpr int kQKeyStride = 16;       // u64 per QRCP key slot: one 128-byte line each
+constexpr int kQKeyStride = 1;        // u64 per QRCP key: a step's keys are contiguous
+// QRCP key and record arrays rotate over kQSlots steps; the exchange fences once every
+// kQFenceEvery steps, and kQSlots >= 2 kQFenceEvery + 2 keeps two fences between a slot's
+// preparation and its next use
+constexpr int kQFenceEvery = 4;
+constexpr int kQSlots = 2 * kQFenceEvery + 2;
+constexpr unsigned char kQSentinelByte = 0xFF;   // fills every record slot at launch
 // SM split of the tensor-core modes (prrp_ctx_set_sm_split): panel CTAs, block-stream CTAs
 constexpr int kSplitPanelDefault = 64;
 constexpr int kSplitBlkDefault = 8;
@@ -30,8 +36,8 @@ struct PanelParams {
   double* xval;           // interchange exchange records: [2][G][kXVal] (value)
   int2* xkey;             // [2][G] (tie-breaks)
   double* xvec;           // [2][G][kMaxW] (row)
-  unsigned long long* qkey;   // QRCP step keys [3][G][kQKeyStride], zero at launch
-  double* qrow;               // QRCP records [3][G][kQStride]
+  unsigned long long* qkey;   // QRCP step keys [kQSlots][G][kQKeyStride], zero at launch
+  double* qrow;               // QRCP records [kQSlots][G][kQStride], kQSentinelByte at launch
   int rows_per_cta;
   int cluster_rows;       // panels of at most this many rows run as one cluster (0: default)
   int nopivot;            // 1: unpivoted QR of the panel (CALU_PRRP's L21), no interchanges

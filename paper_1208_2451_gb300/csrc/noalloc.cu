@@ -28,11 +28,11 @@ constexpr size_t kStateBytes = 256;   // DevState, padded
 constexpr size_t kValBytes = 2 * kStaticMaxCtas * kXVal * sizeof(double);
 constexpr size_t kKeyBytes = 2 * kStaticMaxCtas * sizeof(int2);
 constexpr size_t kVecBytes = 2 * (size_t)kStaticMaxCtas * kMaxW * sizeof(double);
-constexpr size_t kQKeyBytes = 3 * kStaticMaxCtas * kQKeyStride * sizeof(unsigned long long);
-constexpr size_t kQRowBytes = 3 * (size_t)kStaticMaxCtas * kQStride * sizeof(double);
+constexpr size_t kQKeyBytes = kQSlots * kStaticMaxCtas * kQKeyStride * sizeof(unsigned long long);
+constexpr size_t kQRowBytes = kQSlots * (size_t)kStaticMaxCtas * kQStride * sizeof(double);
 constexpr size_t kScratchBytes =
-    kStateBytes + kValBytes + kKeyBytes + kVecBytes + kQKeyBytes + kQRowBytes;   // 898,816 B
-static_assert(kScratchBytes == 898816, "the documented size of the static scratch");
+    kStateBytes + kValBytes + kKeyBytes + kVecBytes + kQKeyBytes + kQRowBytes;   // 2,014,976 B
+static_assert(kScratchBytes == 2014976, "the documented size of the static scratch");
 static_assert(sizeof(DevState) <= kStateBytes, "state word does not fit its slot");
 static_assert(kScratchBytes % 256 == 0, "scratch slots keep 256-byte alignment");
 
@@ -88,11 +88,15 @@ extern "C" prrp_status prrp_panel_select_noalloc(int m, int w, const double* dP,
   if (scratch_address(&base) != cudaSuccess) return PRRP_ERR_CUDA;
   DevState* st = reinterpret_cast<DevState*>(base);
   // The array keeps the previous call's contents: clear the state word (error status,
-  // barrier arrivals, counters) and the QRCP step keys (a slot is empty while it holds 0).
-  // The other records need no clearing: each is written before it is read within a call.
+  // barrier arrivals, counters) and the QRCP step keys (a key is absent while it holds 0),
+  // and fill the QRCP records with the sentinel pattern (a word is taken once it no longer
+  // holds it).  The other records need no clearing: each is written before it is read
+  // within a call.
   if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return PRRP_ERR_CUDA;
   unsigned char* qbase = base + kStateBytes + kValBytes + kKeyBytes + kVecBytes;
   if (cudaMemsetAsync(qbase, 0, kQKeyBytes, s) != cudaSuccess) return PRRP_ERR_CUDA;
+  if (cudaMemsetAsync(qbase + kQKeyBytes, kQSentinelByte, kQSlots * sizeof(double) * G * kQStride, s) != cudaSuccess)
+    return PRRP_ERR_CUDA;
   PanelParams p{};
   p.P = dP; p.ldp = ldp; p.m = m; p.w = w; p.tau = tau; p.max_swaps = max_swaps;
   p.col_offset = 0; p.L21 = dL21; p.ldl = w; p.order = dOrder; p.pairs = nullptr;

@@ -36,17 +36,19 @@
 // arithmetic is the same as applying the whole reflector before proposing.  Rows are
 // spread so that every FP64 unit of the SM gets the same share.
 //
-// Exchange, grid form (one cooperative grid): each CTA writes its proposed row to its
-// record in global memory, with a sentinel (a NaN) in the record's alpha and beta words,
-// then its 64-bit key (below) to its slot of the step's key array with a release store;
-// each slot has a cache line of its own.  Meanwhile the helper warp computes the
-// candidate's alpha and beta and overwrites the sentinels.  Warp 0 of every CTA polls all
-// slots until every key of the step is present (one L2 round trip after the last
-// arrival), takes the largest key, and fetches the winner's record; an alpha or beta word
-// still holding the sentinel is read again (each word is written once per step, whole).
-// Three key arrays rotate over the steps: a CTA clears its slot of the next step's array
-// before it publishes, which is safe because every reader of that array's previous step
-// has already published the step after it.
+// Exchange, grid form (one cooperative grid): key arrays (a step's keys contiguous) and
+// record arrays rotate over kQSlots steps, all keys absent (0) and all record words
+// sentinels (a NaN that finite data never produces) at launch.  At step t a CTA writes its
+// proposed row into its record with plain stores and its 64-bit key (below) with a
+// relaxed store; the helper warp computes the candidate's alpha and beta and writes them
+// into the record.  Warp 0 of every CTA polls all keys until every key of the step is
+// present, takes the largest, and reads again any word of the winner's record that still
+// holds the sentinel.  Right after publishing, it prepares its slot of step t - 2 (every
+// reader of it has published step t - 1 since) for the slot's next use: key absent,
+// record sentinels.  One
+// fence every kQFenceEvery steps orders those preparations before the slot's reuse for
+// every reader, so no stale key or record word is ever taken, and no store waits on the
+// critical path for another store to complete.
 // Exchange, cluster form (m <= 512 by default): the grid is one thread-block cluster;
 // each CTA pushes its key into every CTA's shared memory and arrives on that CTA's
 // mbarrier; the winner's row, alpha and beta are read directly from the winning CTA's
@@ -78,8 +80,10 @@ constexpr int kBarProp = 1;                        // named barriers: proposals 
 constexpr int kBarWin = 2;                         //   winner of the step published,
 constexpr int kBarHelp = 3;                        //   this CTA's record published
 constexpr int kPollSlots = (kPanelMaxCtas + 31) / 32;
-// alpha / beta words of a record whose reflector is not written yet (a NaN: never a value)
-constexpr unsigned long long kSentinel = 0x7FF8DEADBEEF0001ull;
+// A record word not written yet: all bits set, a NaN that finite data never produces (the
+// host fills every record slot with 0xFF bytes at launch, the kernel refills a slot for
+// its reuse).
+constexpr unsigned long long kSentinel = ~0ull;
 
 // Cooperative panel grids from different streams or contexts must not be resident at the
 // same time: two partially resident grids could each wait at their grid barrier for CTAs
@@ -110,6 +114,9 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ double ld_relaxed_f64(const double* p) {
+  return vval(ld_relaxed_u64(reinterpret_cast<const unsigned long long*>(p)));
 }
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
@@ -284,20 +291,28 @@ __global__ void __launch_bounds__(kThreads, 1) panel_rrqr_kernel(PanelParams p) 
       for (int k = 0; k < NV; ++k) xv[k] = 0.0;
       double alpha = 0.0, beta = 0.0;
       if constexpr (!CL) {
-        const int q = t % 3;
+        const int q = t % kQSlots;
         const size_t slot = (size_t)q * G + cta;
         double* rec = p.qrow + slot * kQStride;
-        if (has) {
+        // The key is a relaxed store: this CTA's absent key and sentinel record of slot q,
+        // prepared kQSlots - 2 steps ago, are ordered before it by an exchange fence since
+        // (the host prepared every slot's first use before the launch).  The record's
+        // values need no ordering: a reader takes a word once it no longer holds the
+        // sentinel.
+        if (has)
           for (int i = lane; i < w; i += 32) rec[i] = Ps[d.aux * SP + i];
-          if (lane < 2) rec[kMaxW + lane] = vval(kSentinel);
-        }
         __syncwarp();
-        if (lane == 0) {
-          // release: the record (ordered by the warp barrier) before the key
-          st_relaxed_u64(p.qkey + ((size_t)((t + 1) % 3) * G + cta) * kQKeyStride, 0ull);
-          st_release_u64(p.qkey + slot * kQKeyStride, has ? d.v : kNoCand);
-        }
+        if (lane == 0) st_relaxed_u64(p.qkey + slot * kQKeyStride, has ? d.v : kNoCand);
         named_arrive(kBarHelp, 64);                   // the helper may fill in alpha, beta
+        if (t >= 2 && t - 2 + kQSlots < w) {
+          // the slot of step t - 2, whose readers have all published step t - 1 since: its
+          // key absent and its record sentinels again, for step t - 2 + kQSlots
+          const size_t s2 = (size_t)((t - 2) % kQSlots) * G + cta;
+          unsigned long long* r2 = reinterpret_cast<unsigned long long*>(p.qrow + s2 * kQStride);
+          for (int i = lane; i < w; i += 32) st_relaxed_u64(r2 + i, kSentinel);
+          if (lane < 2) st_relaxed_u64(r2 + kMaxW + lane, kSentinel);
+          if (lane == 0) st_relaxed_u64(p.qkey + s2 * kQKeyStride, 0ull);
+        }
         // Poll every slot of this step until all keys are present.  Whenever the best key
         // seen so far changes, that candidate's record is fetched at once, so the fetch of
         // the final winner is usually complete when its last competitor's key arrives.
@@ -323,19 +338,15 @@ __global__ void __launch_bounds__(kThreads, 1) panel_rrqr_kernel(PanelParams p) 
           const Cand b = warp_max_key(Cand{bk, 0, 0, bs});
           const bool all = __all_sync(0xffffffffu, mine);
           if ((b.v >> kPosBits) != 0ull && b.aux != pref) {
-            // acquire: the record after its key (every lane fences, then the warp barrier
-            // orders the other lanes' loads after the lane that saw the key)
-            fence_acq_rel_gpu();
-            __syncwarp();
             pref = b.aux;
             const double* src = p.qrow + ((size_t)q * G + pref) * kQStride;
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
               const int i = lane + 32 * k;
-              xv[k] = i < w ? __ldcg(src + i) : 0.0;
+              xv[k] = i < w ? ld_relaxed_f64(src + i) : 0.0;
             }
-            alpha = __ldcg(src + kMaxW);
-            beta = __ldcg(src + kMaxW + 1);
+            alpha = ld_relaxed_f64(src + kMaxW);
+            beta = ld_relaxed_f64(src + kMaxW + 1);
           }
           if (all) {
             g = b;
@@ -350,20 +361,38 @@ __global__ void __launch_bounds__(kThreads, 1) panel_rrqr_kernel(PanelParams p) 
             break;
           }
         }
+        // Exchange fence, once every kQFenceEvery steps.  As a release, it orders this CTA's
+        // slot preparations so far before its next key; as an acquire, after every CTA's
+        // key of this step, it makes every CTA's preparations released by their previous
+        // exchange fence visible.  A slot prepared at step s is released by the first
+        // fence at a step >= s and acquired by the next one, at most 2 kQFenceEvery - 1
+        // steps later, before its next use at step s + kQSlots - 2.
+        if (t % kQFenceEvery == kQFenceEvery - 1) fence_acq_rel_gpu();
         if (ok && (g.v >> kPosBits) != 0ull) {
-          // the winner's helper may not have written its reflector yet
+          // words of the winner's record (its row, alpha, beta) still holding the sentinel
+          // are read again
           const double* src = p.qrow + ((size_t)q * G + g.aux) * kQStride;
           unsigned spins2 = 0;
-          while (vbits(alpha) == kSentinel || vbits(beta) == kSentinel) {
-            if (++spins2 > (limit >> 3) || ((spins2 & 63) == 0 && dev_status(st) != 0)) {
-              if (atomicCAS(&st->status, 0, PRRP_ERR_TIMEOUT) == 0) st->timeout_site = 5;
+          while (true) {
+            bool pending = vbits(alpha) == kSentinel || vbits(beta) == kSentinel;
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+              if (lane + 32 * k < w && vbits(xv[k]) == kSentinel) pending = true;
+            if (!__any_sync(0xffffffffu, pending)) break;
+            const bool stop = ++spins2 > (limit >> 3) || ((spins2 & 63) == 0 && dev_status(st) != 0);
+            if (__any_sync(0xffffffffu, stop)) {
+              if (lane == 0 && atomicCAS(&st->status, 0, PRRP_ERR_TIMEOUT) == 0) st->timeout_site = 5;
               ok = 0;
               break;
             }
-            alpha = __ldcg(src + kMaxW);
-            beta = __ldcg(src + kMaxW + 1);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+              const int i = lane + 32 * k;
+              if (i < w && vbits(xv[k]) == kSentinel) xv[k] = ld_relaxed_f64(src + i);
+            }
+            if (vbits(alpha) == kSentinel) alpha = ld_relaxed_f64(src + kMaxW);
+            if (vbits(beta) == kSentinel) beta = ld_relaxed_f64(src + kMaxW + 1);
           }
-          ok = __all_sync(0xffffffffu, ok);
         }
       } else {
         const int q = par;
@@ -460,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1) panel_rrqr_kernel(PanelParams p) 
       named_sync(kBarHelp, 64);                       // the record and its sentinels are out
       if (has && lane == 0) {
         if constexpr (!CL) {
-          double* rec = p.qrow + ((size_t)(t % 3) * G + cta) * kQStride;
+          double* rec = p.qrow + ((size_t)(t % kQSlots) * G + cta) * kQStride;
           rec[kMaxW] = alpha;
           rec[kMaxW + 1] = beta;
         } else {
