@@ -16,6 +16,8 @@ constexpr int kQKeyStride = 1;        // u64 per QRCP key: a step's keys are con
 // preparation and its next use
 constexpr int kQFenceEvery = 4;
 constexpr int kQSlots = 2 * kQFenceEvery + 2;
+static_assert(kQSlots >= 2 * kQFenceEvery + 2 && kQFenceEvery >= 1,
+              "a slot's preparation must be released and acquired before its reuse");
 constexpr unsigned char kQSentinelByte = 0xFF;   // fills every record slot at launch
 // SM split of the tensor-core modes (prrp_ctx_set_sm_split): panel CTAs, block-stream CTAs
 constexpr int kSplitPanelDefault = 64;
