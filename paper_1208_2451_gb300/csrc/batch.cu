@@ -27,6 +27,8 @@ namespace {
 constexpr int kBT = 256;          // threads per batch CTA
 constexpr int kBW = 32;           // largest panel width in the batched kernel
 constexpr int kUnroll = 4;        // global loads a thread keeps in flight in the copy and update loops
+constexpr int kMaxBRows = 4;      // panel rows per thread: the batched entry points refuse n > 1024
+static_assert(kMaxBRows * kBT >= 1024, "every panel row has a thread");
 
 struct BKey {
   unsigned long long v;
@@ -118,8 +120,8 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
         BKey d{dbits(fmax(nrm[r], 0.0)), pos[r], r};
         if (bbetter(d, c)) c = d;
       }
-    // block argmax, then the reflector's scalars (a square root and a division on the
-    // FP64 pipe) formed once by warp 0 and broadcast with the reduction's second barrier
+    // block argmax, then the reflector's scalars formed once and broadcast with the next
+    // barrier
     BKey g = c;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -134,7 +136,9 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
     if (g.v == 0ull) return PRRP_ERR_SINGULAR;
     const int rw = g.k2, pw = g.k1;
     const double* xw = Ps + rw * sp;
-    if (tid == 0) {
+    // the reflector's scalars (a square root and a division on the FP64 pipe), by the last
+    // thread: it owns no panel row while m < kBT, so the rows' partial sums below overlap them
+    if (tid == kBT - 1) {
       const double x0 = xw[t];
       const double normx = sqrt(__longlong_as_double(static_cast<long long>(g.v)));
       const double alpha = (x0 >= 0.0) ? -normx : normx;
@@ -143,11 +147,29 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
       s_refl[2] = x0 - alpha;
       Rs[t * kBW + t] = alpha;
     }
+    // the part of each row's dot product with the reflector that needs no reflector scalar,
+    // sum_{i > t} x_w[i] x[i], while those scalars are formed (same arithmetic as below)
+    double sdot[kMaxBRows];
+#pragma unroll
+    for (int q = 0; q < kMaxBRows; ++q) {
+      const int r = tid + q * kBT;
+      double s1 = 0.0, s2 = 0.0;
+      if (r < m && r != rw && pos[r] >= t) {
+        const double* x = Ps + r * sp;
+        int i = t + 1;
+        for (; i + 1 < w; i += 2) { s1 = fma(xw[i], x[i], s1); s2 = fma(xw[i + 1], x[i + 1], s2); }
+        if (i < w) s1 = fma(xw[i], x[i], s1);
+      }
+      sdot[q] = s1 + s2;
+    }
     for (int i = tid; i < t; i += kBT) Rs[i * kBW + t] = xw[i];
     __syncthreads();
     const double beta = s_refl[1], v0 = s_refl[2];
     // the winner row's values are read by every thread below; it is itself not updated
-    for (int r = tid; r < m; r += kBT) {
+#pragma unroll
+    for (int q = 0; q < kMaxBRows; ++q) {
+      const int r = tid + q * kBT;
+      if (r >= m) break;
       const int pr = pos[r];
       if (r == rw) {                                 // the winner takes position t
         pos[r] = t;
@@ -155,11 +177,8 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
       }
       if (pr < t) continue;
       double* x = Ps + r * sp;
-      double s0 = v0 * x[t], s1 = 0.0, s2 = 0.0;     // three chains over the row
-      int i = t + 1;
-      for (; i + 1 < w; i += 2) { s1 = fma(xw[i], x[i], s1); s2 = fma(xw[i + 1], x[i + 1], s2); }
-      if (i < w) s1 = fma(xw[i], x[i], s1);
-      const double f = beta * (s0 + (s1 + s2));
+      const double s0 = v0 * x[t];                   // three chains over the row
+      const double f = beta * (s0 + sdot[q]);
       const double xt = fma(-f, v0, x[t]);
       x[t] = xt;
       for (int k = t + 1; k < w; ++k) x[k] = fma(-f, xw[k], x[k]);
@@ -478,10 +497,10 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
         }
       }
       __syncthreads();
-      if (tid == 0) {                          // perm follows the same moves
-        for (int k = 0; k < np; ++k) mv[2 * k + 1] = perm[k0 + mv[2 * k + 1]];
-        for (int k = 0; k < np; ++k) perm[k0 + mv[2 * k]] = mv[2 * k + 1];
-      }
+      // perm follows the same moves: every moved row's id is read before any is written
+      for (int k = tid; k < np; k += kBT) mv[2 * k + 1] = perm[k0 + mv[2 * k + 1]];
+      __syncthreads();
+      for (int k = tid; k < np; k += kBT) perm[k0 + mv[2 * k]] = mv[2 * k + 1];
       // block multipliers L21 into the strip of the rows below the block
       for (int e = tid; e < m * w; e += kBT) {
         const int r = e / w, c = e - r * w;
@@ -597,14 +616,11 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
         W[(long long)(k0 + i) * n + k0 + j] = static_cast<T>(Dg[i * (kBW + 1) + j]);
       }
       __syncthreads();
-      if (tid == 0) {
+      if (tid == 0) {                          // GEPP's interchanges composed: position <- row
         for (int t = 0; t < w; ++t) s_src[t] = t;
         for (int t = 0; t < w; ++t) {
           const int p = ipiv[t];
-          if (p != t) {
-            const int x = perm[k0 + t]; perm[k0 + t] = perm[k0 + p]; perm[k0 + p] = x;
-            const int y = s_src[t]; s_src[t] = s_src[p]; s_src[p] = y;
-          }
+          if (p != t) { const int y = s_src[t]; s_src[t] = s_src[p]; s_src[p] = y; }
         }
       }
       for (int e = tid; e < w * w; e += kBT) {
@@ -612,6 +628,11 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
         Lt[i * (kBW + 1) + k] = static_cast<T>(Dg[i * (kBW + 1) + k]);
       }
       __syncthreads();
+      {                                        // perm follows them, all rows read first
+        const int pv = tid < w ? perm[k0 + s_src[tid]] : 0;
+        __syncthreads();
+        if (tid < w) perm[k0 + tid] = pv;
+      }
       // block-row interchanges outside the block and U12 = L11^-1 A12 in T, one column per
       // thread: the column's w values are loaded in their interchanged order into registers
       for (int j = tid; j < n; j += kBT) {
