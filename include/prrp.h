@@ -378,9 +378,10 @@ prrp_status prrp_ctx_set_panel_mode(prrp_ctx* ctx, int cluster_max_rows);
  * not fit them), the diagonal-block work (GEPP, U12, the final multipliers) on at most
  * block_ctas, and the rest of each trailing update on the remaining SMs, so that the
  * panel of step j + 1 runs beside the update of step j.  0 selects the library default
- * (64 and 8); panel_ctas equal to the SM count turns the split off.  INVALID_ARG when a
- * value is negative or above the SM count, or when the two leave fewer than 8 SMs for the
- * rest update.  The plain FP64 mode is not affected. */
+ * (64 and 8; 96 and 8 for PRRP_TF32 and PRRP_BF16X3 at n <= 10240, where the panels take
+ * a larger share of the work); panel_ctas equal to the SM count turns the split off.
+ * INVALID_ARG when a value is negative or above the SM count, or when the two leave fewer
+ * than 8 SMs for the rest update.  The plain FP64 mode is not affected. */
 prrp_status prrp_ctx_set_sm_split(prrp_ctx* ctx, int panel_ctas, int block_ctas);
 
 /* Aggregated trailing update of prrp_factor in the modes PRRP_TF32 and PRRP_BF16X3

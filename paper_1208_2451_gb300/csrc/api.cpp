@@ -566,7 +566,8 @@ prrp_status factor_impl(prrp_ctx* ctx, int n, double* dA, int lda, const prrp_op
   // and keeps the whole GPU.
   int cap_panel = 0, cap_blk = 0, cap_rest = 0;
   if (o.prec != PRRP_FP64) {
-    cap_panel = ctx->split_panel > 0 ? ctx->split_panel : kSplitPanelDefault;
+    const bool small_n = n <= kSplitSmallN && o.prec != PRRP_FP64_EMU;
+    cap_panel = ctx->split_panel > 0 ? ctx->split_panel : (small_n ? kSplitPanelSmallN : kSplitPanelDefault);
     cap_blk = ctx->split_blk > 0 ? ctx->split_blk : kSplitBlkDefault;
     if (cap_panel >= ctx->num_sms) {
       cap_panel = cap_blk = 0;                 // no split: every kernel may take every SM

@@ -21,6 +21,10 @@ static_assert(kQSlots >= 2 * kQFenceEvery + 2 && kQFenceEvery >= 1,
 constexpr unsigned char kQSentinelByte = 0xFF;   // fills every record slot at launch
 // SM split of the tensor-core modes (prrp_ctx_set_sm_split): panel CTAs, block-stream CTAs
 constexpr int kSplitPanelDefault = 64;
+// TF32 / 3xBF16 at n <= kSplitSmallN: the panels' share of the work is larger, and 96
+// panel CTAs were faster (n = 8192, 3xBF16: 51.8 against 55.2 ms; n = 16384: 64 best)
+constexpr int kSplitPanelSmallN = 96;
+constexpr int kSplitSmallN = 10240;
 constexpr int kSplitBlkDefault = 8;
 
 struct PanelParams {
