@@ -241,3 +241,25 @@ def test_update_block_limits(prrp, ctx):
             prrp.prrp_ctx_set_update_block(ctx, bad)
         assert e.value.name == "PRRP_ERR_INVALID_ARG"
     prrp.prrp_ctx_set_update_block(ctx, 0)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_sm_split_changes_no_result(prrp, ctx, prec):
+    """The SM split is a tuning knob: every tile of the update and every panel compute the
+    same arithmetic whichever CTAs run them, so the factors are bit-identical."""
+    n, b = 1536, 64
+    A = pi.randn(n, 41)
+    outs = []
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for split in ((0, 0), (40, 8), (96, 16), (sms, 0)):          # (sms, 0): no split
+        prrp.prrp_ctx_set_sm_split(ctx, *split)
+        try:
+            dA = torch.from_numpy(A).cuda()
+            F = prrp.prrp_factor(ctx, dA, b=b, prec=prec)
+            outs.append((dA.cpu().numpy(), F.perm().astype(np.int64)))
+            F.close()
+        finally:
+            prrp.prrp_ctx_set_sm_split(ctx, 0, 0)
+    for LU, perm in outs[1:]:
+        assert np.array_equal(perm, outs[0][1])
+        assert np.array_equal(LU, outs[0][0])
