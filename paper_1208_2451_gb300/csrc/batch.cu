@@ -305,6 +305,24 @@ __device__ __forceinline__ void stage_block(const T* W, int n, int k0, int kb, d
   __syncthreads();
 }
 
+// sum_k row[k] y_k over one block of the substitution (y_k in Db's spare column), in
+// order k = 0, 1, ...: for a full FP32 block every row value is loaded before the first
+// FMA, so the loads wait on memory once rather than once per term.
+template <typename T>
+__device__ __forceinline__ T block_dot(const T* row, int kb, const double* Db) {
+  T acc = 0;
+  if (sizeof(T) == 4 && kb == 32) {
+    T r[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) r[k] = row[k];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc = fma(r[k], static_cast<T>(Db[k * (kBW + 1) + kBW]), acc);
+  } else {
+    for (int k = 0; k < kb; ++k) acc = fma(row[k], static_cast<T>(Db[k * (kBW + 1) + kBW]), acc);
+  }
+  return acc;
+}
+
 // x (length n, stored in FP64) <- U^-1 L^-1 P y for the T factors in W (ld n); y = b or r
 // in v, x out.  The arithmetic is T's: FP32 factors give FP32-accurate solutions whatever
 // the arithmetic, so the FP32-factor form solves in FP32 (its refinement keeps the
@@ -326,15 +344,14 @@ __device__ void batch_lu_solve(const T* W, int n, const int* perm, const double*
         const T xk = __shfl_sync(0xffffffffu, y, k);
         if (lane > k && lane < kb) y = fma(-static_cast<T>(Db[lane * (kBW + 1) + k]), xk, y);
       }
-      if (lane < kb) x[k0 + lane] = static_cast<double>(y);
+      if (lane < kb) {
+        x[k0 + lane] = static_cast<double>(y);
+        Db[lane * (kBW + 1) + kBW] = static_cast<double>(y);   // the block's solution, for the rows below
+      }
     }
     __syncthreads();
-    for (int i = k0 + kb + tid; i < n; i += kBT) {
-      const T* row = W + (long long)i * n + k0;
-      T acc = 0;
-      for (int k = 0; k < kb; ++k) acc = fma(row[k], static_cast<T>(x[k0 + k]), acc);
-      x[i] = static_cast<double>(static_cast<T>(x[i]) - acc);
-    }
+    for (int i = k0 + kb + tid; i < n; i += kBT)
+      x[i] = static_cast<double>(static_cast<T>(x[i]) - block_dot<T>(W + (long long)i * n + k0, kb, Db));
     __syncthreads();
   }
   for (int kend = n; kend > 0; kend -= 32) {
@@ -347,15 +364,14 @@ __device__ void batch_lu_solve(const T* W, int n, const int* perm, const double*
         const T xk = __shfl_sync(0xffffffffu, y, k);
         if (lane < k) y = fma(-static_cast<T>(Db[lane * (kBW + 1) + k]), xk, y);
       }
-      if (lane < kb) x[k0 + lane] = static_cast<double>(y);
+      if (lane < kb) {
+        x[k0 + lane] = static_cast<double>(y);
+        Db[lane * (kBW + 1) + kBW] = static_cast<double>(y);   // the block's solution, for the rows above
+      }
     }
     __syncthreads();
-    for (int i = tid; i < k0; i += kBT) {
-      const T* row = W + (long long)i * n + k0;
-      T acc = 0;
-      for (int k = 0; k < kb; ++k) acc = fma(row[k], static_cast<T>(x[k0 + k]), acc);
-      x[i] = static_cast<double>(static_cast<T>(x[i]) - acc);
-    }
+    for (int i = tid; i < k0; i += kBT)
+      x[i] = static_cast<double>(static_cast<T>(x[i]) - block_dot<T>(W + (long long)i * n + k0, kb, Db));
     __syncthreads();
   }
 }
