@@ -194,8 +194,11 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
       nrm[r] = n2;
       pos[r] = (pr == t) ? pw : pr;
     }
-    __syncthreads();
+    // no barrier here: the next step's argmax reads only this thread's rows, s_w and
+    // s_refl were read before the barrier above, and the next winner row's update is
+    // ordered by the next step's first barrier
   }
+  __syncthreads();
   for (int i = tid; i < w; i += kBT) rdiag[i] = 1.0 / Rs[i * kBW + i];
   __syncthreads();
   for (int r = tid; r < m; r += kBT) {
