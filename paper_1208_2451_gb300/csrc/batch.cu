@@ -70,15 +70,31 @@ __device__ BKey block_best_key(BKey c, BKey* s_w) {
   return r;
 }
 
-__device__ __forceinline__ double block_sum(double v, double* s_red) {
+// Block-wide sums of three values, each returned to every thread (two __syncthreads);
+// s_red holds 3 kBT / 32 doubles.
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* s_red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if (lane == 0) s_red[warp] = v;
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+    c += __shfl_xor_sync(0xffffffffu, c, off);
+  }
+  if (lane == 0) {
+    s_red[warp] = a;
+    s_red[kBT / 32 + warp] = b;
+    s_red[2 * (kBT / 32) + warp] = c;
+  }
   __syncthreads();
-  double r = 0.0;
-  for (int k = 0; k < kBT / 32; ++k) r += s_red[k];
+  double ra = 0.0, rb = 0.0, rc = 0.0;
+  for (int k = 0; k < kBT / 32; ++k) {
+    ra += s_red[k];
+    rb += s_red[kBT / 32 + k];
+    rc += s_red[2 * (kBT / 32) + k];
+  }
   __syncthreads();
-  return r;
+  a = ra;
+  b = rb;
+  c = rc;
 }
 
 __device__ __forceinline__ double block_max(double v, double* s_red) {
@@ -287,27 +303,6 @@ struct BatchArgs {
   unsigned* counter;         // work list head
 };
 
-// The kb x kb diagonal block at (k0, k0) of W into Db (FP64, stride kBW + 1), every thread
-// loading its share at once, so the dependent block solve reads shared memory.
-template <typename T>
-__device__ __forceinline__ void stage_block(const T* W, int n, int k0, int kb, double* Db) {
-  __syncthreads();
-  for (int e0 = threadIdx.x; e0 < kb * kb; e0 += kUnroll * kBT) {
-    T v[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int e = e0 + u * kBT, i = e / kb, k = e - i * kb;
-      v[u] = e < kb * kb ? W[(long long)(k0 + i) * n + k0 + k] : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int e = e0 + u * kBT, i = e / kb, k = e - i * kb;
-      if (e < kb * kb) Db[i * (kBW + 1) + k] = static_cast<double>(v[u]);
-    }
-  }
-  __syncthreads();
-}
-
 // sum_k row[k] y_k over one block of the substitution (y_k in Db's spare column), in
 // order k = 0, 1, ...: for a full FP32 block every row value is loaded before the first
 // FMA, so the loads wait on memory once rather than once per term.
@@ -326,56 +321,110 @@ __device__ __forceinline__ T block_dot(const T* row, int kb, const double* Db) {
   return acc;
 }
 
+constexpr int kDb = kBW * (kBW + 1);   // one staged diagonal block: FP64, row stride kBW + 1
+static_assert(kUnroll * kBT >= kBW * kBW, "one round of loads stages a whole diagonal block");
+
+// The kb x kb diagonal block at (k0, k0) of W, loaded into registers (kb >= 1) ...
+template <typename T>
+__device__ __forceinline__ void block_load(const T* W, int n, int k0, int kb, T (&v)[kUnroll]) {
+#pragma unroll
+  for (int u = 0; u < kUnroll; ++u) {
+    const int e = threadIdx.x + u * kBT, i = e / kb, k = e - i * kb;
+    v[u] = e < kb * kb ? W[(long long)(k0 + i) * n + k0 + k] : T(0);
+  }
+}
+
+// ... and stored into Db in FP64.
+template <typename T>
+__device__ __forceinline__ void block_store(const T (&v)[kUnroll], int kb, double* Db) {
+#pragma unroll
+  for (int u = 0; u < kUnroll; ++u) {
+    const int e = threadIdx.x + u * kBT, i = e / kb, k = e - i * kb;
+    if (e < kb * kb) Db[i * (kBW + 1) + k] = static_cast<double>(v[u]);
+  }
+}
+
 // x (length n, stored in FP64) <- U^-1 L^-1 P y for the T factors in W (ld n); y = b or r
 // in v, x out.  The arithmetic is T's: FP32 factors give FP32-accurate solutions whatever
 // the arithmetic, so the FP32-factor form solves in FP32 (its refinement keeps the
 // residual and the accumulated solution in FP64, Section 3.3); dependent FP64 chains would
-// cost 64 cycles per step on this GPU.  Db: kBW x (kBW + 1) doubles of shared scratch.
+// cost 64 cycles per step on this GPU.
+// Blocks of 32 rows: warp 0 solves a block's triangle by a chain of shuffles, then every
+// thread takes the block's solution out of its rows beyond the block and, in the same
+// phase, stages the next block's diagonal into the other half of Db, so a block costs two
+// barriers and the staging loads wait on memory together with the update's.  The backward
+// chain multiplies by each diagonal's reciprocal, formed by its lane before the chain.
+// Db: 2 kDb doubles of shared scratch.
 template <typename T>
-__device__ void batch_lu_solve(const T* W, int n, const int* perm, const double* rhs, double* x,
-                               double* s_red, double* Db) {
+__device__ __noinline__ void batch_lu_solve(const T* W, int n, const int* perm, const double* rhs, double* x, double* Db) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nfwd = (n + 31) / 32;                    // forward blocks [32 q, 32 q + 32)
+  T sv[kUnroll];
   for (int i = tid; i < n; i += kBT) x[i] = rhs[perm[i]];
+  block_load(W, n, 0, min(32, n), sv);
+  block_store(sv, min(32, n), Db);
   __syncthreads();
-  // forward substitution, blocks of 32 rows: warp 0 solves the block, all update below
-  for (int k0 = 0; k0 < n; k0 += 32) {
-    const int kb = min(32, n - k0);
-    stage_block(W, n, k0, kb, Db);
+  int buf = 0;
+  // forward substitution
+  for (int q = 0; q < nfwd; ++q) {
+    const int k0 = 32 * q, kb = min(32, n - k0);
+    double* D = Db + buf * kDb;
     if (warp == 0) {
       T y = lane < kb ? static_cast<T>(x[k0 + lane]) : T(0);
-      for (int k = 0; k < kb; ++k) {
-        const T xk = __shfl_sync(0xffffffffu, y, k);
-        if (lane > k && lane < kb) y = fma(-static_cast<T>(Db[lane * (kBW + 1) + k]), xk, y);
+#pragma unroll
+      for (int k = 0; k < kBW - 1; ++k) {
+        const T lk = static_cast<T>(D[lane * (kBW + 1) + k]);   // in the block's buffer: read for every lane
+        if (k + 1 < kb) {
+          const T xk = __shfl_sync(0xffffffffu, y, k);
+          if (lane > k) y = fma(-lk, xk, y);
+        }
       }
       if (lane < kb) {
         x[k0 + lane] = static_cast<double>(y);
-        Db[lane * (kBW + 1) + kBW] = static_cast<double>(y);   // the block's solution, for the rows below
+        D[lane * (kBW + 1) + kBW] = static_cast<double>(y);   // the block's solution, for the rows below
       }
     }
     __syncthreads();
+    // the next block's diagonal: the next forward block, after the last one the first
+    // backward block [max(0, n - 32), n)
+    const int s0 = q + 1 < nfwd ? k0 + 32 : max(0, n - 32);
+    const int sb = q + 1 < nfwd ? min(32, n - s0) : n - s0;
+    block_load(W, n, s0, sb, sv);
     for (int i = k0 + kb + tid; i < n; i += kBT)
-      x[i] = static_cast<double>(static_cast<T>(x[i]) - block_dot<T>(W + (long long)i * n + k0, kb, Db));
+      x[i] = static_cast<double>(static_cast<T>(x[i]) - block_dot<T>(W + (long long)i * n + k0, kb, D));
+    block_store(sv, sb, Db + (buf ^ 1) * kDb);
     __syncthreads();
+    buf ^= 1;
   }
+  // backward substitution, blocks [max(0, kend - 32), kend)
   for (int kend = n; kend > 0; kend -= 32) {
     const int k0 = max(0, kend - 32), kb = kend - k0;
-    stage_block(W, n, k0, kb, Db);
+    double* D = Db + buf * kDb;
     if (warp == 0) {
       T y = lane < kb ? static_cast<T>(x[k0 + lane]) : T(0);
-      for (int k = kb - 1; k >= 0; --k) {
-        if (lane == k) y = y / static_cast<T>(Db[k * (kBW + 1) + k]);
-        const T xk = __shfl_sync(0xffffffffu, y, k);
-        if (lane < k) y = fma(-static_cast<T>(Db[lane * (kBW + 1) + k]), xk, y);
+      const T rinv = lane < kb ? T(1) / static_cast<T>(D[lane * (kBW + 1) + lane]) : T(0);
+#pragma unroll
+      for (int k = kBW - 1; k >= 0; --k) {
+        const T uk = static_cast<T>(D[lane * (kBW + 1) + k]);   // in the block's buffer: read for every lane
+        if (k < kb) {
+          if (lane == k) y *= rinv;
+          const T xk = __shfl_sync(0xffffffffu, y, k);
+          if (lane < k) y = fma(-uk, xk, y);
+        }
       }
       if (lane < kb) {
         x[k0 + lane] = static_cast<double>(y);
-        Db[lane * (kBW + 1) + kBW] = static_cast<double>(y);   // the block's solution, for the rows above
+        D[lane * (kBW + 1) + kBW] = static_cast<double>(y);   // the block's solution, for the rows above
       }
     }
     __syncthreads();
+    const int s0 = max(0, k0 - 32), sb = k0 - s0;
+    if (sb > 0) block_load(W, n, s0, sb, sv);
     for (int i = tid; i < k0; i += kBT)
-      x[i] = static_cast<double>(static_cast<T>(x[i]) - block_dot<T>(W + (long long)i * n + k0, kb, Db));
+      x[i] = static_cast<double>(static_cast<T>(x[i]) - block_dot<T>(W + (long long)i * n + k0, kb, D));
+    if (sb > 0) block_store(sv, sb, Db + (buf ^ 1) * kDb);
     __syncthreads();
+    buf ^= 1;
   }
 }
 
@@ -388,7 +437,7 @@ template <typename T, int RB, int WB>
 __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ BKey s_w[kBT / 32];
-  __shared__ double s_red[kBT / 32];
+  __shared__ double s_red[3 * (kBT / 32)];
   __shared__ int s_sys, s_status, s_np;
   __shared__ double s_rp;                           // reciprocal of the current GEPP pivot
   __shared__ double Rs[kBW * kBW];
@@ -699,6 +748,7 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
       for (int i = tid; i < n; i += kBT) a.perm_out[sys][i] = perm[i];
     // ---- solve and FP64 refinement, one right-hand side at a time
     double* xv = V;
+    double* Db = reinterpret_cast<double*>(smem_raw);   // the substitution's two diagonal blocks (the panel's space)
     double* rv = V + a.nmax;
     double* dv = rv + a.nmax;
     const int nr = a.nrhs[sys], ldb = a.ldb[sys];
@@ -726,21 +776,39 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
       double* bcol = dv;                                   // the right-hand side, packed
       for (int i = tid; i < n; i += kBT) bcol[i] = Bp[(long long)i * ldb + c];
       __syncthreads();
-      batch_lu_solve<T>(W, n, perm, bcol, xv, s_red, Dg);
+      batch_lu_solve<T>(W, n, perm, bcol, xv, Db);
       double eta = 0.0, eta_first = 0.0;
       int it = 0;
       for (;;) {
-        // r = b - A x in FP64 and eta = ||r||_1 / (||A||_1 ||x||_1 + ||b||_1)
+        // r = b - A x in FP64 and eta = ||r||_1 / (||A||_1 ||x||_1 + ||b||_1).  Four rows per
+        // warp pass, lanes along the columns (coalesced, four independent FMA chains per
+        // lane); the four rows' lane sums are reduced together by a transposing butterfly
+        // (lanes 16..31 keep rows 2, 3 and lanes 0..15 rows 0, 1; then the lanes with bit 3
+        // set keep the odd row), six FP64 additions for four rows instead of twenty.
         double rs = 0.0, xs = 0.0, bs = 0.0;
         const int lane = tid & 31, warp = tid >> 5;
-        for (int i = warp; i < n; i += kBT / 32) {        // one warp per row, coalesced
-          const double* arow = A + (long long)i * lda;
-          double acc = 0.0;
-          for (int k = lane; k < n; k += 32) acc = fma(arow[k], xv[k], acc);
-          for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-          if (lane == 0) {
-            const double r = bcol[i] - acc;
-            rv[i] = r;
+        const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+        const int qr = (h16 ? 2 : 0) + (h8 ? 1 : 0);     // the row this lane's sum ends in
+        for (int i0 = 4 * warp; i0 < n; i0 += 4 * (kBT / 32)) {
+          const int nrow = min(4, n - i0);
+          double acc[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int k = lane; k < n; k += 32) {
+            const double xk = xv[k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (q < nrow) acc[q] = fma(A[(long long)(i0 + q) * lda + k], xk, acc[q]);
+          }
+          double k0v = h16 ? acc[2] : acc[0], k1v = h16 ? acc[3] : acc[1];
+          k0v += __shfl_xor_sync(0xffffffffu, h16 ? acc[0] : acc[2], 16);
+          k1v += __shfl_xor_sync(0xffffffffu, h16 ? acc[1] : acc[3], 16);
+          double c = h8 ? k1v : k0v;
+          c += __shfl_xor_sync(0xffffffffu, h8 ? k0v : k1v, 8);
+          c += __shfl_xor_sync(0xffffffffu, c, 4);
+          c += __shfl_xor_sync(0xffffffffu, c, 2);
+          c += __shfl_xor_sync(0xffffffffu, c, 1);
+          if ((lane & 7) == 0 && qr < nrow) {
+            const double r = bcol[i0 + qr] - c;
+            rv[i0 + qr] = r;
             rs += abs_int(r);
           }
         }
@@ -748,9 +816,7 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
           xs += abs_int(xv[i]);
           bs += abs_int(bcol[i]);
         }
-        rs = block_sum(rs, s_red);
-        xs = block_sum(xs, s_red);
-        bs = block_sum(bs, s_red);
+        block_sum3(rs, xs, bs, s_red);
         const double den = anorm * xs + bs;
         const double e = den > 0.0 ? rs / den : (rs > 0.0 ? INFINITY : 0.0);
         if (it == 0) eta_first = e;
@@ -768,7 +834,7 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
         double* rhs_r = V + 3 * a.nmax;
         for (int i = tid; i < n; i += kBT) rhs_r[i] = rv[i];
         __syncthreads();
-        batch_lu_solve<T>(W, n, perm, rhs_r, corr, s_red, Dg);
+        batch_lu_solve<T>(W, n, perm, rhs_r, corr, Db);
         for (int i = tid; i < n; i += kBT) xv[i] += corr[i];
         __syncthreads();
         ++it;
@@ -793,7 +859,10 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
 }  // namespace
 
 size_t batch_smem_bytes(int nmax, int b) {
-  return (size_t)nmax * (b + 1) * sizeof(double) + (size_t)nmax * (2 * sizeof(double) + sizeof(int)) + 64;
+  // the panel (m x (b + 1) doubles, norms, positions), reused by the substitution's two
+  // staged diagonal blocks
+  const size_t panel = (size_t)nmax * (b + 1) * sizeof(double) + (size_t)nmax * (2 * sizeof(double) + sizeof(int));
+  return std::max(panel, (size_t)2 * kDb * sizeof(double)) + 64;
 }
 
 cudaError_t launch_batch(int fp64, int grid, int rb, const BatchLaunch& L, cudaStream_t s) {
