@@ -436,28 +436,54 @@ def prrp_batch_tune(ctx: Context, nmax: int, b=16, prec=PRRP_FP32, stream=None) 
            ctx.handle)
 
 
+def _dev_matrices(ts, name):
+    """One pass over a list of 2-D float64 CUDA tensors with contiguous rows: an int64 array
+    of (data pointer, rows, columns, leading dimension) per tensor."""
+    import torch
+    f64 = torch.float64
+    if not all(isinstance(t, torch.Tensor) and t.dtype is f64 and t.is_cuda and t.dim() == 2 for t in ts):
+        raise TypeError(f"{name}: 2-D float64 CUDA tensors are expected")
+    m = np.array([(t.data_ptr(), *t.shape, *t.stride()) for t in ts], dtype=np.int64).reshape(len(ts), 5)
+    if np.any((m[:, 2] > 1) & (m[:, 4] != 1)):
+        raise ValueError(f"{name}: rows must be contiguous (row-major)")
+    m[:, 4] = np.maximum(np.maximum(m[:, 3], m[:, 2]), 1)
+    return m[:, [0, 1, 2, 4]]
+
+
+_INFO_DTYPE = np.dtype({"names": ["iterations", "eta0", "eta"], "formats": ["<i4", "<f8", "<f8"],
+                        "offsets": [prrp_solve_info.iterations.offset, prrp_solve_info.eta0.offset,
+                                    prrp_solve_info.eta.offset],
+                        "itemsize": C.sizeof(prrp_solve_info)})
+
+
 def prrp_batch_solve(ctx: Context, As, Bs, b=16, tau=2.0, prec=PRRP_FP32, max_swaps=64,
                      refine_max_iter=10, refine_target=2.0 ** -53, stream=None, perms=None):
     """Solve the independent systems As[i] X_i = Bs[i] (float64 CUDA tensors, n_i <= 1024)
     in one batched launch; Bs[i] is overwritten by X_i.  perms (optional): int32 CUDA
     tensors receiving each system's row permutation.  Returns (statuses, infos)."""
     count = len(As)
-    n = (C.c_int * count)(*[int(A.shape[0]) for A in As])
-    lda = (C.c_int * count)(*[_dev_matrix(A, "A") for A in As])
-    nrhs = (C.c_int * count)(*[int(B.shape[1]) for B in Bs])
-    ldb = (C.c_int * count)(*[_dev_matrix(B, "B") for B in Bs])
-    pa = (C.c_void_p * count)(*[A.data_ptr() for A in As])
-    pb = (C.c_void_p * count)(*[B.data_ptr() for B in Bs])
-    pp = (C.c_void_p * count)(*[p.data_ptr() for p in perms]) if perms is not None else None
-    st = (C.c_int * count)()
-    infos = (prrp_solve_info * count)()
+    if len(Bs) != count or (perms is not None and len(perms) != count):
+        raise ValueError("As, Bs (and perms) must have one entry per system")
+    ma = _dev_matrices(As, "A")
+    mb = _dev_matrices(Bs, "B")
+    n = np.ascontiguousarray(ma[:, 1], dtype=np.int32)
+    lda = np.ascontiguousarray(ma[:, 3], dtype=np.int32)
+    nrhs = np.ascontiguousarray(mb[:, 2], dtype=np.int32)
+    ldb = np.ascontiguousarray(mb[:, 3], dtype=np.int32)
+    pa = np.ascontiguousarray(ma[:, 0])
+    pb = np.ascontiguousarray(mb[:, 0])
+    pp = np.array([p.data_ptr() for p in perms], dtype=np.int64) if perms is not None else None
+    st = np.zeros(count, dtype=np.int32)
+    infos = np.zeros(count, dtype=_INFO_DTYPE)
     o = default_opts(b, tau, prec, max_swaps, refine_max_iter, refine_target)
-    rc = _lib.prrp_batch_solve(ctx.handle, count, n, pa, lda, nrhs, pb, ldb, pp, C.byref(o),
-                               _stream_ptr(stream), st, infos)
+    rc = _lib.prrp_batch_solve(ctx.handle, count, n.ctypes.data, pa.ctypes.data, lda.ctypes.data,
+                               nrhs.ctypes.data, pb.ctypes.data, ldb.ctypes.data,
+                               pp.ctypes.data if pp is not None else None, C.byref(o),
+                               _stream_ptr(stream), st.ctypes.data, infos.ctypes.data)
     # outcomes of individual systems are reported per system; anything else raises
     _check(rc, "prrp_batch_solve", ctx.handle,
            allow=(PRRP_ERR_SINGULAR, PRRP_ERR_NONFINITE, PRRP_ERR_SWAP_LIMIT, PRRP_ERR_NOT_CONVERGED))
-    return list(st), [{"iterations": i.iterations, "eta0": i.eta0, "eta": i.eta} for i in infos]
+    return st.tolist(), [{"iterations": i, "eta0": e0, "eta": e} for i, e0, e in infos.tolist()]
 
 
 

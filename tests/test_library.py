@@ -83,3 +83,23 @@ def test_binding_signatures_match_header():
     arity = _prototype_arity()
     wrong = {n: (len(B._SIGS[n][1]), arity[n]) for n in arity if len(B._SIGS[n][1]) != arity[n]}
     assert not wrong, wrong
+
+
+def test_batch_marshalling_host_logic():
+    """prrp_batch_solve's argument marshalling: host tensors are refused before any call,
+    and the per-system results are read back with the C struct's layout."""
+    import numpy as np
+    import torch
+    import paper_1208_2451_gb300 as P
+    B = P.binding
+    try:
+        B._dev_matrices([torch.zeros(4, 4, dtype=torch.float64)], "A")
+    except TypeError:
+        pass
+    else:
+        raise AssertionError("a host tensor was accepted")
+    arr = (B.prrp_solve_info * 3)()
+    for i in range(3):
+        arr[i].iterations, arr[i].eta0, arr[i].eta = i + 1, 10.0 ** -i, 2.0 ** -(50 + i)
+    view = np.frombuffer(arr, dtype=B._INFO_DTYPE)
+    assert view.tolist() == [(i + 1, 10.0 ** -i, 2.0 ** -(50 + i)) for i in range(3)]
