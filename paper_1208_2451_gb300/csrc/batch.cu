@@ -27,6 +27,7 @@ namespace {
 constexpr int kBT = 256;          // threads per batch CTA
 constexpr int kBW = 32;           // largest panel width in the batched kernel
 constexpr int kUnroll = 4;        // global loads a thread keeps in flight in the copy and update loops
+constexpr int kUpd = 8;           // C values a lane loads per row before its FMAs in the Schur update
 constexpr int kMaxBRows = 4;      // panel rows per thread: the batched entry points refuse n > 1024
 static_assert(kMaxBRows * kBT >= 1024, "every panel row has a thread");
 
@@ -606,17 +607,17 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
 #pragma unroll
             for (int k = 0; k < WB; ++k) lr[r][k] = (k < w && i0 + r < rows) ? l[k] : T(0);
           }
-          for (int j0 = lane; j0 < nc; j0 += 32 * kUnroll) {
-            T cv[RB][kUnroll];                       // the C values, loaded before any use
+          for (int j0 = lane; j0 < nc; j0 += 32 * kUpd) {
+            T cv[RB][kUpd];                       // the C values, loaded before any use
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
+            for (int u = 0; u < kUpd; ++u)
 #pragma unroll
               for (int r = 0; r < RB; ++r) {
                 const int j = j0 + 32 * u;
                 cv[r][u] = (j < nc && i0 + r < rows) ? W[(long long)(k0 + w + i0 + r) * n + k0 + w + j] : T(0);
               }
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
+            for (int u = 0; u < kUpd; ++u) {
               const int j = j0 + 32 * u;
               if (j >= nc) break;
               T acc[RB];
