@@ -322,6 +322,42 @@ __device__ __forceinline__ T block_dot(const T* row, int kb, const double* Db) {
   return acc;
 }
 
+// x[i] -= sum_k W[i][k0 + k] y_k for the rows i in [r0, r1) (y_k in D's spare column).
+// FP32: 32 rows per warp pass, lane k reading column k0 + k of every row (one coalesced
+// line per row, all 32 loads in flight), and the 32 rows' products summed over the lanes
+// by a transposing butterfly (31 shuffles), after which lane r holds row r's sum.  FP64:
+// one row per thread (the butterfly's additions would double the FP64 instructions).
+template <typename T>
+__device__ __forceinline__ void block_rows_update(const T* W, int n, int k0, int kb, const double* D, double* x,
+                                                  int r0, int r1) {
+  if constexpr (sizeof(T) == 4) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T yl = lane < kb ? static_cast<T>(D[lane * (kBW + 1) + kBW]) : T(0);
+    for (int g0 = r0 + 32 * warp; g0 < r1; g0 += 32 * (kBT / 32)) {
+      T v[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        v[r] = (lane < kb && g0 + r < r1) ? W[(long long)(g0 + r) * n + k0 + lane] : T(0);
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] *= yl;
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int j = 0; j < off; ++j) {
+          const T send = up ? v[j] : v[j + off];
+          const T keep = up ? v[j + off] : v[j];
+          v[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+      }
+      if (g0 + lane < r1) x[g0 + lane] = static_cast<double>(static_cast<T>(x[g0 + lane]) - v[0]);
+    }
+  } else {
+    for (int i = r0 + threadIdx.x; i < r1; i += kBT)
+      x[i] = static_cast<double>(static_cast<T>(x[i]) - block_dot<T>(W + (long long)i * n + k0, kb, D));
+  }
+}
+
 constexpr int kDb = kBW * (kBW + 1);   // one staged diagonal block: FP64, row stride kBW + 1
 static_assert(kUnroll * kBT >= kBW * kBW, "one round of loads stages a whole diagonal block");
 
@@ -391,8 +427,7 @@ __device__ __noinline__ void batch_lu_solve(const T* W, int n, const int* perm, 
     const int s0 = q + 1 < nfwd ? k0 + 32 : max(0, n - 32);
     const int sb = q + 1 < nfwd ? min(32, n - s0) : n - s0;
     block_load(W, n, s0, sb, sv);
-    for (int i = k0 + kb + tid; i < n; i += kBT)
-      x[i] = static_cast<double>(static_cast<T>(x[i]) - block_dot<T>(W + (long long)i * n + k0, kb, D));
+    block_rows_update<T>(W, n, k0, kb, D, x, k0 + kb, n);
     block_store(sv, sb, Db + (buf ^ 1) * kDb);
     __syncthreads();
     buf ^= 1;
@@ -421,8 +456,7 @@ __device__ __noinline__ void batch_lu_solve(const T* W, int n, const int* perm, 
     __syncthreads();
     const int s0 = max(0, k0 - 32), sb = k0 - s0;
     if (sb > 0) block_load(W, n, s0, sb, sv);
-    for (int i = tid; i < k0; i += kBT)
-      x[i] = static_cast<double>(static_cast<T>(x[i]) - block_dot<T>(W + (long long)i * n + k0, kb, D));
+    block_rows_update<T>(W, n, k0, kb, D, x, 0, k0);
     if (sb > 0) block_store(sv, sb, Db + (buf ^ 1) * kDb);
     __syncthreads();
     buf ^= 1;
