@@ -27,7 +27,8 @@ namespace {
 constexpr int kBT = 256;          // threads per batch CTA
 constexpr int kBW = 32;           // largest panel width in the batched kernel
 constexpr int kUnroll = 4;        // global loads a thread keeps in flight in the copy and update loops
-constexpr int kUpd = 8;           // C values a lane loads per row before its FMAs in the Schur update
+constexpr int kUpd = 8;           // loads a thread keeps in flight in the row moves, and C values a lane
+                                  // loads per row before its FMAs in the Schur update
 constexpr int kMaxBRows = 4;      // panel rows per thread: the batched entry points refuse n > 1024
 static_assert(kMaxBRows * kBT >= 1024, "every panel row has a thread");
 
@@ -114,9 +115,12 @@ __device__ __forceinline__ double block_max(double v, double* s_red) {
 // multipliers M(:, pos - w) = (R11^-1 R12)(:, .).  Returns 0, or a prrp_status.
 // One thread per panel row: an FP64 instruction holds its sub-partition's FP64 unit for
 // 64 cycles whatever its active lanes, so whole rows per lane (no team reductions, no
-// per-row fixed cost spread over several lanes) issue the fewest FP64 instructions.
+// per-row fixed cost spread over several lanes) issue the fewest FP64 instructions.  For
+// the same reason the argmax key and the norm-recompute test compare IEEE bit patterns on
+// the integer pipe (non-negative doubles order as their bits), and thr[r] keeps 1e-4 times
+// the row's last exactly computed squared norm.
 __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, int max_swaps,
-                                  double* nrm, double* nref, int* pos, double* Rs, double* rdiag,
+                                  double* nrm, double* thr, int* pos, double* Rs, double* rdiag,
                                   BKey* s_w, int* swaps_out) {
   __shared__ double s_refl[3];                   // alpha, beta, v0 of the current reflector
   const int tid = threadIdx.x, lane = tid & 31;
@@ -127,14 +131,16 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
     for (; i + 1 < w; i += 2) { s0 = fma(x[i], x[i], s0); s1 = fma(x[i + 1], x[i + 1], s1); }
     if (i < w) s0 = fma(x[i], x[i], s0);
     const double s = s0 + s1;
-    nrm[r] = s; nref[r] = s; pos[r] = r;
+    nrm[r] = s; thr[r] = 1e-4 * s; pos[r] = r;
   }
   __syncthreads();
   for (int t = 0; t < w; ++t) {
     BKey c{0ull, 0x7fffffff, 0};
     for (int r = tid; r < m; r += kBT)
       if (pos[r] >= t) {
-        BKey d{dbits(fmax(nrm[r], 0.0)), pos[r], r};
+        // the key of fmax(nrm, 0): negative values and NaN count as 0
+        const long long nb = static_cast<long long>(dbits(nrm[r]));
+        BKey d{nb > 0 && nb <= static_cast<long long>(kInfBits) ? static_cast<unsigned long long>(nb) : 0ull, pos[r], r};
         if (bbetter(d, c)) c = d;
       }
     // block argmax, then the reflector's scalars formed once and broadcast with the next
@@ -194,19 +200,19 @@ __device__ int batch_panel_select(double* Ps, int sp, int m, int w, double tau, 
       }
       if (pr < t) continue;
       double* x = Ps + r * sp;
-      const double s0 = v0 * x[t];                   // three chains over the row
-      const double f = beta * (s0 + sdot[q]);
+      const double f = beta * fma(v0, x[t], sdot[q]);
       const double xt = fma(-f, v0, x[t]);
       x[t] = xt;
       for (int k = t + 1; k < w; ++k) x[k] = fma(-f, xw[k], x[k]);
       double n2 = fma(-xt, xt, nrm[r]);
-      if (!(n2 > 1e-4 * nref[r])) {
+      const long long nb = static_cast<long long>(dbits(n2)), tb = static_cast<long long>(dbits(thr[r]));
+      if (!(nb > tb && nb <= static_cast<long long>(kInfBits))) {   // !(n2 > thr): recompute
         double e0 = 0.0, e1 = 0.0;
         int k = t + 1;
         for (; k + 1 < w; k += 2) { e0 = fma(x[k], x[k], e0); e1 = fma(x[k + 1], x[k + 1], e1); }
         if (k < w) e0 = fma(x[k], x[k], e0);
         n2 = e0 + e1;
-        nref[r] = n2;
+        thr[r] = 1e-4 * n2;
       }
       nrm[r] = n2;
       pos[r] = (pr == t) ? pw : pr;
@@ -529,8 +535,8 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
       const int sp = w + 1;
       double* Ps = reinterpret_cast<double*>(smem_raw);
       double* nrm = Ps + (size_t)m * sp;
-      double* nref = nrm + m;
-      int* pos = reinterpret_cast<int*>(nref + m);
+      double* thr = nrm + m;
+      int* pos = reinterpret_cast<int*>(thr + m);
       for (int e0 = tid; e0 < m * w; e0 += kUnroll * kBT) {
         T v[kUnroll];
 #pragma unroll
@@ -546,7 +552,7 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
       }
       __syncthreads();
       int sw = 0;
-      const int st = batch_panel_select(Ps, sp, m, w, a.tau, a.max_swaps, nrm, nref, pos, Rs, rdiag,
+      const int st = batch_panel_select(Ps, sp, m, w, a.tau, a.max_swaps, nrm, thr, pos, Rs, rdiag,
                                         s_w, &sw);
       if (st != 0) {
         if (tid == 0) s_status = st;
@@ -572,29 +578,29 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(BatchArgs<T> a) {
         __syncthreads();
         break;
       }
-      for (int e0 = tid; e0 < np * n; e0 += kUnroll * kBT) {
-        T v[kUnroll];
+      for (int e0 = tid; e0 < np * n; e0 += kUpd * kBT) {
+        T v[kUpd];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < kUpd; ++u) {
           const int e = e0 + u * kBT, k = e / n, j = e - k * n;
           v[u] = e < np * n ? W[(long long)(k0 + mv[2 * k + 1]) * n + j] : T(0);
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < kUpd; ++u) {
           const int e = e0 + u * kBT;
           if (e < np * n) Tmp[e] = v[u];
         }
       }
       __syncthreads();
-      for (int e0 = tid; e0 < np * n; e0 += kUnroll * kBT) {
-        T v[kUnroll];
+      for (int e0 = tid; e0 < np * n; e0 += kUpd * kBT) {
+        T v[kUpd];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < kUpd; ++u) {
           const int e = e0 + u * kBT;
           v[u] = e < np * n ? Tmp[e] : T(0);
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < kUpd; ++u) {
           const int e = e0 + u * kBT, k = e / n, j = e - k * n;
           if (e < np * n) W[(long long)(k0 + mv[2 * k]) * n + j] = v[u];
         }
