@@ -441,9 +441,15 @@ def _dev_matrices(ts, name):
     of (data pointer, rows, columns, leading dimension) per tensor."""
     import torch
     f64 = torch.float64
-    if not all(isinstance(t, torch.Tensor) and t.dtype is f64 and t.is_cuda and t.dim() == 2 for t in ts):
+    if len(ts) == 0:
+        return np.zeros((0, 4), dtype=np.int64)
+    try:
+        m = np.array([(t.data_ptr(), *t.shape, *t.stride(), t.dtype is f64 and t.is_cuda) for t in ts],
+                     dtype=np.int64)
+    except (AttributeError, TypeError, ValueError):     # not tensors, or of mixed dimensions
+        m = None
+    if m is None or m.ndim != 2 or m.shape[1] != 6 or not m[:, 5].all():
         raise TypeError(f"{name}: 2-D float64 CUDA tensors are expected")
-    m = np.array([(t.data_ptr(), *t.shape, *t.stride()) for t in ts], dtype=np.int64).reshape(len(ts), 5)
     if np.any((m[:, 2] > 1) & (m[:, 4] != 1)):
         raise ValueError(f"{name}: rows must be contiguous (row-major)")
     m[:, 4] = np.maximum(np.maximum(m[:, 3], m[:, 2]), 1)
