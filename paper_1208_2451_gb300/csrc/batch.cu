@@ -397,7 +397,8 @@ __device__ __forceinline__ void block_store(const T (&v)[kUnroll], int kb, doubl
 // phase, stages the next block's diagonal into the other half of Db, so a block costs two
 // barriers and the staging loads wait on memory together with the update's.  The backward
 // chain multiplies by each diagonal's reciprocal, formed by its lane before the chain.
-// Db: 2 kDb doubles of shared scratch.
+// Db: 2 kDb doubles of shared scratch.  Not inlined: its register needs then stay out of
+// the kernel body's allocation, which spilled with it inlined.
 template <typename T>
 __device__ __noinline__ void batch_lu_solve(const T* W, int n, const int* perm, const double* rhs, double* x, double* Db) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -416,7 +417,7 @@ __device__ __noinline__ void batch_lu_solve(const T* W, int n, const int* perm, 
       T y = lane < kb ? static_cast<T>(x[k0 + lane]) : T(0);
 #pragma unroll
       for (int k = 0; k < kBW - 1; ++k) {
-        const T lk = static_cast<T>(D[lane * (kBW + 1) + k]);   // in the block's buffer: read for every lane
+        const T lk = static_cast<T>(D[lane * (kBW + 1) + k]);   // in the buffer for every lane; used only inside the block
         if (k + 1 < kb) {
           const T xk = __shfl_sync(0xffffffffu, y, k);
           if (lane > k) y = fma(-lk, xk, y);
@@ -447,7 +448,7 @@ __device__ __noinline__ void batch_lu_solve(const T* W, int n, const int* perm, 
       const T rinv = lane < kb ? T(1) / static_cast<T>(D[lane * (kBW + 1) + lane]) : T(0);
 #pragma unroll
       for (int k = kBW - 1; k >= 0; --k) {
-        const T uk = static_cast<T>(D[lane * (kBW + 1) + k]);   // in the block's buffer: read for every lane
+        const T uk = static_cast<T>(D[lane * (kBW + 1) + k]);   // in the buffer for every lane; used only inside the block
         if (k < kb) {
           if (lane == k) y *= rinv;
           const T xk = __shfl_sync(0xffffffffu, y, k);
