@@ -456,6 +456,18 @@ def _dev_matrices(ts, name):
     return m[:, [0, 1, 2, 4]]
 
 
+def _dev_perms(perms, n):
+    """Device pointers of the permutation outputs: contiguous int32 CUDA tensors of at least
+    n[i] elements (checked here, so the kernel never writes through a host pointer)."""
+    import torch
+    i32 = torch.int32
+    if len(perms) != len(n) or not all(
+            isinstance(p, torch.Tensor) and p.dtype is i32 and p.is_cuda and p.is_contiguous() and p.numel() >= int(k)
+            for p, k in zip(perms, n)):
+        raise TypeError("perms: one contiguous int32 CUDA tensor of at least n_i elements per system is expected")
+    return np.array([p.data_ptr() for p in perms], dtype=np.int64)
+
+
 _INFO_DTYPE = np.dtype({"names": ["iterations", "eta0", "eta"], "formats": ["<i4", "<f8", "<f8"],
                         "offsets": [prrp_solve_info.iterations.offset, prrp_solve_info.eta0.offset,
                                     prrp_solve_info.eta.offset],
@@ -478,7 +490,7 @@ def prrp_batch_solve(ctx: Context, As, Bs, b=16, tau=2.0, prec=PRRP_FP32, max_sw
     ldb = np.ascontiguousarray(mb[:, 3], dtype=np.int32)
     pa = np.ascontiguousarray(ma[:, 0])
     pb = np.ascontiguousarray(mb[:, 0])
-    pp = np.array([p.data_ptr() for p in perms], dtype=np.int64) if perms is not None else None
+    pp = _dev_perms(perms, n) if perms is not None else None
     st = np.zeros(count, dtype=np.int32)
     infos = np.zeros(count, dtype=_INFO_DTYPE)
     o = default_opts(b, tau, prec, max_swaps, refine_max_iter, refine_target)

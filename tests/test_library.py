@@ -103,3 +103,12 @@ def test_batch_marshalling_host_logic():
         arr[i].iterations, arr[i].eta0, arr[i].eta = i + 1, 10.0 ** -i, 2.0 ** -(50 + i)
     view = np.frombuffer(arr, dtype=B._INFO_DTYPE)
     assert view.tolist() == [(i + 1, 10.0 ** -i, 2.0 ** -(50 + i)) for i in range(3)]
+    for perms in ([torch.zeros(8, dtype=torch.int32)],          # host memory
+                  [torch.zeros(8, dtype=torch.int64)],          # wrong type
+                  [torch.zeros(8, dtype=torch.int32)] * 2):     # one per system
+        try:
+            B._dev_perms(perms, np.array([8], dtype=np.int32))
+        except TypeError:
+            pass
+        else:
+            raise AssertionError("a permutation output that the kernel cannot write was accepted")
