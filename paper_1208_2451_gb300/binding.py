@@ -284,9 +284,18 @@ def prrp_solve(ctx: Context, F: Factors, B, A_orig=None, refine_max_iter=10,
     """Overwrite the float64 CUDA tensor B (n x nrhs) with A^-1 B; refine in FP64 against
     A_orig when given."""
     ldb = _dev_matrix(B, "B")
+    if B.shape[0] != F.n:
+        raise ValueError(f"B: {F.n} rows are expected")
+    a0 = None
+    if A_orig is not None:
+        # read by the library as n x n with the factored matrix's leading dimension
+        lda0 = _dev_matrix(A_orig, "A_orig")
+        if tuple(A_orig.shape) != (F.n, F.n) or (F.n > 0 and lda0 != _dev_matrix(F.A, "A")):
+            raise ValueError("A_orig: the unfactored n x n matrix, with the factored matrix's row stride, "
+                             "is expected")
+        a0 = C.c_void_p(A_orig.data_ptr())
     o = default_opts(refine_max_iter=refine_max_iter, refine_target=refine_target)
     info = prrp_solve_info()
-    a0 = C.c_void_p(A_orig.data_ptr()) if A_orig is not None else None
     st = _lib.prrp_solve(ctx.handle, F.handle, a0, B.shape[1], C.c_void_p(B.data_ptr()), ldb,
                          C.byref(o), _stream_ptr(stream), C.byref(info))
     _check(st, "prrp_solve", ctx.handle, allow=(PRRP_ERR_NOT_CONVERGED,))
