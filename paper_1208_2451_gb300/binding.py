@@ -343,11 +343,13 @@ def prrp_panel_select(ctx: Context, P, tau=2.0, max_swaps=64, stream=None):
 
 def prrp_schur_update(ctx: Context, L, U, Cm, prec=PRRP_FP64, stream=None) -> None:
     """Cm -= L @ U on float64 CUDA tensors (k = L.shape[1] <= 128)."""
+    ldl, ldu, ldc = _dev_matrix(L, "L"), _dev_matrix(U, "U"), _dev_matrix(Cm, "C")
     m, k = L.shape
     n = U.shape[1]
-    st = _lib.prrp_schur_update(ctx.handle, m, n, k, C.c_void_p(L.data_ptr()), _dev_matrix(L, "L"),
-                                C.c_void_p(U.data_ptr()), _dev_matrix(U, "U"),
-                                C.c_void_p(Cm.data_ptr()), _dev_matrix(Cm, "C"), int(prec),
+    if U.shape[0] != k or tuple(Cm.shape) != (m, n):
+        raise ValueError("L (m x k), U (k x n) and C (m x n) are expected")
+    st = _lib.prrp_schur_update(ctx.handle, m, n, k, C.c_void_p(L.data_ptr()), ldl,
+                                C.c_void_p(U.data_ptr()), ldu, C.c_void_p(Cm.data_ptr()), ldc, int(prec),
                                 _stream_ptr(stream))
     _check(st, "prrp_schur_update", ctx.handle)
 
