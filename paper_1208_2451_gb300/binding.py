@@ -495,6 +495,8 @@ def prrp_batch_solve(ctx: Context, As, Bs, b=16, tau=2.0, prec=PRRP_FP32, max_sw
         raise ValueError("As, Bs (and perms) must have one entry per system")
     ma = _dev_matrices(As, "A")
     mb = _dev_matrices(Bs, "B")
+    if np.any(ma[:, 1] != ma[:, 2]) or np.any(mb[:, 1] != ma[:, 1]):
+        raise ValueError("each A must be square and each B must have as many rows as its A")
     n = np.ascontiguousarray(ma[:, 1], dtype=np.int32)
     lda = np.ascontiguousarray(ma[:, 3], dtype=np.int32)
     nrhs = np.ascontiguousarray(mb[:, 2], dtype=np.int32)
