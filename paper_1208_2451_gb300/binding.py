@@ -549,8 +549,14 @@ class Server:
 
     def submit(self, A: np.ndarray, B: np.ndarray, X: np.ndarray) -> int:
         """Queue A X = B (host float64 arrays, row-major, kept alive until wait)."""
+        for name, M in (("A", A), ("B", B), ("X", X)):
+            if not isinstance(M, np.ndarray) or M.dtype != np.float64 or M.ndim != 2 or \
+                    (M.shape[1] > 1 and M.strides[1] != 8) or M.strides[0] % 8:
+                raise TypeError(f"{name}: a 2-D float64 host array with contiguous rows is expected")
         n = A.shape[0]
         nrhs = B.shape[1]
+        if A.shape[1] != n or B.shape[0] != n or X.shape != (n, nrhs) or not X.flags.writeable:
+            raise ValueError("A (n x n), B (n x nrhs) and a writable X (n x nrhs) are expected")
         r = prrp_request(n, nrhs, A.ctypes.data, A.strides[0] // 8, B.ctypes.data,
                          max(B.strides[0] // 8, nrhs), X.ctypes.data, max(X.strides[0] // 8, nrhs))
         t = C.c_uint64(0)
